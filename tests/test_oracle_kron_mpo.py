@@ -1,0 +1,118 @@
+"""Pins of the Kronecker-product Hamiltonians and of the FSA MPOs.
+
+The Kronecker builders are pinned by textbook closed forms and by the
+canonical anticommutation relations; the MPOs (Section II-B) are then pinned
+by contracting them to dense matrices and comparing with those builders for
+the Section V models (Heisenberg/J1-J2, Hubbard).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import kron
+
+
+def test_two_site_heisenberg_singlet():
+    # singlet energy of J S1.S2 is -3J/4
+    H = kron.heisenberg_hamiltonian(2, [(0, 1, 1.0)])
+    assert abs(kron.ground_energy(H) + 0.75) < 1e-14
+
+
+def test_four_site_heisenberg_ring():
+    # 4-site periodic Heisenberg ring: E0 = -2 J
+    H = kron.heisenberg_hamiltonian(4, [(0, 1, 1.0), (1, 2, 1.0), (2, 3, 1.0), (0, 3, 1.0)])
+    assert abs(kron.ground_energy(H) + 2.0) < 1e-13
+
+
+@pytest.mark.parametrize("U", [0.0, 4.0, 8.0, 8.5])
+def test_two_site_hubbard(U):
+    # half-filled Hubbard dimer, singlet sector: E0 = (U - sqrt(U^2 + 16 t^2)) / 2
+    H = kron.hubbard_hamiltonian(2, [(0, 1, 1.0)], U)
+    q = kron.basis_charges(2, wl.electron_phys())
+    E = kron.ground_energy(H, q, (2, 0))
+    assert abs(E - (U - np.sqrt(U * U + 16.0)) / 2.0) < 1e-13
+
+
+def test_free_fermions_match_single_particle_levels():
+    # U = 0: the ground energy is the sum of the lowest single-particle levels
+    n, hops = 4, [(0, 1, 1.0), (1, 2, 0.8), (2, 3, 1.0), (0, 3, 0.3), (0, 2, 0.2)]
+    T = np.zeros((n, n))
+    for i, j, t in hops:
+        T[i, j] -= t
+        T[j, i] -= t
+    eps = np.sort(np.linalg.eigvalsh(T))
+    H = kron.hubbard_hamiltonian(n, hops, 0.0)
+    q = kron.basis_charges(n, wl.electron_phys())
+    for nup, ndn in [(2, 2), (1, 2), (3, 1)]:
+        E = kron.ground_energy(H, q, (nup + ndn, nup - ndn))
+        assert abs(E - eps[:nup].sum() - eps[:ndn].sum()) < 1e-12
+
+
+def test_fermion_anticommutation():
+    c = kron.fermion_operators(3)
+    modes = [c[i][s] for i in range(3) for s in range(2)]
+    dim = 4 ** 3
+    I = np.eye(dim)
+    for a, A in enumerate(modes):
+        for b, B in enumerate(modes):
+            Ad, Bd = A.toarray(), B.toarray()
+            assert np.abs(Ad @ Bd + Bd @ Ad).max() < 1e-14
+            acomm = Ad @ Bd.T + Bd.T @ Ad
+            assert np.abs(acomm - (I if a == b else 0.0)).max() < 1e-14
+
+
+def test_site_basis_of_fermions():
+    # |up dn> = c+_up c+_dn |0>  on a single site (state index 3 from index 0)
+    c = kron.fermion_operators(1)
+    vac = np.zeros(4)
+    vac[0] = 1.0
+    v = c[0][0].T.toarray() @ (c[0][1].T.toarray() @ vac)
+    assert np.allclose(v, [0, 0, 0, 1])
+
+
+@pytest.mark.parametrize("n,couplings", [(6, [1.0]), (7, [1.0, 0.5, 0.2, 0.1]), (5, [0.0, 1.0])])
+def test_chain_mpo_equals_kron(n, couplings):
+    pairs = wl.chain_pairs(n, couplings)
+    mpo = wl.heisenberg_mpo(n, pairs)
+    Hm = kron.mpo_to_dense(mpo)
+    Hk = kron.heisenberg_hamiltonian(n, pairs).toarray()
+    assert np.abs(Hm - Hk).max() < 1e-13
+
+
+@pytest.mark.parametrize("Lx,Ly", [(3, 2), (2, 3), (2, 4)])
+def test_j1j2_cylinder_mpo_equals_kron(Lx, Ly):
+    pairs = wl.cylinder_pairs(Lx, Ly, 1.0, 0.5)
+    n = Lx * Ly
+    mpo = wl.heisenberg_mpo(n, pairs)
+    Hm = kron.mpo_to_dense(mpo)
+    Hk = kron.heisenberg_hamiltonian(n, pairs).toarray()
+    assert np.abs(Hm - Hk).max() < 1e-12
+
+
+def test_hubbard_mpo_equals_kron():
+    hops = [(0, 1, 1.0), (1, 2, 0.7), (0, 2, 0.3), (2, 3, 1.1), (0, 3, 0.2)]
+    mpo = wl.hubbard_mpo(4, hops, 8.5)
+    Hm = kron.mpo_to_dense(mpo)
+    Hk = kron.hubbard_hamiltonian(4, hops, 8.5).toarray()
+    assert np.abs(Hm - Hk).max() < 1e-12
+
+
+@pytest.mark.parametrize("which", ["spin", "electron"])
+def test_mpo_charge_rule_and_transpose_symmetry(which):
+    w = wl.spin_heff_workload(64, 8, 0) if which == "spin" else wl.electron_heff_workload(96, 3, 6, 24)
+    for W, ql, qr in [(w.W1, w.ql, w.qm), (w.W2, w.qm, w.qr)]:
+        for wl_, t, s, wr in np.argwhere(W != 0):
+            assert np.array_equal(ql[wl_] + w.phys[t] - w.phys[s], qr[wr])
+    # W[wl,t,s,wr] = W[conj wl, s, t, conj wr] (Hermitian MPO, real)
+    from workloads.fill import spin_window, electron_window
+    win = spin_window() if which == "spin" else electron_window()
+    W1 = win["W1"]
+    cl, cm = win["conj_l"], win["conj_m"]
+    W1t = W1[cl][:, :, :, cm].transpose(0, 2, 1, 3)
+    assert np.abs(W1 - W1t).max() == 0.0
+
+
+def test_bulk_window_bond_dims():
+    from workloads.fill import spin_window, electron_window
+    assert spin_window()["W1"].shape == (14, 2, 2, 14)
+    assert electron_window()["W1"].shape == (22, 4, 4, 22)
