@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark of the two-site H_eff matvec (Section II-C / Fig. 1d) on GB300.
+
+Workload (default): the 6x6 J1-J2 cylinder stand-in at m = 4096: spin-1/2, U(1) Sz,
+40 sectors per bond with multinomial(4096, Binom(39, 1/2)) dimensions (seeds 0 and 1),
+range-4 chain MPO (k = 14, couplings 1, 0.5, 0.2, 0.1), symmetrised Gaussian
+environments, Gaussian two-site tensor (seed 2).  One step = one heff_apply (operator
+preparation + pack + the two grouped GEMMs) on inputs resident in HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (bounded sample per step).  With torchrun (N > 1) every rank runs
+an independent problem (its own two-site tensor): weak scaling, no collective on the
+data path; the time is the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
+    ap.add_argument("--workload", default="spin_m4096")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ peaks and clocks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ problem
+def make_problem(name, batch):
+    import workloads as wl
+    from paper_2007_05540_gb300 import heff
+    w = wl.workload_by_name(name)
+    lays = heff.heff_layouts((w.alpha_q, w.alpha_d), (w.beta_q, w.beta_d), w.phys, w.ql, w.qm, w.qr)
+    Ll, W1l, W2l, Rl, xl = lays
+    bufs = {"L": Ll.assemble(lambda k: w.L_block(k)), "R": Rl.assemble(lambda k: w.R_block(k)),
+            "W1": W1l.assemble(lambda k: w.W1[k]), "W2": W2l.assemble(lambda k: w.W2[k]),
+            "x": xl.assemble(lambda k: w.x_block(k, batch))}
+    return w, lays, bufs
+
+
+def cpu_baseline(name, seconds, batch=0):
+    """The FP64 oracle (as it stands) on the host cores, on sampled output sectors."""
+    import workloads as wl
+    from oracle import heff as oh
+    w = wl.workload_by_name(name)
+    L, W1, W2, R, x = oh.problem_from_workload(w, batch)
+    total = oh.canonical_flops(L, W1, W2, R, x)["total"]
+    nsec = len(w.alpha_d)
+    order = list(range(nsec))
+    t0 = time.perf_counter()
+    done_flops, ns = 0.0, 0
+    while time.perf_counter() - t0 < seconds and ns < nsec:
+        s = order[(ns * 7) % nsec] if nsec % 7 else order[ns]
+        cnt = {}
+        oh.heff_apply(L, W1, W2, R, x, count=cnt, left_sectors={s})
+        done_flops += cnt["gemm1"] + cnt["gemm2"]
+        ns += 1
+    dt = time.perf_counter() - t0
+    rate = done_flops / dt
+    return {"value": rate / total, "unit": "applies/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{ns} of {nsec} output left sectors of one apply ({done_flops:.3e} of "
+                      f"{total:.3e} canonical flops) in {dt:.1f} s; applies/s = flop rate / flops per apply",
+            "tflops": rate / 1e12}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2007_05540_gb300 import heff
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision
+    io = "f64" if prec == "fp64" else "f32"
+    dt = torch.float64 if io == "f64" else torch.float32
+    w, lays, bufs = make_problem(args.workload, rank)
+    Ll, W1l, W2l, Rl, xl = lays
+    plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, io)
+    st = plan.stats
+    d = {k: torch.from_numpy(np.asarray(v)).to(dev, dt) for k, v in bufs.items()}
+    ws = plan.workspace(dev)
+    y = torch.empty_like(d["x"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    def step():
+        heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
+
+    heff.heff_plan_set_timing(plan.handle, True)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    if not args.no_clocks:
+        clocks.start()
+        time.sleep(0.3)
+    n0 = heff.heff_launch_count()
+    step_ms, phases = [], np.zeros(4)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                                   # L2 flush between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        phases += np.array(heff.heff_plan_timings(plan.handle))   # waits for this step
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    launches = heff.heff_launch_count() - n0
+    ck = clocks.stop() if not args.no_clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    phases /= args.steps
+
+    # end to end through the C ABI from pinned host buffers (copies inside the timed region)
+    host = {k: torch.from_numpy(np.asarray(v)).to(dt).pin_memory() for k, v in bufs.items()}
+    y_host = torch.empty(y.numel(), dtype=dt).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = y_host.numel() * y_host.element_size()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for k in d:
+            d[k].copy_(host[k], non_blocking=True)
+        step()
+        y_host.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    peaks, peak_src = measured_peaks()
+    canonical = plan.flops_canonical
+    value = world * 1000.0 / ms
+    g_ms = {"gemm1": phases[2], "gemm2": phases[3]}
+    dom = max(g_ms, key=g_ms.get)
+    useful = float(st[18] if dom == "gemm1" else st[19])
+    if prec == "fp64":
+        # FP64 on CUDA cores: the GB300 FP64 rate (nominal 1.25 TFLOP/s) bounds it
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": 1.25,
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                "achieved": useful / (g_ms[dom] * 1e-3) / 1e12}
+    else:
+        passes = 3
+        base = peaks["bf16_tflops"] * (1.0 if prec == "bf16x3" else 0.5)
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": base,
+                "peak_source": ("bf16 burst, " if prec == "bf16x3" else "bf16 burst x 0.5 (nominal tf32/bf16), ")
+                + peak_src,
+                "achieved": passes * useful / (g_ms[dom] * 1e-3) / 1e12,
+                "note": f"{passes} tensor-core products per useful multiply-add (hi/lo split)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof["launch_ms"] = g_ms[dom]
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"bf16x3": "bf16x3->f32", "tf32x3": "tf32x3->f32", "fp64": "f64"}[prec],
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": args.workload, "m": int(w.alpha_d.sum()), "sectors": int(len(w.alpha_d)),
+                   "mpo_k": int(w.W1.shape[0]), "d": int(w.W1.shape[1]), "precision": prec, "io_dtype": io,
+                   "l2": "flushed (512 MB write) between timed steps; working set > L2",
+                   "parallelism": f"independent problems per rank x{world}"},
+        "tflops_canonical": canonical * value / 1e12,
+        "flops_per_apply": canonical,
+        "phase_ms": {"prepare": phases[0], "pack": phases[1], "gemm1": phases[2], "gemm2": phases[3]},
+        "wall_s": wall,
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "applies/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": ck,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    base = None
+    for _ in range(args.warmup + args.steps):
+        base = cpu_baseline(args.workload, max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))))
+        steps.append(base["value"])
+    v = float(np.median(steps[args.warmup:]))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "applies/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; no dataset)",
+           "config": {"workload": args.workload, "precision": "fp64 oracle (CPU)"},
+           "cpu_baseline": {"value": v, "unit": "applies/s", "cores": base["cores"], "kind": "oracle",
+                            "sample": base["sample"]},
+           "e2e": {"value": v, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

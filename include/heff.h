@@ -1,0 +1,211 @@
+/*
+ * heff.h -- C ABI of the GB300 (sm_103a) two-site effective-Hamiltonian library.
+ *
+ * The operation (Levy, Solomonik, Clark, "Distributed-Memory DMRG via Sparse and
+ * Dense Parallel Tensor Contractions", Section II-C equation for K in the two-site
+ * form of Section III, tensor diagram Fig. 1d) is the matrix-free product
+ *
+ *     y[a',t1,t2,b'] = sum L[a',wl,a] W1[wl,t1,s1,wm] W2[wm,t2,s2,wr] R[b',wr,b] x[a,s1,s2,b]
+ *
+ * with every tensor block-sparse under U(1) (or U(1)^nq) charge conservation
+ * (Section II-D).  All buffers are plain pointers: device pointers for tensors and
+ * workspaces, host pointers for metadata.  No function throws; every function that
+ * can fail returns an int status (HEFF_OK = 0 or a negative HEFF_ERR_* code) and
+ * records a message readable with heff_last_error() on the calling thread.
+ *
+ * Block layout (shared by every tensor argument).  A tensor index is a list of
+ * sectors (charge vector, dimension) plus a flow (+1/-1).  A block is a tuple of
+ * sector numbers, one per index, and is allowed when sum_k flow_k * charge_k equals
+ * the tensor's target charge.  A tensor's buffer holds all allowed blocks in
+ * lexicographic order of their sector tuples, each block dense and row-major over
+ * its index dimensions, with no padding.  heff_layout_blocks() returns the tuples and
+ * element offsets.  Sectors of the bond and physical indices of x must carry distinct
+ * charges; MPO channel indices may repeat a charge.
+ *
+ * Index conventions expected by heff_plan_create (checked, HEFF_ERR_CHARGE_MISMATCH
+ * otherwise):
+ *   x, y : (a, s1, s2, b)   flows (+1, +1, +1, -1)   target: any
+ *   L    : (a', wl, a)      flows (-1, +1, +1)       target 0   (q(a') = q(a) + q(wl))
+ *   R    : (b', wr, b)      flows (-1, +1, +1)       target 0   (q(b') = q(b) + q(wr))
+ *   W1   : (wl, t1, s1, wm) flows (+1, +1, -1, -1)   target 0
+ *   W2   : (wm, t2, s2, wr) flows (+1, +1, -1, -1)   target 0
+ * The bra and ket indices of L are the left bond of x, those of R its right bond;
+ * MPO and physical indices have sectors of dimension 1 (one sector per channel or
+ * per local state).
+ *
+ * Ownership.  The caller owns every device buffer (tensors, workspaces).  Layout and
+ * plan objects are owned by the library (host metadata plus small device tables
+ * allocated at plan creation) until the matching *_destroy call.  Compute calls are
+ * asynchronous on the given CUDA stream (a cudaStream_t passed as void*; NULL is the
+ * legacy default stream) and never synchronise.  A plan may be used by one stream at
+ * a time.
+ */
+#ifndef HEFF_H
+#define HEFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define HEFF_OK 0
+#define HEFF_ERR_INVALID_ARG -1     /* null pointer, bad size, bad option           */
+#define HEFF_ERR_CHARGE_MISMATCH -2 /* layouts inconsistent with the selection rules */
+#define HEFF_ERR_UNSUPPORTED -3     /* precision / dtype / device not supported      */
+#define HEFF_ERR_OOM -4             /* host or device allocation failed             */
+#define HEFF_ERR_CUDA -5            /* a CUDA runtime/driver call failed            */
+#define HEFF_ERR_TIMEOUT -6         /* a bounded device-side wait expired            */
+#define HEFF_ERR_WORKSPACE -7       /* workspace too small or misaligned (256 B)     */
+
+/* ---- precisions and element types ----------------------------------------- */
+#define HEFF_PREC_FP64 0   /* FP64 CUDA-core block GEMMs (reference GPU path)        */
+#define HEFF_PREC_BF16X3 1 /* tcgen05 BF16 hi/lo split, 3 products, FP32 accumulate   */
+#define HEFF_PREC_TF32X3 2 /* tcgen05 TF32 hi/lo split, 3 products, FP32 accumulate   */
+
+#define HEFF_DTYPE_F64 0   /* tensors in device memory are double                   */
+#define HEFF_DTYPE_F32 1   /* tensors in device memory are float (mixed paths only) */
+
+typedef struct heff_index {
+    int32_t nsec;           /* number of sectors (>= 1)                          */
+    int32_t nq;             /* charge components (1..4), equal for all indices   */
+    const int32_t* charges; /* host, [nsec * nq] row-major                        */
+    const int32_t* dims;    /* host, [nsec], each >= 1                            */
+    int32_t flow;           /* +1 or -1                                          */
+} heff_index;
+
+typedef struct heff_layout heff_layout;
+typedef struct heff_plan heff_plan;
+
+typedef struct heff_plan_opts {
+    int32_t precision; /* HEFF_PREC_*                                            */
+    int32_t io_dtype;  /* HEFF_DTYPE_*; FP64 precision requires HEFF_DTYPE_F64    */
+    int32_t max_batch; /* largest nbatch passed to heff_apply_batched (>= 1)      */
+    int32_t reserved[5];
+} heff_plan_opts;
+
+/*
+ * heff_qn_block_layout -- enumerate the allowed blocks of a block-sparse tensor
+ * (Section II-D: "a list of quantum number label tuples, one dense block per tuple";
+ * the label matching of Algorithm 2).  idx: host array of nidx index descriptors
+ * (copied); target: host [nq] charge vector (NULL = zero).  *out receives a new
+ * layout.  Errors: INVALID_ARG (nidx < 1 or > 16, nsec < 1, dims < 1, nq outside
+ * 1..4 or mixed, flow not +-1), OOM.
+ */
+int heff_qn_block_layout(const heff_index* idx, int32_t nidx, const int32_t* target,
+                         heff_layout** out);
+
+/* Number of blocks, total elements and number of indices of a layout. */
+int heff_layout_info(const heff_layout* lay, int64_t* nblocks, int64_t* nelem, int32_t* nidx);
+
+/*
+ * Copy the block list to host arrays: keys [nblocks * nidx] (sector numbers, int32) and
+ * offsets [nblocks] (element offset of each block in the tensor buffer).  Either may be NULL.
+ */
+int heff_layout_blocks(const heff_layout* lay, int32_t* keys, int64_t* offsets);
+
+void heff_layout_destroy(heff_layout* lay);
+
+/*
+ * heff_plan_create -- build the block-triple schedule of y = K x for fixed layouts
+ * (the charge-matched block pairs of Algorithm 2 for both contractions, their GEMM
+ * task lists, workspace layout and flop counts) and upload the schedule tables to the
+ * current CUDA device.  W1_host / W2_host: host copies of the MPO tensors in their
+ * layouts (double); an entry equal to 0.0 is dropped from the schedule, so later calls
+ * must pass device MPO tensors that are zero there too.  Synchronises once (table
+ * upload).  Errors: INVALID_ARG, CHARGE_MISMATCH, UNSUPPORTED, OOM, CUDA.
+ */
+int heff_plan_create(const heff_layout* L, const heff_layout* W1, const heff_layout* W2,
+                     const heff_layout* R, const heff_layout* x, const double* W1_host,
+                     const double* W2_host, const heff_plan_opts* opts, heff_plan** out);
+
+/* Workspace bytes needed by every call on this plan (for nbatch = max_batch). */
+int heff_plan_workspace_size(const heff_plan* plan, size_t* bytes);
+
+/*
+ * Flop counts of one apply.  canonical: sum of 2*M*N*K over the block products of the
+ * two-contraction list algorithm (L-block x x-block, then the MPO-mixed result x
+ * R-block^T), the definition the FP64 oracle counts; executed: sum of 2*M*N*K over the
+ * GEMM tiles this plan issues (valid rows and columns, padded K), per product pass.
+ */
+int heff_plan_flops(const heff_plan* plan, double* canonical, double* executed);
+
+/*
+ * Plan statistics for diagnostics, stats[24]: [0] charge sectors, [1] LW row groups,
+ * [2] RW row groups, [3] GEMM-1 tasks, [4] GEMM-2 tasks, [5] pack tiles, [6] mix tiles,
+ * [7] mix terms, [8] XT rows, [9] XT/LW pitch, [10] LW rows, [11] T rows, [12] T/RW
+ * pitch, [13] RW rows, [14] tile M, [15] tile N, [16] canonical flops of the first
+ * contraction, [17] of the second, [18] GEMM-1 flops over valid rows, columns and
+ * unpadded K, [19] the same for GEMM 2, [20] GEMM-1 issued flops (padded K), [21] GEMM 2.
+ */
+int heff_plan_stats(const heff_plan* plan, int64_t* stats /* [24] */);
+
+/*
+ * Copy one schedule table of the plan into host memory dst (NULL: query only) and its
+ * size in bytes into *bytes.  table: 0 pack tiles, 1 mix tiles, 2 mix terms, 3 GEMM-1
+ * tasks, 4 GEMM-1 segments, 5 GEMM-2 tasks, 6 GEMM-2 segments (record formats in
+ * csrc/internal.h).  For inspection and host-side testing of the schedule.  A plan
+ * created on a machine without a CUDA device is host-only: this call and the query
+ * calls work, compute calls return HEFF_ERR_UNSUPPORTED.
+ */
+int heff_plan_export(const heff_plan* plan, int32_t table, void* dst, int64_t* bytes);
+
+void heff_plan_destroy(heff_plan* plan);
+
+/*
+ * heff_apply -- y = K x (Section II-C / Fig. 1d, two-site).  L, W1, W2, R, x: device
+ * buffers in their layouts, element type opts.io_dtype; y: device buffer in x's layout
+ * (overwritten, must not alias x).  workspace: device, >= heff_plan_workspace_size
+ * bytes, 256-byte aligned, not shared with another call in flight.  stream: cudaStream_t.
+ * Runs heff_prepare then heff_apply_prepared.  Errors: INVALID_ARG, WORKSPACE, CUDA.
+ */
+int heff_apply(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+               const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * heff_prepare -- fold the MPO tensors into the environments inside the workspace
+ * (LW = L.W1 summed over wl, RW = W2.R summed over wr), so that repeated applies with the
+ * same L, W1, W2, R (an eigensolver's Krylov steps) skip that work.  The prepared state
+ * lives in the workspace and is valid until the workspace is reused by another plan.
+ */
+int heff_prepare(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* y = K x using operators prepared in the workspace by heff_prepare. */
+int heff_apply_prepared(heff_plan* plan, const void* x, void* y, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
+/*
+ * heff_apply_batched -- y_b = K x_b for b < nbatch (<= max_batch) vectors sharing L, W1,
+ * W2, R: one preparation and one launch of each GEMM over all vectors.  x, y: HOST arrays
+ * of nbatch device pointers.  Errors as heff_apply.
+ */
+int heff_apply_batched(heff_plan* plan, const void* L, const void* W1, const void* W2,
+                       const void* R, const void* const* x, void* const* y, int32_t nbatch,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Phase timers (the time breakdown of Section VI / Fig. 7, on the GPU): when enabled,
+ * every compute call records CUDA events on its stream around its phases.
+ * heff_plan_timings waits for the last call's final event and writes the milliseconds
+ * of ms[4] = {prepare, pack, GEMM 1, GEMM 2} (prepare is 0 when the call skipped it).
+ */
+int heff_plan_set_timing(heff_plan* plan, int32_t enable);
+int heff_plan_timings(heff_plan* plan, float* ms);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* heff_last_error(void);
+
+/* Number of kernels this library has launched in the process (all threads). */
+int64_t heff_launch_count(void);
+
+/* Library version string. */
+const char* heff_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEFF_H */

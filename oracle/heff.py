@@ -44,8 +44,12 @@ def w12_pattern(W1, W2):
     return np.einsum("atsm,muvr->atusvr", b1, b2) > 0
 
 
-def heff_apply(L, W1, W2, R, x, count=None):
+def heff_apply(L, W1, W2, R, x, count=None, left_sectors=None):
     """y = K x by blocks.  ``count`` (a dict) receives the matmul flop counts.
+
+    ``left_sectors``: if given, only output blocks whose first (a') sector is in this
+    set are computed (the others stay zero); an output block depends only on the
+    step-1 products with that a', so this is a restriction, not an approximation.
 
     ``count['gemm1']``: sum of 2*M*N*K over the step-1 products L-block @ x-block
     that feed a structurally nonzero W12 entry; ``count['gemm2']``: the same
@@ -72,6 +76,8 @@ def heff_apply(L, W1, W2, R, x, count=None):
     for (i, s1, s2, j), xb in x.blocks.items():
         xm = xb[:, 0, 0, :]
         for ip, wl, Lm in L_by_ket.get(i, ()):
+            if left_sectors is not None and ip not in left_sectors:
+                continue
             f = feeds.get((wl, s1, s2))
             if not f:
                 continue

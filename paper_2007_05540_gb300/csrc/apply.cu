@@ -1,0 +1,446 @@
+// Packing, operator preparation, the FP64 CUDA-core block GEMMs, and the C-ABI compute
+// entry points of the two-site H_eff matvec (Section II-C / Fig. 1d).
+//
+// One apply is four launches on the caller's stream:
+//   mix_kernel   LW = L.W1 and RW = W2.R into the workspace (operator preparation)
+//   pack_kernel  x -> XT (per charge sector, transposed so the contraction index is
+//                contiguous; hi/lo split for the tensor-core precisions)
+//   GEMM 1       T = LW . XT^T              (tensor cores: tc_gemm.cu; FP64: below)
+//   GEMM 2       y = T . RW^T               (written straight into y's block layout)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "internal.h"
+
+using heff::fail;
+
+namespace heff {
+
+// ------------------------------------------------------------------ element planes
+// A workspace operand is stored as `planes` arrays of one element type:
+//   FP64   : one double plane
+//   BF16X3 : hi = bf16(v), lo = bf16(v - hi)
+//   TF32X3 : hi = v with the 13 low mantissa bits cleared (exact in TF32), lo = v - hi
+template <int PREC> struct Plane;
+template <> struct Plane<HEFF_PREC_FP64> {
+    using T = double;
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { hi = v; lo = 0.0; }
+};
+template <> struct Plane<HEFF_PREC_BF16X3> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
+        float f = (float)v;
+        hi = __float2bfloat16_rn(f);
+        lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+    }
+};
+template <> struct Plane<HEFF_PREC_TF32X3> {
+    using T = float;
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
+        float f = (float)v;
+        hi = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
+        lo = f - hi;
+    }
+};
+
+constexpr int MAXB = 64;   // batch entries per launch (kernel parameter arrays)
+struct PtrBatch { const void* p[MAXB]; };
+
+// ------------------------------------------------------------------ pack x -> XT
+template <typename In, int PREC>
+__global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, PtrBatch xs,
+                                                   char* __restrict__ xt, int64_t ld, int64_t plane_elems,
+                                                   int64_t batch_elems) {
+    using E = typename Plane<PREC>::T;
+    __shared__ double s[32][33];
+    const PackTile t = tiles[blockIdx.x];
+    const In* x = static_cast<const In*>(xs.p[blockIdx.y]);
+    E* hi = reinterpret_cast<E*>(xt) + (int64_t)blockIdx.y * batch_elems;
+    E* lo = hi + plane_elems;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // read rows a (stride m_b), columns b contiguous
+    for (int r = ty; r < 32; r += 8) {
+        int a = t.a0 + r, b = t.b0 + tx;
+        double v = 0.0;
+        if (a < t.m_a && b < t.m_b) v = (double)x[t.x_off + (int64_t)a * t.m_b + b];
+        s[r][tx] = v;
+    }
+    __syncthreads();
+    // write XT rows b, columns a contiguous (a in [m_a, a_pad) are zero padding)
+    for (int r = ty; r < 32; r += 8) {
+        int b = t.b0 + r, a = t.a0 + tx;
+        if (b < t.m_b && a < t.a_pad) {
+            E h, l;
+            Plane<PREC>::split(s[tx][r], h, l);
+            int64_t o = (t.xt_row0 + b) * ld + t.xt_col0 + a;
+            hi[o] = h;
+            if (PREC != HEFF_PREC_FP64) lo[o] = l;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ LW / RW preparation
+template <typename In, int PREC>
+__global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ tiles,
+                                                  const MixTerm* __restrict__ terms,
+                                                  const In* __restrict__ L, const In* __restrict__ W1,
+                                                  const In* __restrict__ W2, const In* __restrict__ R,
+                                                  char* __restrict__ lw, int64_t ld_lw, int64_t lw_plane,
+                                                  char* __restrict__ rw, int64_t ld_rw, int64_t rw_plane) {
+    using E = typename Plane<PREC>::T;
+    __shared__ double coef[64];
+    __shared__ int64_t srco[64];
+    const MixTile t = tiles[blockIdx.x];
+    const In* src = t.which ? R : L;
+    const In* W = t.which ? W2 : W1;
+    const int nt = t.term_count < 64 ? t.term_count : 64;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+        MixTerm m = terms[t.term_begin + k];
+        coef[k] = (double)W[m.w_idx];
+        srco[k] = m.src_off;
+    }
+    __syncthreads();
+    E* hi = reinterpret_cast<E*>(t.which ? rw : lw);
+    const int64_t ld = t.which ? ld_rw : ld_lw;
+    E* lo = hi + (t.which ? rw_plane : lw_plane);
+    const int total = t.nrows * t.cols_pad;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int r = t.r0 + e / t.cols_pad, c = e % t.cols_pad;
+        double acc = 0.0;
+        if (c < t.cols) {
+            int64_t rc = (int64_t)r * t.cols + c;
+            for (int k = 0; k < nt; ++k) acc += coef[k] * (double)src[srco[k] + rc];
+            for (int k = 64; k < t.term_count; ++k) {     // rare: more than 64 terms
+                MixTerm m = terms[t.term_begin + k];
+                acc += (double)W[m.w_idx] * (double)src[m.src_off + rc];
+            }
+        }
+        E h, l;
+        Plane<PREC>::split(acc, h, l);
+        int64_t o = (t.dst_row0 + r) * ld + t.dst_col0 + c;
+        hi[o] = h;
+        if (PREC != HEFF_PREC_FP64) lo[o] = l;
+    }
+}
+
+// ------------------------------------------------------------------ FP64 CUDA-core GEMM
+// C[m x n] = sum_seg A[a_row + r, k] B[b_row + c, k] over 64 x 64 tiles, 4 x 4 per thread.
+struct GemmArgs {
+    const GemmTask* tasks;
+    const KSeg* segs;
+    int ntasks;
+    const char* A; int64_t a_batch_rows;    // operand arrays and their per-batch row offsets
+    const char* B; int64_t b_batch_rows;
+    int64_t ld;                             // shared row pitch of A and B
+    char* C; int64_t c_batch_elems;         // GEMM 1 output (T) and per-batch offset
+    PtrBatch y;                             // GEMM 2 outputs (one per batch entry)
+    int mode;                               // 0: write T (plane type), 1: write y (io type)
+    int64_t c_plane_elems;                  // plane stride of T
+};
+
+__global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
+    __shared__ double As[16][64 + 1];
+    __shared__ double Bs[16][64 + 1];
+    const GemmTask t = g.tasks[blockIdx.x];
+    const int bz = blockIdx.y;
+    const double* A = reinterpret_cast<const double*>(g.A) + (int64_t)bz * g.a_batch_rows * g.ld;
+    const double* B = reinterpret_cast<const double*>(g.B) + (int64_t)bz * g.b_batch_rows * g.ld;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    for (int s = 0; s < t.seg_count; ++s) {
+        const KSeg sg = g.segs[t.seg_begin + s];
+        for (int k0 = sg.k0; k0 < sg.k0 + sg.klen; k0 += 16) {
+            for (int l = 0; l < 4; ++l) {
+                int idx = tid + 256 * l, row = idx >> 4, kk = idx & 15;
+                As[kk][row] = row < t.m ? A[(t.a_row + row) * g.ld + k0 + kk] : 0.0;
+                Bs[kk][row] = row < t.n ? B[(t.b_row + row) * g.ld + k0 + kk] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+    double* C = g.mode == 0 ? reinterpret_cast<double*>(g.C) + (int64_t)bz * g.c_batch_elems
+                            : static_cast<double*>(const_cast<void*>(g.y.p[bz]));
+    for (int i = 0; i < 4; ++i) {
+        int r = ty * 4 + i;
+        if (r >= t.m) continue;
+        for (int j = 0; j < 4; ++j) {
+            int c = tx * 4 + j;
+            if (c < t.n) C[t.c_off + (int64_t)r * t.ldc + c] = acc[i][j];
+            else if (c < t.n + t.n_zero) C[t.c_off + (int64_t)r * t.ldc + c] = 0.0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return fail(HEFF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+static int upload(const std::vector<T>& v, T** d) {
+    *d = nullptr;
+    if (v.empty()) return HEFF_OK;
+    CK(cudaMalloc((void**)d, v.size() * sizeof(T)));
+    CK(cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HEFF_OK;
+}
+
+int plan_upload(heff_plan* p) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();          // no device: a host-only plan for inspection
+        p->uploaded = false;
+        return HEFF_OK;
+    }
+    CK(cudaGetDevice(&p->device));
+    CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    int rc;
+    if ((rc = upload(p->pack, &p->d_pack)) != HEFF_OK) return rc;
+    if ((rc = upload(p->mix, &p->d_mix)) != HEFF_OK) return rc;
+    if ((rc = upload(p->terms, &p->d_terms)) != HEFF_OK) return rc;
+    for (GemmList* g : {&p->g1, &p->g2}) {
+        if ((rc = upload(g->tasks, &g->d_tasks)) != HEFF_OK) return rc;
+        if ((rc = upload(g->segs, &g->d_segs)) != HEFF_OK) return rc;
+    }
+    p->uploaded = true;
+    return HEFF_OK;
+}
+
+void record_phase(heff_plan* p, int k, void* stream) {
+    if (p->timing && p->ev[k]) cudaEventRecord(static_cast<cudaEvent_t>(p->ev[k]), static_cast<cudaStream_t>(stream));
+}
+
+void plan_free_device(heff_plan* p) {
+    for (int k = 0; k < 5; ++k)
+        if (p->ev[k]) { cudaEventDestroy(static_cast<cudaEvent_t>(p->ev[k])); p->ev[k] = nullptr; }
+    cudaFree(p->d_pack); cudaFree(p->d_mix); cudaFree(p->d_terms);
+    cudaFree(p->g1.d_tasks); cudaFree(p->g1.d_segs); cudaFree(p->g2.d_tasks); cudaFree(p->g2.d_segs);
+    p->d_pack = nullptr; p->d_mix = nullptr; p->d_terms = nullptr;
+    p->g1.d_tasks = p->g2.d_tasks = nullptr; p->g1.d_segs = p->g2.d_segs = nullptr;
+}
+
+static int64_t plane_elems_xt(const heff_plan* p) { return (int64_t)p->opts.max_batch * p->rows_x * p->ld_x; }
+
+template <typename In, int PREC>
+static void launch_pack_t(heff_plan* p, const PtrBatch& xs, int nb, char* ws, cudaStream_t st) {
+    dim3 grid((unsigned)p->pack.size(), nb);
+    pack_kernel<In, PREC><<<grid, 256, 0, st>>>(p->d_pack, xs, ws + p->off_xt, p->ld_x, plane_elems_xt(p),
+                                               p->rows_x * p->ld_x);
+}
+
+int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->pack.empty()) return HEFF_OK;
+    for (int b0 = 0; b0 < nbatch; b0 += MAXB) {
+        int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
+        PtrBatch xs{};
+        for (int b = 0; b < nb; ++b) xs.p[b] = x[b0 + b];
+        char* w = static_cast<char*>(ws) + (size_t)b0 * p->rows_x * p->ld_x * p->esize;
+        const bool f32 = p->opts.io_dtype == HEFF_DTYPE_F32;
+        switch (p->opts.precision) {
+            case HEFF_PREC_FP64: launch_pack_t<double, HEFF_PREC_FP64>(p, xs, nb, w, st); break;
+            case HEFF_PREC_BF16X3:
+                if (f32) launch_pack_t<float, HEFF_PREC_BF16X3>(p, xs, nb, w, st);
+                else launch_pack_t<double, HEFF_PREC_BF16X3>(p, xs, nb, w, st);
+                break;
+            default:
+                if (f32) launch_pack_t<float, HEFF_PREC_TF32X3>(p, xs, nb, w, st);
+                else launch_pack_t<double, HEFF_PREC_TF32X3>(p, xs, nb, w, st);
+        }
+        count_launches(1);
+    }
+    CK(cudaGetLastError());
+    return HEFF_OK;
+}
+
+template <typename In, int PREC>
+static void launch_mix_t(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R,
+                         char* ws, cudaStream_t st) {
+    mix_kernel<In, PREC><<<(unsigned)p->mix.size(), 256, 0, st>>>(
+        p->d_mix, p->d_terms, (const In*)L, (const In*)W1, (const In*)W2, (const In*)R,
+        ws + p->off_lw, p->ld_x, p->rows_lw * p->ld_x, ws + p->off_rw, p->ld_t, p->rows_rw * p->ld_t);
+}
+
+int launch_mix(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R, void* ws,
+               void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->mix.empty()) return HEFF_OK;
+    char* w = static_cast<char*>(ws);
+    const bool f32 = p->opts.io_dtype == HEFF_DTYPE_F32;
+    switch (p->opts.precision) {
+        case HEFF_PREC_FP64: launch_mix_t<double, HEFF_PREC_FP64>(p, L, W1, W2, R, w, st); break;
+        case HEFF_PREC_BF16X3:
+            if (f32) launch_mix_t<float, HEFF_PREC_BF16X3>(p, L, W1, W2, R, w, st);
+            else launch_mix_t<double, HEFF_PREC_BF16X3>(p, L, W1, W2, R, w, st);
+            break;
+        default:
+            if (f32) launch_mix_t<float, HEFF_PREC_TF32X3>(p, L, W1, W2, R, w, st);
+            else launch_mix_t<double, HEFF_PREC_TF32X3>(p, L, W1, W2, R, w, st);
+    }
+    count_launches(1);
+    CK(cudaGetLastError());
+    return HEFF_OK;
+}
+
+int launch_tc_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream);
+
+int launch_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream) {
+    if (p->opts.precision != HEFF_PREC_FP64) return launch_tc_gemm(p, which, ws, y, nbatch, stream);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const GemmList& gl = which == 1 ? p->g1 : p->g2;
+    if (gl.tasks.empty()) return HEFF_OK;
+    char* w = static_cast<char*>(ws);
+    for (int b0 = 0; b0 < nbatch; b0 += MAXB) {
+        int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
+        GemmArgs g{};
+        g.tasks = gl.d_tasks;
+        g.segs = gl.d_segs;
+        g.ntasks = (int)gl.tasks.size();
+        if (which == 1) {
+            g.A = w + p->off_lw; g.a_batch_rows = 0;
+            g.B = w + p->off_xt + (size_t)b0 * p->rows_x * p->ld_x * 8; g.b_batch_rows = p->rows_x;
+            g.ld = p->ld_x;
+            g.C = w + p->off_t + (size_t)b0 * p->rows_t * p->ld_t * 8; g.c_batch_elems = p->rows_t * p->ld_t;
+            g.mode = 0;
+        } else {
+            g.A = w + p->off_t + (size_t)b0 * p->rows_t * p->ld_t * 8; g.a_batch_rows = p->rows_t;
+            g.B = w + p->off_rw; g.b_batch_rows = 0;
+            g.ld = p->ld_t;
+            for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
+            g.mode = 1;
+        }
+        dim3 grid((unsigned)gl.tasks.size(), nb);
+        gemm_fp64_kernel<<<grid, 256, 0, st>>>(g);
+        count_launches(1);
+    }
+    CK(cudaGetLastError());
+    return HEFF_OK;
+}
+
+}  // namespace heff
+
+// ------------------------------------------------------------------ C ABI
+static int check_ws(const heff_plan* p, void* ws, size_t bytes) {
+    if (!p->uploaded) return fail(HEFF_ERR_UNSUPPORTED, "plan was created without a CUDA device");
+    if (!ws) return fail(HEFF_ERR_WORKSPACE, "null workspace");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(HEFF_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (bytes < p->ws_bytes)
+        return fail(HEFF_ERR_WORKSPACE, "workspace of %zu bytes, plan needs %zu", bytes, p->ws_bytes);
+    return HEFF_OK;
+}
+
+static int do_prepare(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                      void* workspace, void* stream) {
+    heff::record_phase(plan, 0, stream);
+    int rc = heff::launch_mix(plan, L, W1, W2, R, workspace, stream);
+    heff::record_phase(plan, 1, stream);
+    return rc;
+}
+
+static int do_matvec(heff_plan* plan, const void* const* x, void* const* y, int nbatch, void* workspace,
+                     void* stream) {
+    int rc;
+    if ((rc = heff::launch_pack_batch(plan, x, nbatch, workspace, stream))) return rc;
+    heff::record_phase(plan, 2, stream);
+    if ((rc = heff::launch_gemm(plan, 1, workspace, y, nbatch, stream))) return rc;
+    heff::record_phase(plan, 3, stream);
+    if ((rc = heff::launch_gemm(plan, 2, workspace, y, nbatch, stream))) return rc;
+    heff::record_phase(plan, 4, stream);
+    return HEFF_OK;
+}
+
+extern "C" int heff_prepare(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !L || !W1 || !W2 || !R) return fail(HEFF_ERR_INVALID_ARG, "heff_prepare: null argument");
+    int rc = check_ws(plan, workspace, workspace_bytes);
+    if (rc) return rc;
+    plan->ev_prepare = true;
+    return do_prepare(plan, L, W1, W2, R, workspace, stream);
+}
+
+extern "C" int heff_apply_prepared(heff_plan* plan, const void* x, void* y, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_apply_prepared: null argument");
+    if (x == y) return fail(HEFF_ERR_INVALID_ARG, "y must not alias x");
+    int rc = check_ws(plan, workspace, workspace_bytes);
+    if (rc) return rc;
+    const void* xs[1] = {x};
+    void* ys[1] = {y};
+    plan->ev_prepare = false;
+    heff::record_phase(plan, 1, stream);
+    return do_matvec(plan, xs, ys, 1, workspace, stream);
+}
+
+extern "C" int heff_apply(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                          const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_apply: null argument");
+    if (x == y) return fail(HEFF_ERR_INVALID_ARG, "y must not alias x");
+    int rc = check_ws(plan, workspace, workspace_bytes);
+    if (rc) return rc;
+    const void* xs[1] = {x};
+    void* ys[1] = {y};
+    plan->ev_prepare = true;
+    if ((rc = do_prepare(plan, L, W1, W2, R, workspace, stream))) return rc;
+    return do_matvec(plan, xs, ys, 1, workspace, stream);
+}
+
+extern "C" int heff_apply_batched(heff_plan* plan, const void* L, const void* W1, const void* W2,
+                                  const void* R, const void* const* x, void* const* y, int32_t nbatch,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x || !y)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_apply_batched: null argument");
+    if (nbatch < 1 || nbatch > plan->opts.max_batch)
+        return fail(HEFF_ERR_INVALID_ARG, "nbatch %d outside 1..max_batch (%d)", nbatch, plan->opts.max_batch);
+    for (int b = 0; b < nbatch; ++b) {
+        if (!x[b] || !y[b]) return fail(HEFF_ERR_INVALID_ARG, "null x or y at batch entry %d", b);
+        if (x[b] == y[b]) return fail(HEFF_ERR_INVALID_ARG, "y must not alias x (batch entry %d)", b);
+    }
+    int rc = check_ws(plan, workspace, workspace_bytes);
+    if (rc) return rc;
+    plan->ev_prepare = true;
+    if ((rc = do_prepare(plan, L, W1, W2, R, workspace, stream))) return rc;
+    return do_matvec(plan, x, y, nbatch, workspace, stream);
+}
+
+extern "C" int heff_plan_set_timing(heff_plan* plan, int32_t enable) {
+    heff::clear_error();
+    if (!plan) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_set_timing: null plan");
+    if (!plan->uploaded) return fail(HEFF_ERR_UNSUPPORTED, "plan was created without a CUDA device");
+    if (enable && !plan->ev[0])
+        for (int k = 0; k < 5; ++k) CK(cudaEventCreate(reinterpret_cast<cudaEvent_t*>(&plan->ev[k])));
+    plan->timing = enable != 0;
+    return HEFF_OK;
+}
+
+extern "C" int heff_plan_timings(heff_plan* plan, float* ms) {
+    heff::clear_error();
+    if (!plan || !ms) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_timings: null argument");
+    if (!plan->timing) return fail(HEFF_ERR_INVALID_ARG, "timing is not enabled on this plan");
+    cudaEvent_t* e = reinterpret_cast<cudaEvent_t*>(plan->ev);
+    CK(cudaEventSynchronize(e[4]));
+    ms[0] = 0.f;
+    if (plan->ev_prepare) CK(cudaEventElapsedTime(&ms[0], e[0], e[1]));
+    CK(cudaEventElapsedTime(&ms[1], e[1], e[2]));
+    CK(cudaEventElapsedTime(&ms[2], e[2], e[3]));
+    CK(cudaEventElapsedTime(&ms[3], e[3], e[4]));
+    return HEFF_OK;
+}

@@ -1,0 +1,141 @@
+// Internal declarations shared by the host planner (plan.cpp, capi.cpp) and the
+// CUDA translation units.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/heff.h"
+
+namespace heff {
+
+// Padding unit of every contraction (K) segment in the workspace operand arrays:
+// one 128-byte row of a 64-element bf16 TMA box.  K tiles never straddle segments.
+constexpr int KPAD = 64;
+
+inline int64_t pad_up(int64_t v, int64_t p) { return (v + p - 1) / p * p; }
+
+int fail(int code, const char* fmt, ...);
+void clear_error();
+void count_launches(int64_t n);
+
+struct IndexDesc {
+    int nsec = 0, nq = 0, flow = 1;
+    std::vector<int32_t> charges;   // nsec * nq
+    std::vector<int32_t> dims;      // nsec
+    std::vector<int32_t> q(int s) const {
+        return std::vector<int32_t>(charges.begin() + s * nq, charges.begin() + (s + 1) * nq);
+    }
+    int find(const std::vector<int32_t>& qv) const;
+    bool same_sectors(const IndexDesc& o) const { return charges == o.charges && dims == o.dims; }
+};
+
+// ---------------------------------------------------------------- device tables
+// x block -> XT (x transposed per charge sector, contraction index contiguous)
+struct PackTile {
+    int64_t x_off;     // element offset of the x block (rows a, cols b, row-major)
+    int64_t xt_row0;   // XT row of b = 0 of this block
+    int32_t xt_col0;   // XT column of a = 0 of this block
+    int32_t m_a, m_b;  // block dims
+    int32_t a_pad;     // padded extent of a (multiple of KPAD): columns [m_a, a_pad) get 0
+    int32_t a0, b0;    // origin of this 32 x 32 tile inside the block
+};
+
+// LW / RW preparation: dst[r][c] = sum_t W[w_idx_t] * src[src_off_t + r * cols + c]
+struct MixTile {
+    int64_t dst_row0;  // first destination row in LW or RW
+    int32_t dst_col0;  // first destination column (segment start)
+    int32_t rows, cols, cols_pad;
+    int32_t r0, nrows; // row range handled by this tile
+    int32_t term_begin, term_count;
+    int32_t which;     // 0: L with W1 into LW, 1: R with W2 into RW
+};
+struct MixTerm {
+    int64_t src_off;   // element offset of the environment block
+    int32_t w_idx;     // element index into the MPO buffer
+    int32_t pad_;
+};
+
+// One output tile C[m x n] = sum over segments of A[a_row.., k0:k0+klen] . B[b_row.., k0:k0+klen]^T
+struct GemmTask {
+    int64_t a_row, b_row;   // first row of the tile in the A and B operand arrays
+    int64_t c_off;          // element offset of the tile origin in the output
+    int32_t m, n;           // valid rows / columns of the tile
+    int32_t ldc;            // output row pitch (elements)
+    int32_t n_zero;         // columns [n, n + n_zero) of the tile are written as 0 (padding)
+    int32_t seg_begin, seg_count;
+};
+struct KSeg {
+    int32_t k0, klen;       // column range shared by A and B (klen multiple of KPAD)
+};
+
+struct GemmList {
+    std::vector<GemmTask> tasks;
+    std::vector<KSeg> segs;
+    GemmTask* d_tasks = nullptr;
+    KSeg* d_segs = nullptr;
+    int tm = 0, tn = 0;
+    double flops = 0;       // executed (valid m, n; padded K)
+    double useful = 0;      // valid m, n and unpadded K
+};
+
+}  // namespace heff
+
+struct heff_layout {
+    std::vector<heff::IndexDesc> idx;
+    std::vector<int32_t> target;
+    int nq = 0;
+    std::vector<int32_t> keys;      // nblocks * nidx
+    std::vector<int64_t> offsets;   // nblocks
+    int64_t nelem = 0;
+    std::map<std::vector<int32_t>, int64_t> block_of;
+    int64_t offset_of(const std::vector<int32_t>& key) const {
+        auto it = block_of.find(key);
+        return it == block_of.end() ? -1 : offsets[it->second];
+    }
+};
+
+struct heff_plan {
+    heff_plan_opts opts{};
+    int planes = 1;           // operand planes (hi/lo) in the workspace
+    int esize = 8;            // bytes per plane element
+    int64_t nelem_x = 0, nelem_L = 0, nelem_R = 0, nelem_W1 = 0, nelem_W2 = 0;
+    // operand arrays (rows x pitch, per plane)
+    int64_t rows_x = 0, ld_x = 0, rows_lw = 0, rows_t = 0, ld_t = 0, rows_rw = 0;
+    // workspace byte offsets
+    size_t off_xt = 0, off_lw = 0, off_t = 0, off_rw = 0, off_flags = 0, ws_bytes = 0;
+    double flops_canonical = 0;
+    // device tables
+    std::vector<heff::PackTile> pack;
+    std::vector<heff::MixTile> mix;
+    std::vector<heff::MixTerm> terms;
+    heff::PackTile* d_pack = nullptr;
+    heff::MixTile* d_mix = nullptr;
+    heff::MixTerm* d_terms = nullptr;
+    heff::GemmList g1, g2;
+    int64_t stats[24] = {0};
+    // tensor-map cache for the tensor-core path (keyed by workspace pointer)
+    void* tmap_ws = nullptr;
+    alignas(64) unsigned char tmaps[8][128];
+    int device = 0;
+    int num_sms = 0;
+    bool uploaded = false;    // false: created without a CUDA device (inspection only)
+    // phase timers: events recorded around prepare, pack, GEMM 1, GEMM 2 when enabled
+    bool timing = false;
+    void* ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool ev_prepare = false;  // whether the last call ran the prepare phase
+};
+
+namespace heff {
+// launchers (apply.cu)
+int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, void* stream);
+int launch_mix(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R,
+               void* ws, void* stream);
+int launch_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream);
+int plan_upload(heff_plan* p);
+void plan_free_device(heff_plan* p);
+void record_phase(heff_plan* p, int k, void* stream);
+}  // namespace heff

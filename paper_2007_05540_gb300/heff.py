@@ -1,0 +1,333 @@
+"""Python binding of the C ABI in include/heff.h (ctypes; argument marshalling only).
+
+Every function named ``heff_*`` here calls the C function of the same name in the
+in-tree ``libheff.so``; device buffers are passed as ``torch.Tensor`` (their
+``data_ptr()``) and streams as ``torch.cuda.Stream`` (default: the current
+stream).  If the library has not been built this module raises ImportError: there is
+no fallback implementation.
+
+``Layout`` and ``Plan`` are small owners of the C handles with helpers to move block
+tensors between a per-block description and the flat buffer layout.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libheff.so")
+if not os.path.exists(_LIBPATH):
+    raise ImportError(f"{_LIBPATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = C.CDLL(_LIBPATH)
+
+HEFF_OK = 0
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+DTYPE = {"f64": 0, "f32": 1}
+ERRORS = {-1: "INVALID_ARG", -2: "CHARGE_MISMATCH", -3: "UNSUPPORTED", -4: "OOM", -5: "CUDA",
+          -6: "TIMEOUT", -7: "WORKSPACE"}
+
+
+class HeffError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what} failed with {ERRORS.get(code, code)}: "
+                         f"{_lib.heff_last_error().decode()}")
+
+
+class _Index(C.Structure):
+    _fields_ = [("nsec", C.c_int32), ("nq", C.c_int32), ("charges", C.POINTER(C.c_int32)),
+                ("dims", C.POINTER(C.c_int32)), ("flow", C.c_int32)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("io_dtype", C.c_int32), ("max_batch", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+_vp, _i32, _i64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+_P = C.POINTER
+_sig = {
+    "heff_qn_block_layout": (C.c_int, [_P(_Index), _i32, _P(_i32), _P(_vp)]),
+    "heff_layout_info": (C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i32)]),
+    "heff_layout_blocks": (C.c_int, [_vp, _P(_i32), _P(_i64)]),
+    "heff_layout_destroy": (None, [_vp]),
+    "heff_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _P(C.c_double),
+                                   _P(_Opts), _P(_vp)]),
+    "heff_plan_workspace_size": (C.c_int, [_vp, _P(_sz)]),
+    "heff_plan_flops": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double)]),
+    "heff_plan_stats": (C.c_int, [_vp, _P(_i64)]),
+    "heff_plan_export": (C.c_int, [_vp, _i32, _vp, _P(_i64)]),
+    "heff_plan_destroy": (None, [_vp]),
+    "heff_prepare": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "heff_apply_prepared": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
+    "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
+    "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
+    "heff_last_error": (C.c_char_p, []),
+    "heff_launch_count": (C.c_int64, []),
+    "heff_version": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+def _check(rc, what):
+    if rc != HEFF_OK:
+        raise HeffError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        s = torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ C-named functions
+def heff_qn_block_layout(indices, target=None):
+    """indices: list of (charges [nsec, nq] int, dims [nsec] int, flow +-1)."""
+    keep = []
+    arr = (_Index * len(indices))()
+    nq = None
+    for k, (q, d, flow) in enumerate(indices):
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.int32).reshape(len(d), -1))
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.int32))
+        nq = q.shape[1]
+        keep += [q, d]
+        arr[k] = _Index(len(d), nq, q.ctypes.data_as(_P(_i32)), d.ctypes.data_as(_P(_i32)), int(flow))
+    tgt = None
+    if target is not None:
+        t = np.ascontiguousarray(np.asarray(target, dtype=np.int32).reshape(-1))
+        keep.append(t)
+        tgt = t.ctypes.data_as(_P(_i32))
+    out = _vp()
+    _check(_lib.heff_qn_block_layout(arr, len(indices), tgt, C.byref(out)), "heff_qn_block_layout")
+    return out
+
+
+def heff_layout_info(lay):
+    nb, ne, ni = _i64(), _i64(), _i32()
+    _check(_lib.heff_layout_info(lay, C.byref(nb), C.byref(ne), C.byref(ni)), "heff_layout_info")
+    return nb.value, ne.value, ni.value
+
+
+def heff_layout_blocks(lay):
+    nb, ne, ni = heff_layout_info(lay)
+    keys = np.zeros((nb, ni), dtype=np.int32)
+    offs = np.zeros(nb, dtype=np.int64)
+    _check(_lib.heff_layout_blocks(lay, keys.ctypes.data_as(_P(_i32)), offs.ctypes.data_as(_P(_i64))),
+           "heff_layout_blocks")
+    return keys, offs
+
+
+def heff_layout_destroy(lay):
+    _lib.heff_layout_destroy(lay)
+
+
+def heff_plan_create(L, W1, W2, R, x, W1_host, W2_host, precision="bf16x3", io_dtype="f32",
+                     max_batch=1):
+    w1 = np.ascontiguousarray(W1_host, dtype=np.float64)
+    w2 = np.ascontiguousarray(W2_host, dtype=np.float64)
+    opts = _Opts(PREC[precision], DTYPE[io_dtype], int(max_batch))
+    out = _vp()
+    _check(_lib.heff_plan_create(L, W1, W2, R, x, w1.ctypes.data_as(_P(C.c_double)),
+                                 w2.ctypes.data_as(_P(C.c_double)), C.byref(opts), C.byref(out)),
+           "heff_plan_create")
+    return out
+
+
+def heff_plan_workspace_size(plan):
+    b = _sz()
+    _check(_lib.heff_plan_workspace_size(plan, C.byref(b)), "heff_plan_workspace_size")
+    return b.value
+
+
+def heff_plan_flops(plan):
+    c, e = C.c_double(), C.c_double()
+    _check(_lib.heff_plan_flops(plan, C.byref(c), C.byref(e)), "heff_plan_flops")
+    return c.value, e.value
+
+
+def heff_plan_stats(plan):
+    s = np.zeros(24, dtype=np.int64)
+    _check(_lib.heff_plan_stats(plan, s.ctypes.data_as(_P(_i64))), "heff_plan_stats")
+    return s
+
+
+def heff_plan_destroy(plan):
+    _lib.heff_plan_destroy(plan)
+
+
+# record formats of the schedule tables (match csrc/internal.h)
+TABLE_DTYPES = {
+    0: np.dtype([("x_off", "<i8"), ("xt_row0", "<i8"), ("xt_col0", "<i4"), ("m_a", "<i4"),
+                 ("m_b", "<i4"), ("a_pad", "<i4"), ("a0", "<i4"), ("b0", "<i4")]),
+    1: np.dtype([("dst_row0", "<i8"), ("dst_col0", "<i4"), ("rows", "<i4"), ("cols", "<i4"),
+                 ("cols_pad", "<i4"), ("r0", "<i4"), ("nrows", "<i4"), ("term_begin", "<i4"),
+                 ("term_count", "<i4"), ("which", "<i4"), ("_pad", "<i4")]),
+    2: np.dtype([("src_off", "<i8"), ("w_idx", "<i4"), ("_pad", "<i4")]),
+    3: np.dtype([("a_row", "<i8"), ("b_row", "<i8"), ("c_off", "<i8"), ("m", "<i4"), ("n", "<i4"),
+                 ("ldc", "<i4"), ("n_zero", "<i4"), ("seg_begin", "<i4"), ("seg_count", "<i4")]),
+    4: np.dtype([("k0", "<i4"), ("klen", "<i4")]),
+}
+TABLE_DTYPES[5] = TABLE_DTYPES[3]
+TABLE_DTYPES[6] = TABLE_DTYPES[4]
+
+
+def heff_plan_export(plan, table):
+    """The plan's schedule table as a numpy structured array."""
+    n = _i64()
+    _check(_lib.heff_plan_export(plan, int(table), None, C.byref(n)), "heff_plan_export")
+    dt = TABLE_DTYPES[int(table)]
+    if n.value % dt.itemsize:
+        raise HeffError(-1, f"heff_plan_export: record size mismatch for table {table}")
+    out = np.zeros(n.value // dt.itemsize, dtype=dt)
+    if n.value:
+        _check(_lib.heff_plan_export(plan, int(table), C.c_void_p(out.ctypes.data), C.byref(n)),
+               "heff_plan_export")
+    return out
+
+
+def heff_prepare(plan, L, W1, W2, R, ws, stream=None):
+    _check(_lib.heff_prepare(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(ws), _nbytes(ws),
+                             _stream(stream)), "heff_prepare")
+
+
+def heff_apply_prepared(plan, x, y, ws, stream=None):
+    _check(_lib.heff_apply_prepared(plan, _ptr(x), _ptr(y), _ptr(ws), _nbytes(ws), _stream(stream)),
+           "heff_apply_prepared")
+
+
+def heff_apply(plan, L, W1, W2, R, x, y, ws, stream=None):
+    _check(_lib.heff_apply(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y), _ptr(ws),
+                           _nbytes(ws), _stream(stream)), "heff_apply")
+
+
+def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
+    n = len(xs)
+    xa = (_vp * n)(*[t.data_ptr() for t in xs])
+    ya = (_vp * n)(*[t.data_ptr() for t in ys])
+    _check(_lib.heff_apply_batched(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), xa, ya, n, _ptr(ws),
+                                   _nbytes(ws), _stream(stream)), "heff_apply_batched")
+
+
+def heff_plan_set_timing(plan, enable=True):
+    _check(_lib.heff_plan_set_timing(plan, 1 if enable else 0), "heff_plan_set_timing")
+
+
+def heff_plan_timings(plan):
+    """Milliseconds of (prepare, pack, GEMM 1, GEMM 2) of the last call."""
+    ms = (C.c_float * 4)()
+    _check(_lib.heff_plan_timings(plan, ms), "heff_plan_timings")
+    return [float(v) for v in ms]
+
+
+def heff_last_error():
+    return _lib.heff_last_error().decode()
+
+
+def heff_launch_count():
+    return int(_lib.heff_launch_count())
+
+
+def heff_version():
+    return _lib.heff_version().decode()
+
+
+# ------------------------------------------------------------------ owners
+class Layout:
+    """Owner of a heff_layout with the block list as numpy arrays."""
+
+    def __init__(self, indices, target=None):
+        self.indices = [(np.asarray(q, dtype=np.int32).reshape(len(d), -1),
+                         np.asarray(d, dtype=np.int32), int(f)) for q, d, f in indices]
+        self.handle = heff_qn_block_layout(self.indices, target)
+        self.nblocks, self.nelem, self.nidx = heff_layout_info(self.handle)
+        self.keys, self.offsets = heff_layout_blocks(self.handle)
+        dims = [d for _, d, _ in self.indices]
+        self.sizes = np.ones(self.nblocks, dtype=np.int64)
+        for k in range(self.nidx):
+            self.sizes *= dims[k][self.keys[:, k]]
+
+    def blocks(self):
+        """Iterate (key tuple, offset, size)."""
+        for b in range(self.nblocks):
+            yield tuple(int(v) for v in self.keys[b]), int(self.offsets[b]), int(self.sizes[b])
+
+    def assemble(self, fill, dtype=np.float64):
+        """Flat buffer with fill(key) (an array of the block's size) at each block."""
+        out = np.zeros(self.nelem, dtype=dtype)
+        for key, off, size in self.blocks():
+            v = np.asarray(fill(key), dtype=np.float64).reshape(-1)
+            if v.size != size:
+                raise ValueError(f"block {key}: got {v.size} values, layout wants {size}")
+            out[off:off + size] = v
+        return out
+
+    def split(self, flat):
+        """Dict key -> block view (1-D) of a flat buffer."""
+        return {key: flat[off:off + size] for key, off, size in self.blocks()}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            heff_layout_destroy(self.handle)
+            self.handle = None
+
+
+def heff_layouts(alpha, beta, phys, ql, qm, qr, target=None):
+    """Layouts of (L, W1, W2, R, x) for a two-site problem in the library's conventions.
+
+    alpha/beta: (charges, dims) of the left/right bond; phys: site charges [d, nq];
+    ql/qm/qr: MPO channel charges of the three MPO bonds.
+    """
+    aq, ad = alpha
+    bq, bd = beta
+    ph = np.asarray(phys, dtype=np.int32)
+    ones = lambda n: np.ones(n, dtype=np.int32)
+    A = lambda f: (aq, ad, f)
+    B = lambda f: (bq, bd, f)
+    S = lambda f: (ph, ones(len(ph)), f)
+    ch = lambda q, f: (np.asarray(q, dtype=np.int32), ones(len(q)), f)
+    Ll = Layout([A(-1), ch(ql, 1), A(1)])
+    W1l = Layout([ch(ql, 1), S(1), S(-1), ch(qm, -1)])
+    W2l = Layout([ch(qm, 1), S(1), S(-1), ch(qr, -1)])
+    Rl = Layout([B(-1), ch(qr, 1), B(1)])
+    xl = Layout([A(1), S(1), S(1), B(-1)], target)
+    return Ll, W1l, W2l, Rl, xl
+
+
+class Plan:
+    """Owner of a heff_plan built from the five layouts and host MPO values."""
+
+    def __init__(self, L, W1, W2, R, x, W1_host, W2_host, precision="bf16x3", io_dtype="f32",
+                 max_batch=1):
+        self.layouts = (L, W1, W2, R, x)
+        self.precision, self.io_dtype, self.max_batch = precision, io_dtype, max_batch
+        self.handle = heff_plan_create(L.handle, W1.handle, W2.handle, R.handle, x.handle,
+                                       W1_host, W2_host, precision, io_dtype, max_batch)
+        self.workspace_bytes = heff_plan_workspace_size(self.handle)
+        self.flops_canonical, self.flops_executed = heff_plan_flops(self.handle)
+        self.stats = heff_plan_stats(self.handle)
+
+    def workspace(self, device="cuda"):
+        import torch
+        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            heff_plan_destroy(self.handle)
+            self.handle = None
