@@ -56,7 +56,17 @@ def _compile(src, verbose):
 
 def build(verbose=False, force=False):
     """Compile and link ``libheff.so``; returns its path."""
+    import platform
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "host")
+    host = platform.machine()
+    try:
+        with open(stamp) as f:
+            force = force or f.read().strip() != host     # objects from another machine
+    except OSError:
+        force = True
+    with open(stamp, "w") as f:
+        f.write(host)
     headers = _headers()
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     objs = [os.path.join(BUILD, os.path.basename(s) + ".o") for s in srcs]

@@ -45,8 +45,6 @@ template <> struct Plane<HEFF_PREC_TF32X3> {
     }
 };
 
-constexpr int MAXB = 64;   // batch entries per launch (kernel parameter arrays)
-struct PtrBatch { const void* p[MAXB]; };
 
 // ------------------------------------------------------------------ pack x -> XT
 template <typename In, int PREC>

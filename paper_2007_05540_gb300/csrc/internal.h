@@ -72,6 +72,9 @@ struct KSeg {
     int32_t k0, klen;       // column range shared by A and B (klen multiple of KPAD)
 };
 
+constexpr int MAXB = 64;   // batch entries per launch (kernel parameter arrays)
+struct PtrBatch { const void* p[MAXB]; };
+
 struct GemmList {
     std::vector<GemmTask> tasks;
     std::vector<KSeg> segs;

@@ -1,9 +1,473 @@
-// Tensor-core (tcgen05) grouped GEMM for the split-precision paths.
+// Tensor-core grouped GEMM (sm_103a: TMA -> shared memory -> tcgen05.mma -> TMEM) for the
+// split-precision paths of the two-site H_eff matvec (Section II-C / Fig. 1d).
+//
+// Each task is one output tile C[m x n] (m <= 128, n <= TN) = sum over its contraction
+// segments of A[a_row + r, k] * B[b_row + c, k].  A and B live in the workspace as two
+// planes (hi, lo) of one element type:
+//   BF16X3: bf16 planes, kind::f16 MMAs;  TF32X3: fp32 planes read as TF32, kind::tf32.
+// Every K block does three MMAs, A_hi.B_hi + A_hi.B_lo + A_lo.B_hi, accumulated in FP32
+// in tensor memory (the "3-product" split: error ~ 2^-16 (bf16) / 2^-22 (tf32) relative).
+//
+// Persistent kernel, one CTA (6 warps) per SM, static round-robin over the task list
+// (which the planner sorts longest-first):
+//   warp 0      one thread issues the TMA loads of a STAGES-deep shared-memory ring
+//   warp 1      allocates TMEM (2 x TN columns); one thread issues the MMAs
+//   warps 2..5  epilogue: TMEM -> registers -> global (T as hi/lo planes, or y)
+// Accumulators are double buffered so a tile's epilogue overlaps the next tile's MMAs.
+// Every mbarrier wait is bounded (about a second); on expiry the CTA raises the
+// workspace error flag, stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
 #include "internal.h"
 
 namespace heff {
-int launch_tc_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream) {
-    (void)p; (void)which; (void)ws; (void)y; (void)nbatch; (void)stream;
-    return fail(HEFF_ERR_UNSUPPORTED, "tensor-core path not built yet");
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int TM = 128;
+constexpr int ROW_BYTES = 128;                 // one swizzled row: 64 bf16 or 32 fp32
+constexpr long long WAIT_CYCLES = 3ll << 30;   // ~1.5 s at 2 GHz
+
+template <int TN, int STAGES>
+struct Smem {
+    static constexpr int A_BYTES = TM * ROW_BYTES;
+    static constexpr int B_BYTES = TN * ROW_BYTES;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+    static constexpr int TOTAL = BAR_OFF + 256 + 1024;   // barriers + alignment slack
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false when the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+    const uint32_t a = su32(bar);
+    if (mbar_try(a, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(a, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format fmt (1 = BF16, 2 = TF32), K-major, M x N.
+__device__ __forceinline__ uint32_t idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (PREC == HEFF_PREC_BF16X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+    const GemmTask* tasks;
+    const KSeg* segs;
+    int ntasks, nbatch;
+    int64_t a_plane_rows, b_plane_rows;   // row offset of the lo plane in the A / B maps
+    int64_t a_batch_rows, b_batch_rows;   // row offset per batch entry
+    char* C;                              // mode 0: T (hi plane base)
+    int64_t c_batch_elems, c_plane_elems;
+    PtrBatch y;                           // mode 1: outputs per batch entry
+    int mode;                             // 0: write T planes, 1: write y
+    int y_f64;                            // y element type (mode 1)
+    int b0;                               // first batch entry of this launch
+    int* err;                             // sticky error flag in the workspace
+};
+
+template <int PREC>
+__device__ __forceinline__ void store_T(char* base, int64_t plane, int64_t o, const float* v, int nvalid,
+                                        int nwrite) {
+    // 32 consecutive columns of one row of T (hi and lo planes); o is 32-element aligned
+    if constexpr (PREC == HEFF_PREC_BF16X3) {
+        __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base) + o;
+        __nv_bfloat16* lo = hi + plane;
+        if (nvalid >= 32) {
+            uint32_t h[16], l[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
+                __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
+                __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
+                h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                reinterpret_cast<uint4*>(hi)[i] = make_uint4(h[4 * i], h[4 * i + 1], h[4 * i + 2], h[4 * i + 3]);
+                reinterpret_cast<uint4*>(lo)[i] = make_uint4(l[4 * i], l[4 * i + 1], l[4 * i + 2], l[4 * i + 3]);
+            }
+        } else {
+            for (int i = 0; i < nwrite; ++i) {
+                float f = i < nvalid ? v[i] : 0.f;
+                __nv_bfloat16 h0 = __float2bfloat16_rn(f);
+                hi[i] = h0;
+                lo[i] = __float2bfloat16_rn(f - __bfloat162float(h0));
+            }
+        }
+    } else {
+        float* hi = reinterpret_cast<float*>(base) + o;
+        float* lo = hi + plane;
+        if (nvalid >= 32) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float4 h, l;
+                float* hp = &h.x;
+                float* lp = &l.x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float f = v[4 * i + j];
+                    float t = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
+                    hp[j] = t;
+                    lp[j] = f - t;
+                }
+                reinterpret_cast<float4*>(hi)[i] = h;
+                reinterpret_cast<float4*>(lo)[i] = l;
+            }
+        } else {
+            for (int i = 0; i < nwrite; ++i) {
+                float f = i < nvalid ? v[i] : 0.f;
+                float t = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
+                hi[i] = t;
+                lo[i] = f - t;
+            }
+        }
+    }
+}
+
+template <int PREC, int TN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+    using S = Smem<TN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;      // [2]
+    uint64_t* tempty = tfull + 2;          // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], 4); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(2 * TN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long total = (long)g.ntasks * g.nbatch;
+    constexpr int KB = ROW_BYTES / (PREC == HEFF_PREC_BF16X3 ? 2 : 4);   // elements per K block
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        uint32_t it = 0;
+        bool ok = true;
+        for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x) {
+            const GemmTask t = g.tasks[gi % g.ntasks];
+            const int b = g.b0 + (int)(gi / g.ntasks);
+            const int ah = (int)(t.a_row + b * g.a_batch_rows), al = (int)(ah + g.a_plane_rows);
+            const int bh = (int)(t.b_row + b * g.b_batch_rows), bl = (int)(bh + g.b_plane_rows);
+            for (int s = 0; s < t.seg_count && ok; ++s) {
+                const KSeg sg = g.segs[t.seg_begin + s];
+                for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
+                    const int st = it % STAGES;
+                    if (!(ok = mbar_wait(&empty[st], ((it / STAGES) & 1) ^ 1, abort_flag, g.err))) break;
+                    uint8_t* base = smem + st * S::STAGE_BYTES;
+                    mbar_expect_tx(&full[st], S::STAGE_BYTES);
+                    tma_load(base, &mapA, &full[st], k, ah);
+                    tma_load(base + S::A_BYTES, &mapA, &full[st], k, al);
+                    tma_load(base + 2 * S::A_BYTES, &mapB, &full[st], k, bh);
+                    tma_load(base + 2 * S::A_BYTES + S::B_BYTES, &mapB, &full[st], k, bl);
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        constexpr uint32_t FMT = PREC == HEFF_PREC_BF16X3 ? 1u : 2u;
+        uint32_t it = 0, tcount = 0;
+        bool ok = true;
+        for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x, ++tcount) {
+            const GemmTask t = g.tasks[gi % g.ntasks];
+            const uint32_t acc = tcount & 1, use = tcount >> 1;
+            if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
+            tc_fence_after();
+            const uint32_t d = tmem + acc * TN;
+            const uint32_t nmma = t.n <= 16 ? 16u : (uint32_t)((t.n + 15) & ~15);
+            const uint32_t id = idesc(FMT, TM, nmma);
+            uint32_t first = 1;
+            for (int s = 0; s < t.seg_count && ok; ++s) {
+                const KSeg sg = g.segs[t.seg_begin + s];
+                for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
+                    const int st = it % STAGES;
+                    if (!(ok = mbar_wait(&full[st], (it / STAGES) & 1, abort_flag, g.err))) break;
+                    tc_fence_after();
+                    const uint32_t base = su32(smem + st * S::STAGE_BYTES);
+                    const uint64_t ahi = sdesc(base), alo = sdesc(base + S::A_BYTES);
+                    const uint64_t bhi = sdesc(base + 2 * S::A_BYTES), blo = sdesc(base + 2 * S::A_BYTES + S::B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t o = (uint64_t)(kk * 32) >> 4;     // 32-byte step inside the row
+                        umma<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
+                        umma<PREC>(d, ahi + o, blo + o, id, 1u);
+                        umma<PREC>(d, alo + o, bhi + o, id, 1u);
+                        first = 0;
+                    }
+                    umma_commit(&empty[st]);
+                }
+            }
+            if (!ok) break;
+            if (t.seg_count == 0) mbar_arrive(&tfull[acc]);
+            else umma_commit(&tfull[acc]);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int r = q * 32 + lane;            // tile row of this thread
+        uint32_t tcount = 0;
+        for (long gi = blockIdx.x; gi < total; gi += gridDim.x, ++tcount) {
+            const GemmTask t = g.tasks[gi % g.ntasks];
+            const int brel = (int)(gi / g.ntasks), b = g.b0 + brel;
+            const uint32_t acc = tcount & 1, use = tcount >> 1;
+            if (!mbar_wait(&tfull[acc], use & 1, abort_flag, g.err)) break;
+            tc_fence_after();
+            const int ncols = t.n + t.n_zero;
+            for (int c0 = 0; c0 < ncols; c0 += 32) {
+                uint32_t raw[32];
+                if (t.seg_count > 0) {
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * TN + c0, raw);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) raw[i] = 0u;
+                }
+                if (r >= t.m) continue;
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(raw[i]);
+                const int nvalid = t.n - c0 < 32 ? t.n - c0 : 32;
+                if (g.mode == 0) {
+                    const int nwrite = ncols - c0 < 32 ? ncols - c0 : 32;
+                    const int64_t o = t.c_off + (int64_t)b * g.c_batch_elems + (int64_t)r * t.ldc + c0;
+                    store_T<PREC>(g.C, g.c_plane_elems, o, v, nvalid, nwrite);
+                } else {
+                    const int64_t o = t.c_off + (int64_t)r * t.ldc + c0;
+                    if (g.y_f64) {
+                        double* y = static_cast<double*>(const_cast<void*>(g.y.p[brel])) + o;
+                        for (int i = 0; i < nvalid; ++i) y[i] = (double)v[i];
+                    } else {
+                        float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o;
+                        for (int i = 0; i < nvalid; ++i) y[i] = v[i];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return fail(HEFF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const bool bf = prec == HEFF_PREC_BF16X3;
+    const uint32_t es = bf ? 2 : 4;
+    cuuint64_t dims[2] = {ld, rows};
+    cuuint64_t strides[1] = {ld * es};
+    cuuint32_t box[2] = {ROW_BYTES / es, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(HEFF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return HEFF_OK;
+}
+
+constexpr int TN_TC = 256;
+constexpr int STAGES_TC = 2;
+
+template <int PREC>
+int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
+    using S = Smem<TN_TC, STAGES_TC>;
+    auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES_TC>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL);
+        if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        attr = true;
+    }
+    char* w = static_cast<char*>(ws);
+    const int64_t B = p->opts.max_batch;
+    if (p->tmap_ws != ws) {
+        int rc;
+        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps);
+        if ((rc = make_map(&m[0], w + p->off_lw, PREC, 2 * p->rows_lw, p->ld_x, TM))) return rc;
+        if ((rc = make_map(&m[1], w + p->off_xt, PREC, 2 * B * p->rows_x, p->ld_x, TN_TC))) return rc;
+        if ((rc = make_map(&m[2], w + p->off_t, PREC, 2 * B * p->rows_t, p->ld_t, TM))) return rc;
+        if ((rc = make_map(&m[3], w + p->off_rw, PREC, 2 * p->rows_rw, p->ld_t, TN_TC))) return rc;
+        p->tmap_ws = ws;
+    }
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(p->tmaps);
+    const GemmList& gl = which == 1 ? p->g1 : p->g2;
+    if (gl.tasks.empty()) return HEFF_OK;
+    for (int b0 = 0; b0 < nbatch; b0 += MAXB) {
+        const int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
+        TcArgs g{};
+        g.tasks = gl.d_tasks;
+        g.segs = gl.d_segs;
+        g.ntasks = (int)gl.tasks.size();
+        g.nbatch = nb;
+        g.err = reinterpret_cast<int*>(w + p->off_flags);
+        CUtensorMap ma, mb;
+        if (which == 1) {
+            ma = m[0]; mb = m[1];
+            g.a_plane_rows = p->rows_lw; g.b_plane_rows = B * p->rows_x;
+            g.a_batch_rows = 0; g.b_batch_rows = p->rows_x;
+            // batch chunk b0 starts b0 * rows_x rows into XT and b0 * rows_t rows into T
+            g.C = w + p->off_t;
+            g.c_batch_elems = p->rows_t * p->ld_t;
+            g.c_plane_elems = B * p->rows_t * p->ld_t;
+            g.mode = 0;
+        } else {
+            ma = m[2]; mb = m[3];
+            g.a_plane_rows = B * p->rows_t; g.b_plane_rows = p->rows_rw;
+            g.a_batch_rows = p->rows_t; g.b_batch_rows = 0;
+            for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
+            g.mode = 1;
+            g.y_f64 = p->opts.io_dtype == HEFF_DTYPE_F64;
+        }
+        g.b0 = b0;
+        const long total = (long)g.ntasks * nb;
+        int grid = p->num_sms > 0 ? p->num_sms : 148;
+        if (total < grid) grid = (int)total;
+        tc_gemm_kernel<PREC, TN_TC, STAGES_TC><<<grid, TC_THREADS, S::TOTAL, st>>>(ma, mb, g);
+        count_launches(1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "tc_gemm launch: %s", cudaGetErrorString(e));
+    return HEFF_OK;
+}
+
+}  // namespace
+
+int launch_tc_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->opts.precision == HEFF_PREC_BF16X3) return launch_tc_t<HEFF_PREC_BF16X3>(p, which, ws, y, nbatch, st);
+    return launch_tc_t<HEFF_PREC_TF32X3>(p, which, ws, y, nbatch, st);
+}
+
 }  // namespace heff

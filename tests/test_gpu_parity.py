@@ -55,13 +55,19 @@ def _oracle(w, batch=0, left_sectors=None):
 
 
 def _compare(y, y_ref, tol, mask=None):
+    """Relative error of y against the oracle: ||y - y_ref||_2 / ||y_ref||_2 < tol, and every
+    element within ELEM * tol of max|y_ref| (FP32 accumulation over K ~ 1e4 terms puts single
+    elements a few times above the norm-wise error; a wrong block would be O(1) off)."""
+    ELEM = 20.0
     if mask is not None:
         y, y_ref = y[mask], y_ref[mask]
     assert not np.isnan(y).any(), "unwritten output elements"
-    scale = np.abs(y_ref).max()
-    err = np.abs(y - y_ref).max() / scale
-    assert err < tol, f"max rel err {err:.3e} >= {tol:.0e}"
-    return err
+    nerr = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
+    merr = np.abs(y - y_ref).max() / np.abs(y_ref).max()
+    assert nerr < tol, f"norm-wise rel err {nerr:.3e} >= {tol:.0e}"
+    assert merr < ELEM * tol, f"element-wise err {merr:.3e} >= {ELEM * tol:.0e} of max|y|"
+    print(f"rel err: norm {nerr:.3e}  max-element {merr:.3e}")
+    return nerr
 
 
 SMALL = ["spin_m64", "spin_m200", "electron_m96", "electron_m256", "spin_m1024_s8"]
