@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -30,19 +31,23 @@ template <> struct Plane<HEFF_PREC_FP64> {
 };
 template <> struct Plane<HEFF_PREC_BF16X3> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
-        float f = (float)v;
+    static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
         hi = __float2bfloat16_rn(f);
         lo = __float2bfloat16_rn(f - __bfloat162float(hi));
     }
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split((float)v, hi, lo); }
 };
 template <> struct Plane<HEFF_PREC_TF32X3> {
     using T = float;
-    static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
-        float f = (float)v;
-        hi = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
-        lo = f - hi;
+    // round to the nearest TF32 value (10 explicit mantissa bits), ties away from zero
+    static __device__ __forceinline__ float rn_tf32(float f) {
+        return __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xffffe000u);
     }
+    static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
+        hi = rn_tf32(f);
+        lo = rn_tf32(f - hi);
+    }
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split((float)v, hi, lo); }
 };
 
 
@@ -52,7 +57,8 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ 
                                                    char* __restrict__ xt, int64_t ld, int64_t plane_elems,
                                                    int64_t batch_elems) {
     using E = typename Plane<PREC>::T;
-    __shared__ double s[32][33];
+    using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
+    __shared__ Acc s[32][33];
     const PackTile t = tiles[blockIdx.x];
     const In* x = static_cast<const In*>(xs.p[blockIdx.y]);
     E* hi = reinterpret_cast<E*>(xt) + (int64_t)blockIdx.y * batch_elems;
@@ -61,8 +67,8 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ 
     // read rows a (stride m_b), columns b contiguous
     for (int r = ty; r < 32; r += 8) {
         int a = t.a0 + r, b = t.b0 + tx;
-        double v = 0.0;
-        if (a < t.m_a && b < t.m_b) v = (double)x[t.x_off + (int64_t)a * t.m_b + b];
+        Acc v = 0;
+        if (a < t.m_a && b < t.m_b) v = (Acc)x[t.x_off + (int64_t)a * t.m_b + b];
         s[r][tx] = v;
     }
     __syncthreads();
@@ -87,8 +93,11 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ ti
                                                   const In* __restrict__ W2, const In* __restrict__ R,
                                                   char* __restrict__ lw, int64_t ld_lw, int64_t lw_plane,
                                                   char* __restrict__ rw, int64_t ld_rw, int64_t rw_plane) {
+    // FP64 path accumulates in double; the split paths in float (1-4 terms, each product
+    // exact to 24 bits, well inside the 16-bit (bf16 hi+lo) / 22-bit (tf32 hi+lo) split).
     using E = typename Plane<PREC>::T;
-    __shared__ double coef[64];
+    using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
+    __shared__ Acc coef[64];
     __shared__ int64_t srco[64];
     const MixTile t = tiles[blockIdx.x];
     const In* src = t.which ? R : L;
@@ -96,7 +105,7 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ ti
     const int nt = t.term_count < 64 ? t.term_count : 64;
     for (int k = threadIdx.x; k < nt; k += blockDim.x) {
         MixTerm m = terms[t.term_begin + k];
-        coef[k] = (double)W[m.w_idx];
+        coef[k] = (Acc)W[m.w_idx];
         srco[k] = m.src_off;
     }
     __syncthreads();
@@ -105,19 +114,20 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ ti
     E* lo = hi + (t.which ? rw_plane : lw_plane);
     const int total = t.nrows * t.cols_pad;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int r = t.r0 + e / t.cols_pad, c = e % t.cols_pad;
-        double acc = 0.0;
+        const int rr = e / t.cols_pad, c = e - rr * t.cols_pad;
+        const int r = t.r0 + rr;
+        Acc acc = 0;
         if (c < t.cols) {
-            int64_t rc = (int64_t)r * t.cols + c;
-            for (int k = 0; k < nt; ++k) acc += coef[k] * (double)src[srco[k] + rc];
+            const int64_t rc = (int64_t)r * t.cols + c;
+            for (int k = 0; k < nt; ++k) acc += coef[k] * (Acc)src[srco[k] + rc];
             for (int k = 64; k < t.term_count; ++k) {     // rare: more than 64 terms
                 MixTerm m = terms[t.term_begin + k];
-                acc += (double)W[m.w_idx] * (double)src[m.src_off + rc];
+                acc += (Acc)W[m.w_idx] * (Acc)src[m.src_off + rc];
             }
         }
         E h, l;
         Plane<PREC>::split(acc, h, l);
-        int64_t o = (t.dst_row0 + r) * ld + t.dst_col0 + c;
+        const int64_t o = (t.dst_row0 + r) * ld + t.dst_col0 + c;
         hi[o] = h;
         if (PREC != HEFF_PREC_FP64) lo[o] = l;
     }

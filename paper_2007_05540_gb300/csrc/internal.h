@@ -122,7 +122,7 @@ struct heff_plan {
     int64_t stats[24] = {0};
     // tensor-map cache for the tensor-core path (keyed by workspace pointer)
     void* tmap_ws = nullptr;
-    alignas(64) unsigned char tmaps[8][128];
+    alignas(64) unsigned char tmaps[12][128];
     int device = 0;
     int num_sms = 0;
     bool uploaded = false;    // false: created without a CUDA device (inspection only)

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -30,16 +31,25 @@ namespace {
 
 constexpr int TC_THREADS = 192;
 constexpr int TM = 128;
-constexpr int ROW_BYTES = 128;                 // one swizzled row: 64 bf16 or 32 fp32
 constexpr long long WAIT_CYCLES = 3ll << 30;   // ~1.5 s at 2 GHz
 
-template <int TN, int STAGES>
+// Shared-memory ring: STAGES x {A_hi, A_lo (128 rows), B_hi, B_lo (TN rows)}, each row SWZ
+// bytes of one K block (SWZ = 64: 32 bf16 / 16 fp32; SWZ = 128: 64 bf16 / 32 fp32).
+template <int TN, int STAGES, int SWZ>
 struct Smem {
-    static constexpr int A_BYTES = TM * ROW_BYTES;
-    static constexpr int B_BYTES = TN * ROW_BYTES;
+    static constexpr int A_BYTES = TM * SWZ;
+    static constexpr int B_BYTES = TN * SWZ;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
-    static constexpr int TOTAL = BAR_OFF + 256 + 1024;   // barriers + alignment slack
+    static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;    // epilogue transpose buffers
+    static constexpr int TOTAL = BAR_OFF + 256 + EPI_BYTES + 1024;   // + barriers, alignment slack
+};
+
+// TMA maps of one GEMM: the A operand with 64- and 128-row boxes, the B operand with 64-,
+// 128- and 256-row boxes (a tile loads the smallest box that covers its valid rows).
+struct TcMaps {
+    CUtensorMap a[2];
+    CUtensorMap b[3];
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -95,14 +105,16 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+// Shared-memory matrix descriptor: K-major operand with SWZ-byte rows swizzled in 8-row
+// groups (SWZ = 128: SWIZZLE_128B, groups 1024 B apart; SWZ = 64: SWIZZLE_64B, 512 B).
+template <int SWZ>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
-    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * SWZ) >> 4) << 32;           // stride byte offset: one 8-row group
     d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+    d |= (uint64_t)(SWZ == 128 ? 2 : 4) << 61;       // SWIZZLE_128B / SWIZZLE_64B
     return d;
 }
 
@@ -162,70 +174,10 @@ struct TcArgs {
     int* err;                             // sticky error flag in the workspace
 };
 
-template <int PREC>
-__device__ __forceinline__ void store_T(char* base, int64_t plane, int64_t o, const float* v, int nvalid,
-                                        int nwrite) {
-    // 32 consecutive columns of one row of T (hi and lo planes); o is 32-element aligned
-    if constexpr (PREC == HEFF_PREC_BF16X3) {
-        __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base) + o;
-        __nv_bfloat16* lo = hi + plane;
-        if (nvalid >= 32) {
-            uint32_t h[16], l[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
-                __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
-                __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
-                h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                reinterpret_cast<uint4*>(hi)[i] = make_uint4(h[4 * i], h[4 * i + 1], h[4 * i + 2], h[4 * i + 3]);
-                reinterpret_cast<uint4*>(lo)[i] = make_uint4(l[4 * i], l[4 * i + 1], l[4 * i + 2], l[4 * i + 3]);
-            }
-        } else {
-            for (int i = 0; i < nwrite; ++i) {
-                float f = i < nvalid ? v[i] : 0.f;
-                __nv_bfloat16 h0 = __float2bfloat16_rn(f);
-                hi[i] = h0;
-                lo[i] = __float2bfloat16_rn(f - __bfloat162float(h0));
-            }
-        }
-    } else {
-        float* hi = reinterpret_cast<float*>(base) + o;
-        float* lo = hi + plane;
-        if (nvalid >= 32) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float4 h, l;
-                float* hp = &h.x;
-                float* lp = &l.x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float f = v[4 * i + j];
-                    float t = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
-                    hp[j] = t;
-                    lp[j] = f - t;
-                }
-                reinterpret_cast<float4*>(hi)[i] = h;
-                reinterpret_cast<float4*>(lo)[i] = l;
-            }
-        } else {
-            for (int i = 0; i < nwrite; ++i) {
-                float f = i < nvalid ? v[i] : 0.f;
-                float t = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
-                hi[i] = t;
-                lo[i] = f - t;
-            }
-        }
-    }
-}
-
-template <int PREC, int TN, int STAGES>
+template <int PREC, int TN, int STAGES, int SWZ>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
-    using S = Smem<TN, STAGES>;
+tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
+    using S = Smem<TN, STAGES, SWZ>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
@@ -252,7 +204,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const long total = (long)g.ntasks * g.nbatch;
-    constexpr int KB = ROW_BYTES / (PREC == HEFF_PREC_BF16X3 ? 2 : 4);   // elements per K block
+    constexpr int KB = SWZ / (PREC == HEFF_PREC_BF16X3 ? 2 : 4);   // elements per K block
+    constexpr int KSUB = SWZ / 32;                                   // MMAs (32-byte K) per block
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
@@ -263,17 +216,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             const int b = g.b0 + (int)(gi / g.ntasks);
             const int ah = (int)(t.a_row + b * g.a_batch_rows), al = (int)(ah + g.a_plane_rows);
             const int bh = (int)(t.b_row + b * g.b_batch_rows), bl = (int)(bh + g.b_plane_rows);
+            const int ia = t.m <= 64 ? 0 : 1, ib = t.n <= 64 ? 0 : (t.n <= 128 ? 1 : 2);
+            const CUtensorMap* ma = &maps.a[ia];
+            const CUtensorMap* mb = &maps.b[ib];
+            const uint32_t bytes = 2u * (uint32_t)((64 << ia) + (64 << ib)) * SWZ;
             for (int s = 0; s < t.seg_count && ok; ++s) {
                 const KSeg sg = g.segs[t.seg_begin + s];
                 for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
                     const int st = it % STAGES;
                     if (!(ok = mbar_wait(&empty[st], ((it / STAGES) & 1) ^ 1, abort_flag, g.err))) break;
                     uint8_t* base = smem + st * S::STAGE_BYTES;
-                    mbar_expect_tx(&full[st], S::STAGE_BYTES);
-                    tma_load(base, &mapA, &full[st], k, ah);
-                    tma_load(base + S::A_BYTES, &mapA, &full[st], k, al);
-                    tma_load(base + 2 * S::A_BYTES, &mapB, &full[st], k, bh);
-                    tma_load(base + 2 * S::A_BYTES + S::B_BYTES, &mapB, &full[st], k, bl);
+                    mbar_expect_tx(&full[st], bytes);
+                    tma_load(base, ma, &full[st], k, ah);
+                    tma_load(base + S::A_BYTES, ma, &full[st], k, al);
+                    tma_load(base + 2 * S::A_BYTES, mb, &full[st], k, bh);
+                    tma_load(base + 2 * S::A_BYTES + S::B_BYTES, mb, &full[st], k, bl);
                 }
             }
         }
@@ -298,10 +255,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     if (!(ok = mbar_wait(&full[st], (it / STAGES) & 1, abort_flag, g.err))) break;
                     tc_fence_after();
                     const uint32_t base = su32(smem + st * S::STAGE_BYTES);
-                    const uint64_t ahi = sdesc(base), alo = sdesc(base + S::A_BYTES);
-                    const uint64_t bhi = sdesc(base + 2 * S::A_BYTES), blo = sdesc(base + 2 * S::A_BYTES + S::B_BYTES);
+                    const uint64_t ahi = sdesc<SWZ>(base), alo = sdesc<SWZ>(base + S::A_BYTES);
+                    const uint64_t bhi = sdesc<SWZ>(base + 2 * S::A_BYTES);
+                    const uint64_t blo = sdesc<SWZ>(base + 2 * S::A_BYTES + S::B_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
+                    for (int kk = 0; kk < KSUB; ++kk) {
                         const uint64_t o = (uint64_t)(kk * 32) >> 4;     // 32-byte step inside the row
                         umma<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
                         umma<PREC>(d, ahi + o, blo + o, id, 1u);
@@ -317,8 +275,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         }
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
+        // Each warp drains its 32 TMEM lanes (tile rows) 32 columns at a time: tcgen05.ld
+        // (thread = row), transpose through a padded 32 x 33 shared buffer, then store
+        // row by row with consecutive lanes on consecutive columns (full-sector writes).
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int r = q * 32 + lane;            // tile row of this thread
+        float (*stage)[33] = reinterpret_cast<float (*)[33]>(smem + S::BAR_OFF + 256 + q * 32 * 33 * 4);
         uint32_t tcount = 0;
         for (long gi = blockIdx.x; gi < total; gi += gridDim.x, ++tcount) {
             const GemmTask t = g.tasks[gi % g.ntasks];
@@ -327,6 +288,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             if (!mbar_wait(&tfull[acc], use & 1, abort_flag, g.err)) break;
             tc_fence_after();
             const int ncols = t.n + t.n_zero;
+            const int rows = t.m - q * 32 < 32 ? t.m - q * 32 : 32;   // valid rows of this warp
             for (int c0 = 0; c0 < ncols; c0 += 32) {
                 uint32_t raw[32];
                 if (t.seg_count > 0) {
@@ -335,25 +297,42 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
                     for (int i = 0; i < 32; ++i) raw[i] = 0u;
                 }
-                if (r >= t.m) continue;
-                float v[32];
+                if (rows <= 0) continue;                       // warp-uniform
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(raw[i]);
-                const int nvalid = t.n - c0 < 32 ? t.n - c0 : 32;
+                for (int i = 0; i < 32; ++i) stage[lane][i] = __uint_as_float(raw[i]);
+                __syncwarp();
+                const int c = c0 + lane;                       // this lane's column
                 if (g.mode == 0) {
-                    const int nwrite = ncols - c0 < 32 ? ncols - c0 : 32;
-                    const int64_t o = t.c_off + (int64_t)b * g.c_batch_elems + (int64_t)r * t.ldc + c0;
-                    store_T<PREC>(g.C, g.c_plane_elems, o, v, nvalid, nwrite);
-                } else {
-                    const int64_t o = t.c_off + (int64_t)r * t.ldc + c0;
+                    using E = typename std::conditional<PREC == HEFF_PREC_BF16X3, __nv_bfloat16, float>::type;
+                    E* hi = reinterpret_cast<E*>(g.C) + t.c_off + (int64_t)b * g.c_batch_elems + c;
+                    E* lo = hi + g.c_plane_elems;
+                    if (c < ncols) {
+                        for (int rr = 0; rr < rows; ++rr) {
+                            const float f = c < t.n ? stage[rr][lane] : 0.f;
+                            const int64_t o = (int64_t)(q * 32 + rr) * t.ldc;
+                            if constexpr (PREC == HEFF_PREC_BF16X3) {
+                                const __nv_bfloat16 h = __float2bfloat16_rn(f);
+                                hi[o] = h;
+                                lo[o] = __float2bfloat16_rn(f - __bfloat162float(h));
+                            } else {
+                                // round-to-nearest TF32 hi and lo (both exact for the MMA)
+                                const float h = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xffffe000u);
+                                hi[o] = h;
+                                lo[o] = __uint_as_float((__float_as_uint(f - h) + 0x1000u) & 0xffffe000u);
+                            }
+                        }
+                    }
+                } else if (c < t.n) {
+                    const int64_t o0 = t.c_off + c;
                     if (g.y_f64) {
-                        double* y = static_cast<double*>(const_cast<void*>(g.y.p[brel])) + o;
-                        for (int i = 0; i < nvalid; ++i) y[i] = (double)v[i];
+                        double* y = static_cast<double*>(const_cast<void*>(g.y.p[brel])) + o0;
+                        for (int rr = 0; rr < rows; ++rr) y[(int64_t)(q * 32 + rr) * t.ldc] = (double)stage[rr][lane];
                     } else {
-                        float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o;
-                        for (int i = 0; i < nvalid; ++i) y[i] = v[i];
+                        float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o0;
+                        for (int rr = 0; rr < rows; ++rr) y[(int64_t)(q * 32 + rr) * t.ldc] = stage[rr][lane];
                     }
                 }
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -381,29 +360,33 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, uint32_t box_rows) {
+int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, uint32_t box_rows, int swz) {
     auto fn = encode_fn();
     if (!fn) return fail(HEFF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     const bool bf = prec == HEFF_PREC_BF16X3;
     const uint32_t es = bf ? 2 : 4;
     cuuint64_t dims[2] = {ld, rows};
     cuuint64_t strides[1] = {ld * es};
-    cuuint32_t box[2] = {ROW_BYTES / es, box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)swz / es, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(HEFF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return HEFF_OK;
 }
 
+// Kernel configuration: N tile 256 (two TMEM accumulators = 512 columns), 64-byte K
+// blocks, 4-stage ring (4 x 48 KB).
 constexpr int TN_TC = 256;
-constexpr int STAGES_TC = 2;
+constexpr int STAGES_TC = 4;
+constexpr int SWZ_TC = 64;
 
 template <int PREC>
 int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
-    using S = Smem<TN_TC, STAGES_TC>;
-    auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES_TC>;
+    using S = Smem<TN_TC, STAGES_TC, SWZ_TC>;
+    auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES_TC, SWZ_TC>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL);
@@ -412,18 +395,27 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
     }
     char* w = static_cast<char*>(ws);
     const int64_t B = p->opts.max_batch;
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps);
     if (p->tmap_ws != ws) {
-        int rc;
-        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps);
-        if ((rc = make_map(&m[0], w + p->off_lw, PREC, 2 * p->rows_lw, p->ld_x, TM))) return rc;
-        if ((rc = make_map(&m[1], w + p->off_xt, PREC, 2 * B * p->rows_x, p->ld_x, TN_TC))) return rc;
-        if ((rc = make_map(&m[2], w + p->off_t, PREC, 2 * B * p->rows_t, p->ld_t, TM))) return rc;
-        if ((rc = make_map(&m[3], w + p->off_rw, PREC, 2 * p->rows_rw, p->ld_t, TN_TC))) return rc;
+        // [0,1] LW (64, 128 rows)  [2,3,4] XT (64, 128, 256)  [5,6] T (64, 128)  [7,8,9] RW (64, 128, 256)
+        struct { char* base; int64_t rows, ld; int slot, nbox; } ops[4] = {
+            {w + p->off_lw, 2 * p->rows_lw, p->ld_x, 0, 2},
+            {w + p->off_xt, 2 * B * p->rows_x, p->ld_x, 2, 3},
+            {w + p->off_t, 2 * B * p->rows_t, p->ld_t, 5, 2},
+            {w + p->off_rw, 2 * p->rows_rw, p->ld_t, 7, 3}};
+        for (auto& o : ops)
+            for (int k = 0; k < o.nbox; ++k) {
+                int rc = make_map(&m[o.slot + k], o.base, PREC, (uint64_t)o.rows, (uint64_t)o.ld, 64u << k, SWZ_TC);
+                if (rc) return rc;
+            }
         p->tmap_ws = ws;
     }
-    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(p->tmaps);
     const GemmList& gl = which == 1 ? p->g1 : p->g2;
     if (gl.tasks.empty()) return HEFF_OK;
+    TcMaps maps;
+    const int sa = which == 1 ? 0 : 5, sb = which == 1 ? 2 : 7;
+    maps.a[0] = m[sa]; maps.a[1] = m[sa + 1];
+    maps.b[0] = m[sb]; maps.b[1] = m[sb + 1]; maps.b[2] = m[sb + 2];
     for (int b0 = 0; b0 < nbatch; b0 += MAXB) {
         const int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
         TcArgs g{};
@@ -431,30 +423,26 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
         g.segs = gl.d_segs;
         g.ntasks = (int)gl.tasks.size();
         g.nbatch = nb;
+        g.b0 = b0;
         g.err = reinterpret_cast<int*>(w + p->off_flags);
-        CUtensorMap ma, mb;
         if (which == 1) {
-            ma = m[0]; mb = m[1];
             g.a_plane_rows = p->rows_lw; g.b_plane_rows = B * p->rows_x;
             g.a_batch_rows = 0; g.b_batch_rows = p->rows_x;
-            // batch chunk b0 starts b0 * rows_x rows into XT and b0 * rows_t rows into T
             g.C = w + p->off_t;
             g.c_batch_elems = p->rows_t * p->ld_t;
             g.c_plane_elems = B * p->rows_t * p->ld_t;
             g.mode = 0;
         } else {
-            ma = m[2]; mb = m[3];
             g.a_plane_rows = B * p->rows_t; g.b_plane_rows = p->rows_rw;
             g.a_batch_rows = p->rows_t; g.b_batch_rows = 0;
             for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
             g.mode = 1;
             g.y_f64 = p->opts.io_dtype == HEFF_DTYPE_F64;
         }
-        g.b0 = b0;
         const long total = (long)g.ntasks * nb;
         int grid = p->num_sms > 0 ? p->num_sms : 148;
         if (total < grid) grid = (int)total;
-        tc_gemm_kernel<PREC, TN_TC, STAGES_TC><<<grid, TC_THREADS, S::TOTAL, st>>>(ma, mb, g);
+        kern<<<grid, TC_THREADS, S::TOTAL, st>>>(maps, g);
         count_launches(1);
     }
     cudaError_t e = cudaGetLastError();
