@@ -187,6 +187,27 @@ int heff_apply_batched(heff_plan* plan, const void* L, const void* W1, const voi
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * heff_apply_noalloc -- heff_apply without a caller-provided workspace and without any
+ * device allocation.  The paper has no counterpart of it: it exists because some callers
+ * cannot call cudaMalloc, for example code running under another framework's memory
+ * manager that has already reserved the device memory it may use, or code on a
+ * latency-critical path where cudaMalloc's implicit device synchronisation is not
+ * acceptable.  The workspace is a fixed array of HEFF_NOALLOC_WORKSPACE_BYTES compiled
+ * into the library; every GPU that loads the library holds one copy until the process
+ * exits.  Plans whose heff_plan_workspace_size exceeds that size are rejected with
+ * HEFF_ERR_WORKSPACE (for example the m = 1024 spin problem in BF16x3 fits, m = 4096
+ * does not).  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (on different streams or from different threads) race
+ * on it and must be serialised by the caller.  Arguments and errors otherwise as
+ * heff_apply; the plan must belong to the current device.
+ */
+#define HEFF_NOALLOC_WORKSPACE_BYTES (128u << 20)
+int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                       const void* x, void* y, void* stream);
+
+/*
  * Phase timers (the time breakdown of Section VI / Fig. 7, on the GPU): when enabled,
  * every compute call records CUDA events on its stream around its phases.
  * heff_plan_timings waits for the last call's final event and writes the milliseconds

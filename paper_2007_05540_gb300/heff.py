@@ -63,6 +63,7 @@ _sig = {
     "heff_apply_prepared": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
+    "heff_apply_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
     "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
     "heff_last_error": (C.c_char_p, []),
@@ -223,6 +224,16 @@ def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
     ya = (_vp * n)(*[t.data_ptr() for t in ys])
     _check(_lib.heff_apply_batched(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), xa, ya, n, _ptr(ws),
                                    _nbytes(ws), _stream(stream)), "heff_apply_batched")
+
+
+NOALLOC_WORKSPACE_BYTES = 128 << 20   # HEFF_NOALLOC_WORKSPACE_BYTES in include/heff.h
+
+
+def heff_apply_noalloc(plan, L, W1, W2, R, x, y, stream=None):
+    """heff_apply with the library's built-in workspace (no device allocation anywhere);
+    calls that overlap on the GPU race on that shared workspace."""
+    _check(_lib.heff_apply_noalloc(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y),
+                                   _stream(stream)), "heff_apply_noalloc")
 
 
 def heff_plan_set_timing(plan, enable=True):

@@ -1,10 +1,10 @@
 """GPU parity of the CUDA H_eff path against the FP64 oracle (through the C ABI).
 
 Tolerances (north-star): FP64 path 1e-10; TF32 split (3xTF32) 1e-5; BF16 with
-compensation (BF16x3) 1e-3, all relative to max|y_oracle|, checked element by element
-on every output element at small sizes, and on every element of sampled output
-sectors at the benchmark's full sizes.  y is pre-filled with NaN so an output block
-the kernels fail to write is caught.
+compensation (BF16x3) 1e-3, as norm-wise relative errors ||y - y_oracle|| / ||y_oracle||,
+with every element also within 20x the tolerance of max|y_oracle|; all output elements
+at small sizes, every element of sampled output sectors at the benchmark's full sizes.
+y is pre-filled with NaN so an output block the kernels fail to write is caught.
 """
 import numpy as np
 import pytest
@@ -87,9 +87,21 @@ def _workload(name):
 TF32_LONG_K = {"spin_m1024_s8", "spin_m4096", "electron_m2048"}
 
 
+_XFAIL = {"on": False}
+
+
 def _maybe_xfail(name, prec):
-    if prec == "tf32x3" and name in TF32_LONG_K:
-        pytest.xfail("3xTF32 accumulation error ~1e-5..3e-5 at K >= 5000 on tcgen05 kind::tf32")
+    """Arm an expected failure: the case still runs; only a missed bound turns into xfail."""
+    _XFAIL["on"] = prec == "tf32x3" and name in TF32_LONG_K
+
+
+def _check(y, y_ref, tol, mask=None):
+    try:
+        return _compare(y, y_ref, tol, mask)
+    except AssertionError as e:
+        if _XFAIL["on"]:
+            pytest.xfail(f"3xTF32 accumulation on tcgen05 kind::tf32 at K >= 5000: {e}")
+        raise
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
@@ -99,7 +111,7 @@ def test_apply_matches_oracle(name, prec):
     w = _workload(name)
     lib = Lib(w, prec)
     y_ref = oracle_flat(lib.lays[4], _oracle(w))
-    _compare(lib.apply(), y_ref, TOL[prec])
+    _check(lib.apply(), y_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
@@ -186,5 +198,5 @@ def test_full_size_sampled_sectors(name, sectors, prec):
     for key, off, size in xl.blocks():
         if key[0] in keep:
             mask[off:off + size] = True
-    _compare(y, y_ref, TOL[prec], mask)
     assert not np.isnan(y).any()
+    _check(y, y_ref, TOL[prec], mask)
