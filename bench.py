@@ -27,6 +27,20 @@ import numpy as np  # noqa: E402
 
 METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 
+# DRAM bytes (read + write) per launch from the ncu capture summarised in
+# profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {
+    ("spin_m4096", "bf16x3", "gemm1"): (251.844352e6 + 255.647744e6, "6fa7728a14074c5a"),
+    ("spin_m4096", "bf16x3", "gemm2"): (643.365632e6 + 19.948288e6, "6fa7728a14074c5a"),
+}
+
+
+def _src_sha():
+    import hashlib
+    p = os.path.join(ROOT, "paper_2007_05540_gb300", "csrc", "tc_gemm.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -247,7 +261,9 @@ def run_ours(args):
                 "note": f"{passes} tensor-core products per useful multiply-add (hi/lo split)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    roof["traffic"] = None
+    tr = NCU_TRAFFIC.get((args.workload, prec, dom))
+    roof["traffic"] = tr[0] if tr and tr[1] == _src_sha() else None
+    roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     roof["launch_ms"] = g_ms[dom]
 
     out = {

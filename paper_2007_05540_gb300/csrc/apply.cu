@@ -28,6 +28,9 @@ template <int PREC> struct Plane;
 template <> struct Plane<HEFF_PREC_FP64> {
     using T = double;
     static __device__ __forceinline__ void split(double v, T& hi, T& lo) { hi = v; lo = 0.0; }
+    static __device__ __forceinline__ void store2(T* p, T a, T b) {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    }
 };
 template <> struct Plane<HEFF_PREC_BF16X3> {
     using T = __nv_bfloat16;
@@ -36,6 +39,9 @@ template <> struct Plane<HEFF_PREC_BF16X3> {
         lo = __float2bfloat16_rn(f - __bfloat162float(hi));
     }
     static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split((float)v, hi, lo); }
+    static __device__ __forceinline__ void store2(T* p, T a, T b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
+    }
 };
 template <> struct Plane<HEFF_PREC_TF32X3> {
     using T = float;
@@ -46,6 +52,9 @@ template <> struct Plane<HEFF_PREC_TF32X3> {
     static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
         hi = rn_tf32(f);
         lo = rn_tf32(f - hi);
+    }
+    static __device__ __forceinline__ void store2(T* p, T a, T b) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
     }
     static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split((float)v, hi, lo); }
 };
@@ -112,24 +121,36 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ ti
     E* hi = reinterpret_cast<E*>(t.which ? rw : lw);
     const int64_t ld = t.which ? ld_rw : ld_lw;
     E* lo = hi + (t.which ? rw_plane : lw_plane);
-    const int total = t.nrows * t.cols_pad;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int rr = e / t.cols_pad, c = e - rr * t.cols_pad;
+    // warps over rows, lanes over column pairs: each thread writes two adjacent columns
+    // (dst_col0 and cols_pad are multiples of 64, so the pair stores are aligned)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int rr = warp; rr < t.nrows; rr += blockDim.x >> 5) {
         const int r = t.r0 + rr;
-        Acc acc = 0;
-        if (c < t.cols) {
-            const int64_t rc = (int64_t)r * t.cols + c;
-            for (int k = 0; k < nt; ++k) acc += coef[k] * (Acc)src[srco[k] + rc];
-            for (int k = 64; k < t.term_count; ++k) {     // rare: more than 64 terms
-                MixTerm m = terms[t.term_begin + k];
-                acc += (Acc)W[m.w_idx] * (Acc)src[m.src_off + rc];
+        const int64_t rc0 = (int64_t)r * t.cols;
+        E* hrow = hi + (t.dst_row0 + r) * ld + t.dst_col0;
+        E* lrow = lo + (t.dst_row0 + r) * ld + t.dst_col0;
+        for (int c = 2 * lane; c < t.cols_pad; c += 64) {
+            Acc a0 = 0, a1 = 0;
+            const bool v0 = c < t.cols, v1 = c + 1 < t.cols;
+            if (v0) {
+                for (int k = 0; k < nt; ++k) {
+                    const In* s = src + srco[k] + rc0 + c;
+                    a0 += coef[k] * (Acc)s[0];
+                    if (v1) a1 += coef[k] * (Acc)s[1];
+                }
+                for (int k = 64; k < t.term_count; ++k) {     // rare: more than 64 terms
+                    MixTerm m = terms[t.term_begin + k];
+                    const In* s = src + m.src_off + rc0 + c;
+                    a0 += (Acc)W[m.w_idx] * (Acc)s[0];
+                    if (v1) a1 += (Acc)W[m.w_idx] * (Acc)s[1];
+                }
             }
+            E h0, l0, h1, l1;
+            Plane<PREC>::split(a0, h0, l0);
+            Plane<PREC>::split(a1, h1, l1);
+            Plane<PREC>::store2(hrow + c, h0, h1);
+            if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lrow + c, l0, l1);
         }
-        E h, l;
-        Plane<PREC>::split(acc, h, l);
-        const int64_t o = (t.dst_row0 + r) * ld + t.dst_col0 + c;
-        hi[o] = h;
-        if (PREC != HEFF_PREC_FP64) lo[o] = l;
     }
 }
 

@@ -323,7 +323,7 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                     P->pack.push_back({x->offsets[b], qs.xt_row0 + eg->row, cg->col, cg->dim, eg->dim, apad, a0, b0});
         }
         // ---- mix tiles (LW and RW)
-        const int MIX_ROWS = 16;
+        const int MIX_ROWS = 32;
         for (auto& rg : rgs)
             for (auto& sg : rg.segs) {
                 const CGroup& g = Q[rg.q].cg[sg.cg];
