@@ -187,6 +187,28 @@ int heff_apply_batched(heff_plan* plan, const void* L, const void* W1, const voi
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * heff_lanczos -- lowest eigenpair of H_eff by n_iter Lanczos steps (the eigensolver of
+ * the two-site DMRG step, Section II-C and III; the fixed-iteration alternative to the
+ * Davidson routine of Algorithm 1), all in FP64 on the device except the matvecs, which
+ * run in the plan's precision.  Full reorthogonalisation by two classical Gram-Schmidt
+ * passes per step; the tridiagonal eigenproblem is solved on the device (bisection on the
+ * Sturm count + inverse iteration).  The plan must use HEFF_DTYPE_F64 tensors.
+ *   x0      device, nelem(x) doubles: start vector (need not be normalised, must be nonzero)
+ *   x_out   device, nelem(x) doubles: normalised Ritz vector of the lowest Ritz value
+ *   result  device, 3 + 2 * (n_iter + 1) doubles: [0] lowest Ritz value theta,
+ *           [1] Lanczos residual estimate |beta_last * s_last|, [2] Krylov dimension used,
+ *           then alpha[n_iter + 1], beta[n_iter + 1]
+ *   apply_ws  the plan's workspace (heff_plan_workspace_size), overwritten
+ *   lz_ws     >= heff_lanczos_workspace_size bytes, 256-byte aligned, overwritten
+ * n_iter 1..126.  If the Krylov space becomes invariant (beta < 1e-13 |alpha|) the
+ * remaining steps are skipped on the device.  Asynchronous; never synchronises.
+ */
+int heff_lanczos_workspace_size(const heff_plan* plan, int32_t n_iter, size_t* bytes);
+int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                 const double* x0, int32_t n_iter, double* x_out, double* result, void* apply_ws,
+                 size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes, void* stream);
+
+/*
  * heff_apply_noalloc -- heff_apply without a caller-provided workspace and without any
  * device allocation.  The paper has no counterpart of it: it exists because some callers
  * cannot call cudaMalloc, for example code running under another framework's memory

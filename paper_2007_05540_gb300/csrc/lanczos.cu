@@ -1,0 +1,357 @@
+// FP64 Lanczos eigensolver on the GPU around the H_eff matvec (the eigensolver of the
+// two-site DMRG step, Section II-C / III; Lanczos is the fixed-iteration alternative to
+// the Davidson routine of Algorithm 1).
+//
+// Every vector operation runs in FP64 on the device and the loop never synchronises with
+// the host.  Per iteration k:
+//   w = H v_k                       (heff_apply_prepared; any precision, FP64 vectors)
+//   h = V^T w, w -= V h   (twice)   (classical Gram-Schmidt with re-orthogonalisation,
+//                                    "CGS2": full reorthogonalisation against v_0..v_k;
+//                                    alpha_k = h_k + h2_k)
+//   beta_k = ||w||, v_{k+1} = w / beta_k
+// then the lowest eigenpair of the (n x n) tridiagonal matrix is found on the device
+// (bisection + inverse iteration), and the Ritz vector x = sum_j s_j v_j is formed and
+// normalised.  If beta_k falls below 1e-13 |alpha_k| the Krylov space is invariant: the
+// remaining iterations become no-ops and the eigenproblem uses the k + 1 vectors built.
+// Reductions are two-stage with a fixed order, so results are deterministic.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+using heff::fail;
+
+namespace heff {
+namespace {
+
+constexpr int RT = 256;          // threads per reduction block
+constexpr int RB = 512;          // reduction blocks (partial sums per vector)
+constexpr int VT = 8;            // vectors per multi-dot pass
+
+// State in the Lanczos workspace (doubles): [0] n_eff (as double), [1] active flag,
+// [2] theta, [3] residual estimate, [8..8+NMAX) alpha, [8+NMAX..) beta,
+// then h (NMAX), s (NMAX), partials (RB * VT).
+struct LzLayout {
+    int nmax;
+    int64_t n;
+    size_t off_state, off_h, off_s, off_part, off_T, off_V, bytes;
+};
+
+LzLayout lz_layout(int64_t n, int n_iter) {
+    LzLayout l{};
+    l.nmax = n_iter + 1;
+    l.n = n;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    size_t o = 0;
+    l.off_state = o; o = al(o + sizeof(double) * (8 + 2 * (size_t)l.nmax));
+    l.off_h = o;     o = al(o + sizeof(double) * (size_t)l.nmax);
+    l.off_s = o;     o = al(o + sizeof(double) * (size_t)l.nmax);
+    l.off_part = o;  o = al(o + sizeof(double) * (size_t)RB * VT);
+    l.off_T = o;     o = al(o + sizeof(double) * 2 * (size_t)l.nmax * l.nmax);
+    l.off_V = o;     o = al(o + sizeof(double) * (size_t)(l.nmax + 1) * (size_t)n);   // V + w
+    l.bytes = o;
+    return l;
+}
+
+struct Lz {
+    double* state;   // n_eff, active, theta, resid, alpha[nmax], beta[nmax]
+    double* h;
+    double* s;
+    double* part;
+    double* T;       // nmax x nmax matrix + nmax x nmax eigenvectors
+    double* V;       // (nmax) basis vectors, then w
+    int64_t n;
+    int nmax;
+    double* alpha() const { return state + 8; }
+    double* beta() const { return state + 8 + nmax; }
+    double* w() const { return V + (int64_t)nmax * n; }
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;
+}
+
+// partial[b * VT + t] = sum over block b's chunk of V[j0 + t] . w, t < nv
+__global__ void __launch_bounds__(RT) multidot_kernel(const double* __restrict__ V, const double* __restrict__ w,
+                                                      int64_t n, int j0, int nv, double* __restrict__ part,
+                                                      const double* __restrict__ state) {
+    __shared__ double sh[RT / 32];
+    if (state[1] == 0.0) return;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t beg = (int64_t)blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+    double acc[VT];
+#pragma unroll
+    for (int t = 0; t < VT; ++t) acc[t] = 0.0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += RT) {
+        const double wi = w[i];
+#pragma unroll
+        for (int t = 0; t < VT; ++t)
+            if (t < nv) acc[t] = fma(V[(int64_t)(j0 + t) * n + i], wi, acc[t]);
+    }
+    for (int t = 0; t < nv; ++t) {
+        double s = block_sum(acc[t], sh);
+        if (threadIdx.x == 0) part[blockIdx.x * VT + t] = s;
+    }
+}
+
+// out[j0 + t] = (accumulate ? out : 0) + sum_b partial[b * VT + t]
+__global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int j0, int nv, double* out,
+                                   int accumulate, const double* __restrict__ state) {
+    __shared__ double sh[RT / 32];
+    if (state[1] == 0.0) return;
+    for (int t = 0; t < nv; ++t) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT + t];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) out[j0 + t] = accumulate ? out[j0 + t] + v : v;
+    }
+}
+
+// y[i] = (beta_y * y[i]) + sign * sum_{j < nv} c[j] V[j][i]   (c from device memory)
+__global__ void __launch_bounds__(RT) combine_kernel(const double* __restrict__ V, int64_t n, int nv,
+                                                     const double* __restrict__ c, double sign, double beta_y,
+                                                     double* __restrict__ y, const double* __restrict__ state,
+                                                     int ignore_active) {
+    __shared__ double cs[128];
+    if (!ignore_active && state[1] == 0.0) return;
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = c[j];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        double a = 0.0;
+        for (int j = 0; j < nv; ++j) a = fma(cs[j], V[(int64_t)j * n + i], a);
+        y[i] = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a;
+    }
+}
+
+// sum of squares of x into part (stage 1)
+__global__ void __launch_bounds__(RT) sumsq_kernel(const double* __restrict__ x, int64_t n, double* part) {
+    __shared__ double sh[RT / 32];
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT)
+        a = fma(x[i], x[i], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * VT] = a;
+}
+
+// dst = src / sqrt(sum part); mode 0: initial vector (sets active); mode 1: Lanczos step k
+__global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict__ part, int nb,
+                                                       const double* __restrict__ src, double* __restrict__ dst,
+                                                       int64_t n, double* state, int mode, int k, int nmax) {
+    __shared__ double sh[RT / 32];
+    __shared__ double nrm;
+    if (mode == 1 && state[1] == 0.0) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) nrm = sqrt(v);
+    __syncthreads();
+    const double r = nrm;
+    if (mode == 1) {
+        // alpha_k was accumulated in h[k]; beta_k = ||w||
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const double a = state[8 + k];
+            state[8 + nmax + k] = r;
+            state[0] = (double)(k + 1);
+            if (!(r > 1e-13 * fabs(a)) || !(r > 1e-300)) state[1] = 0.0;    // invariant subspace
+        }
+        if (!(r > 1e-13 * fabs(state[8 + k])) || !(r > 1e-300)) return;
+    } else if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        state[0] = 0.0;
+        state[1] = r > 0.0 ? 1.0 : 0.0;
+    }
+    if (!(r > 0.0)) return;
+    const double inv = 1.0 / r;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) dst[i] = src[i] * inv;
+}
+
+// alpha_k = h1[k] + h2[k], the projections of H v_k on v_k of both Gram-Schmidt passes
+__global__ void set_alpha_kernel(double* state, const double* h1, const double* h2, int k) {
+    if (state[1] == 0.0) return;
+    state[8 + k] = h1[k] + h2[k];
+}
+
+// Lowest eigenpair of the n_eff x n_eff tridiagonal matrix T (diagonal alpha, off-diagonal
+// beta), in FP64 on one thread: the eigenvalue by bisection on the Sturm count (the number
+// of negative pivots of the LDL^T factorisation of T - x I equals the number of
+// eigenvalues below x), the eigenvector by inverse iteration with the tridiagonal system
+// solved by Gaussian elimination with partial pivoting.  Writes theta to state[2],
+// |beta_{n-1} s_{n-1}| (the Lanczos residual norm of the Ritz pair) to state[3], the
+// eigenvector to s; T holds 4 * nmax doubles of scratch.
+__global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int n = (int)state[0];
+    for (int i = 0; i < nmax; ++i) s[i] = 0.0;
+    if (n <= 0) return;
+    const double* al = state + 8;
+    const double* be = state + 8 + nmax;
+    double lo = al[0], hi = al[0];
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < n ? fabs(be[i]) : 0.0);
+        lo = fmin(lo, al[i] - r);
+        hi = fmax(hi, al[i] + r);
+    }
+    const double scale = fmax(fabs(lo), fabs(hi)) + 1e-300;
+    auto count_below = [&](double x) {
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < n; ++i) {
+            const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+            d = (al[i] - x) - (i > 0 ? b2 / d : 0.0);
+            if (d == 0.0) d = -1e-300 * scale;
+            if (d < 0.0) ++c;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200 && hi - lo > 4e-16 * scale; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_below(mid) >= 1) hi = mid; else lo = mid;
+    }
+    const double theta = 0.5 * (lo + hi);
+    // inverse iteration: (T - theta I) z_new = z, banded LU with partial pivoting
+    double* dl = T;              // sub-diagonal / multipliers
+    double* dd = T + nmax;       // diagonal
+    double* du = T + 2 * nmax;   // first super-diagonal
+    double* du2 = T + 3 * nmax;  // second super-diagonal (fill-in from pivoting)
+    for (int i = 0; i < n; ++i) s[i] = 1.0 / sqrt((double)n);
+    for (int iter = 0; iter < 4; ++iter) {
+        for (int i = 0; i < n; ++i) {
+            dd[i] = al[i] - theta;
+            du[i] = i + 1 < n ? be[i] : 0.0;
+            dl[i] = i + 1 < n ? be[i] : 0.0;
+            du2[i] = 0.0;
+        }
+        for (int i = 0; i + 1 < n; ++i) {
+            if (fabs(dd[i]) >= fabs(dl[i])) {              // no row swap
+                if (dd[i] == 0.0) dd[i] = 1e-300 * scale;
+                const double f = dl[i] / dd[i];
+                dl[i] = f;
+                dd[i + 1] -= f * du[i];
+                s[i + 1] -= f * s[i];
+            } else {                                      // swap rows i and i+1
+                const double f = dd[i] / dl[i];
+                dd[i] = dl[i];
+                dl[i] = f;
+                const double t = du[i];
+                du[i] = dd[i + 1];
+                dd[i + 1] = t - f * dd[i + 1];
+                if (i + 2 < n) {
+                    du2[i] = du[i + 1];
+                    du[i + 1] = -f * du[i + 1];
+                }
+                const double sv = s[i];
+                s[i] = s[i + 1];
+                s[i + 1] = sv - f * s[i + 1];
+            }
+        }
+        if (dd[n - 1] == 0.0) dd[n - 1] = 1e-300 * scale;
+        // back substitution
+        for (int i = n - 1; i >= 0; --i) {
+            double v = s[i];
+            if (i + 1 < n) v -= du[i] * s[i + 1];
+            if (i + 2 < n) v -= du2[i] * s[i + 2];
+            s[i] = v / dd[i];
+        }
+        double nr = 0.0;
+        for (int i = 0; i < n; ++i) nr += s[i] * s[i];
+        nr = sqrt(nr);
+        for (int i = 0; i < n; ++i) s[i] /= nr;
+    }
+    // fix the sign (largest component positive) for reproducible Ritz vectors
+    int im = 0;
+    for (int i = 1; i < n; ++i) if (fabs(s[i]) > fabs(s[im])) im = i;
+    if (s[im] < 0) for (int i = 0; i < n; ++i) s[i] = -s[i];
+    state[2] = theta;
+    state[3] = fabs(be[n - 1] * s[n - 1]);
+}
+
+int grid_for(int64_t n) {
+    int64_t g = (n + RT - 1) / RT;
+    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+}  // namespace
+}  // namespace heff
+
+using namespace heff;
+
+extern "C" int heff_lanczos_workspace_size(const heff_plan* plan, int32_t n_iter, size_t* bytes) {
+    clear_error();
+    if (!plan || !bytes || n_iter < 1 || n_iter > 126)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_lanczos_workspace_size: bad arguments (n_iter 1..126)");
+    *bytes = lz_layout(plan->nelem_x, n_iter).bytes;
+    return HEFF_OK;
+}
+
+extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                            const double* x0, int32_t n_iter, double* x_out, double* result,
+                            void* apply_ws, size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes,
+                            void* stream) {
+    clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x0 || !x_out || !result || !lz_ws)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_lanczos: null argument");
+    if (plan->opts.io_dtype != HEFF_DTYPE_F64)
+        return fail(HEFF_ERR_UNSUPPORTED, "heff_lanczos needs a plan with HEFF_DTYPE_F64 tensors");
+    if (n_iter < 1 || n_iter > 126) return fail(HEFF_ERR_INVALID_ARG, "n_iter must be 1..126");
+    const LzLayout lay = lz_layout(plan->nelem_x, n_iter);
+    if (lz_ws_bytes < lay.bytes || reinterpret_cast<uintptr_t>(lz_ws) % 256)
+        return fail(HEFF_ERR_WORKSPACE, "Lanczos workspace of %zu bytes, needs %zu (256-byte aligned)",
+                    lz_ws_bytes, lay.bytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(lz_ws);
+    Lz z{reinterpret_cast<double*>(base + lay.off_state), reinterpret_cast<double*>(base + lay.off_h),
+         reinterpret_cast<double*>(base + lay.off_s), reinterpret_cast<double*>(base + lay.off_part),
+         reinterpret_cast<double*>(base + lay.off_T), reinterpret_cast<double*>(base + lay.off_V),
+         plan->nelem_x, lay.nmax};
+    const int64_t n = z.n;
+    const int G = grid_for(n);
+    int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
+    if (rc) return rc;
+    // v_0 = x0 / ||x0||
+    sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, z.part);
+    normalize_kernel<<<G, RT, 0, st>>>(z.part, RB, x0, z.V, n, z.state, 0, 0, z.nmax);
+    count_launches(2);
+    for (int k = 0; k < n_iter; ++k) {
+        double* vk = z.V + (int64_t)k * n;
+        // w = H v_k (skipped work is harmless after breakdown: the result is not used)
+        if ((rc = heff_apply_prepared(plan, vk, z.w(), apply_ws, apply_ws_bytes, stream))) return rc;
+        // two classical Gram-Schmidt passes: h1 -> z.h, h2 -> z.s
+        for (int pass = 0; pass < 2; ++pass) {
+            double* hp = pass == 0 ? z.h : z.s;
+            for (int j0 = 0; j0 <= k; j0 += VT) {
+                const int nv = k + 1 - j0 < VT ? k + 1 - j0 : VT;
+                multidot_kernel<<<RB, RT, 0, st>>>(z.V, z.w(), n, j0, nv, z.part, z.state);
+                finish_dots_kernel<<<1, RT, 0, st>>>(z.part, RB, j0, nv, hp, 0, z.state);
+                count_launches(2);
+            }
+            combine_kernel<<<G, RT, 0, st>>>(z.V, n, k + 1, hp, -1.0, 1.0, z.w(), z.state, 0);
+            count_launches(1);
+        }
+        set_alpha_kernel<<<1, 1, 0, st>>>(z.state, z.h, z.s, k);
+        sumsq_kernel<<<RB, RT, 0, st>>>(z.w(), n, z.part);
+        normalize_kernel<<<G, RT, 0, st>>>(z.part, RB, z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, 1, k,
+                                           z.nmax);
+        count_launches(3);
+    }
+    tridiag_eig_kernel<<<1, 32, 0, st>>>(z.state, z.T, z.s, z.nmax);
+    // x = V s (rows beyond n_eff have s = 0), then normalise
+    combine_kernel<<<G, RT, 0, st>>>(z.V, n, z.nmax, z.s, 1.0, 0.0, x_out, z.state, 1);
+    sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, z.part);
+    normalize_kernel<<<G, RT, 0, st>>>(z.part, RB, x_out, x_out, n, z.state, 2, 0, z.nmax);
+    count_launches(4);
+    // result: [theta, residual estimate, n_eff, alpha..., beta...]
+    cudaMemcpyAsync(result, z.state + 2, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(result + 2, z.state, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(result + 3, z.state + 8, sizeof(double) * 2 * z.nmax, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_lanczos: %s", cudaGetErrorString(e));
+    return HEFF_OK;
+}

@@ -64,6 +64,8 @@ _sig = {
     "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
     "heff_apply_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "heff_lanczos_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
+    "heff_lanczos": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
     "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
     "heff_last_error": (C.c_char_p, []),
@@ -224,6 +226,20 @@ def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
     ya = (_vp * n)(*[t.data_ptr() for t in ys])
     _check(_lib.heff_apply_batched(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), xa, ya, n, _ptr(ws),
                                    _nbytes(ws), _stream(stream)), "heff_apply_batched")
+
+
+def heff_lanczos_workspace_size(plan, n_iter):
+    b = _sz()
+    _check(_lib.heff_lanczos_workspace_size(plan, int(n_iter), C.byref(b)), "heff_lanczos_workspace_size")
+    return b.value
+
+
+def heff_lanczos(plan, L, W1, W2, R, x0, n_iter, x_out, result, apply_ws, lz_ws, stream=None):
+    """Lowest Ritz pair after n_iter FP64 Lanczos steps; result (device, float64) receives
+    [theta, residual estimate, Krylov dimension, alpha..., beta...]."""
+    _check(_lib.heff_lanczos(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x0), int(n_iter),
+                             _ptr(x_out), _ptr(result), _ptr(apply_ws), _nbytes(apply_ws), _ptr(lz_ws),
+                             _nbytes(lz_ws), _stream(stream)), "heff_lanczos")
 
 
 NOALLOC_WORKSPACE_BYTES = 128 << 20   # HEFF_NOALLOC_WORKSPACE_BYTES in include/heff.h

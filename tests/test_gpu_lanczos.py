@@ -1,0 +1,122 @@
+"""GPU FP64 Lanczos (heff_lanczos) against the oracle's Lanczos and exact eigenpairs.
+
+* FP64 path: the lowest Ritz value after n steps from the same start vector equals the
+  oracle's (Section II-C eigensolver; Lanczos with full reorthogonalisation) to 1e-10
+  relative, and the Ritz vectors agree;
+* BF16x3 / TF32x3 matvecs inside the FP64 Lanczos: the Ritz value is within the split
+  precision of the exact lowest eigenvalue; one FP64 Rayleigh quotient of the returned
+  vector (a single FP64 apply) brings the energy within 1e-8 relative of it (the
+  second-order accuracy of the Rayleigh quotient in the eigenvector error).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import heff as oh, eig
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2007_05540_gb300 import heff               # noqa: E402
+from tests.helpers import library_problem              # noqa: E402
+
+
+class LzProblem:
+    def __init__(self, name):
+        self.w = wl.workload_by_name(name)
+        self.lays, self.bufs = library_problem(self.w)
+        self.d = {k: torch.from_numpy(np.asarray(self.bufs[k])).to("cuda", torch.float64)
+                  for k in ("L", "W1", "W2", "R")}
+        self.x0 = torch.from_numpy(self.bufs["x"][0]).to("cuda", torch.float64)
+        self.plans = {}
+
+    def plan(self, prec):
+        if prec not in self.plans:
+            Ll, W1l, W2l, Rl, xl = self.lays
+            self.plans[prec] = heff.Plan(Ll, W1l, W2l, Rl, xl, self.bufs["W1"], self.bufs["W2"], prec, "f64")
+        return self.plans[prec]
+
+    def lanczos(self, prec, n_iter):
+        P = self.plan(prec)
+        ws = P.workspace()
+        lz = torch.empty(heff.heff_lanczos_workspace_size(P.handle, n_iter), dtype=torch.uint8, device="cuda")
+        x = torch.empty_like(self.x0)
+        res = torch.zeros(3 + 2 * (n_iter + 1), dtype=torch.float64, device="cuda")
+        d = self.d
+        heff.heff_lanczos(P.handle, d["L"], d["W1"], d["W2"], d["R"], self.x0, n_iter, x, res, ws, lz)
+        torch.cuda.synchronize()
+        return res.cpu().numpy(), x
+
+    def rayleigh_fp64(self, x):
+        P = self.plan("fp64")
+        ws = P.workspace()
+        y = torch.empty_like(x)
+        d = self.d
+        heff.heff_apply(P.handle, d["L"], d["W1"], d["W2"], d["R"], x, y, ws)
+        torch.cuda.synchronize()
+        return float(torch.dot(x, y) / torch.dot(x, x))
+
+    def oracle(self, n_iter):
+        L, W1, W2, R, x = oh.problem_from_workload(self.w)
+
+        def mv(v):
+            return oh.heff_apply(L, W1, W2, R, x.copy().set_flat(v)).flat()
+        return eig.lanczos(mv, x.flat(), n_iter)
+
+    def exact_lowest(self):
+        L, W1, W2, R, x = oh.problem_from_workload(self.w)
+        K = oh.heff_matrix_dense(L.to_dense(), W1, W2, R.to_dense())
+        mask = x.to_dense().reshape(-1) != 0
+        return float(np.linalg.eigvalsh(K[mask][:, mask])[0])
+
+
+@pytest.mark.parametrize("name,n_iter", [("spin_m64", 20), ("electron_m96", 25), ("spin_m1024", 30)])
+def test_fp64_lanczos_matches_oracle(name, n_iter):
+    p = LzProblem(name)
+    res, x = p.lanczos("fp64", n_iter)
+    th_o, x_o, info = p.oracle(n_iter)
+    th = res[0]
+    assert int(res[2]) == info["n"]
+    assert abs(th - th_o) < 1e-10 * abs(th_o), (th, th_o)
+    np.testing.assert_allclose(res[3:3 + info["n"]], info["alpha"], rtol=0, atol=1e-9 * abs(th_o))
+    ov = abs(float(np.dot(x.cpu().numpy(), x_o)))
+    assert ov > 1 - 1e-8, ov
+    print(f"{name}: theta {th:.15f} oracle {th_o:.15f} rel {abs(th - th_o) / abs(th_o):.2e}")
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-3), ("tf32x3", 1e-4)])
+@pytest.mark.parametrize("name", ["spin_m24", "electron_m40"])
+def test_mixed_lanczos_with_fp64_refinement(name, prec, tol):
+    p = LzProblem(name)
+    E0 = p.exact_lowest()
+    n_iter = min(120, p.lays[4].nelem)
+    res, x = p.lanczos(prec, n_iter)
+    th = res[0]
+    err_mixed = abs(th - E0) / abs(E0)
+    assert err_mixed < tol, err_mixed
+    th_rq = p.rayleigh_fp64(x)
+    err_rq = abs(th_rq - E0) / abs(E0)
+    print(f"{name} {prec}: E0 {E0:.12f} mixed Ritz err {err_mixed:.2e} refined err {err_rq:.2e}")
+    assert err_rq < 1e-8, err_rq
+
+
+def test_fp64_lanczos_converges_to_exact_lowest_eigenvalue():
+    p = LzProblem("spin_m24")
+    E0 = p.exact_lowest()
+    res, x = p.lanczos("fp64", min(120, p.lays[4].nelem))
+    assert abs(res[0] - E0) < 1e-11 * abs(E0)
+    assert res[1] < 1e-6 * abs(E0)          # Lanczos residual estimate of a converged pair
+
+
+def test_lanczos_rejects_f32_plans():
+    w = wl.workload_by_name("spin_m64")
+    lays, bufs = library_problem(w)
+    P = heff.Plan(*lays, bufs["W1"], bufs["W2"], "bf16x3", "f32")
+    t = torch.zeros(16, dtype=torch.float64, device="cuda")
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_lanczos(P.handle, t, t, t, t, t, 5, t, t, ws, ws)
+    assert e.value.code == -3
