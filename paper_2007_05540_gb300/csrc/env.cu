@@ -1,0 +1,238 @@
+// Environment extension on the GPU (Section II-C: the left environment A and right
+// environment B grow by one site as the sweep moves), in FP64 on the block-product engine.
+//
+// Left (site tensor A[a, s, b], flows (+1, +1, -1); environment L[a', w, a]):
+//   X[(a', w), (s, b)]  = L[a', w, a] . A[a, s, b]                      (step 1)
+//   Lnew[c, v, d]       = sum W[w, t, s, v] A[a', t, c]^T . X[(a', w), (s, d)]   (step 2)
+// Right (site tensor B[a, s, b]; environment R[b', w, b]):
+//   Y[(b', v), (a, s)]  = R[b', v, b] . B[a, s, b]^T                    (step 1)
+//   Rnew[c, w, d]       = sum W[w, t, s, v] B[c, t, b'] . Y[(b', v), (d, s)]     (step 2)
+// Each charge-matched block pair is one small dense product; step 2 sums, per output
+// block, the products whose MPO coefficient is nonzero in the host copy of W.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <new>
+#include <tuple>
+
+#include "internal.h"
+
+using heff::fail;
+using heff::BList;
+using heff::BProd;
+
+struct heff_env_plan {
+    int side = 0;
+    BList step1, step2;
+    int64_t ws_elems = 0;      // intermediate (X or Y) in doubles
+    size_t ws_bytes = 0;
+    bool uploaded = false;
+};
+
+namespace {
+
+using Charge = std::vector<int32_t>;
+
+bool same(const heff::IndexDesc& a, const heff::IndexDesc& b) { return a.same_sectors(b); }
+
+Charge add(const Charge& a, const Charge& b, int sb = 1) {
+    Charge r(a);
+    for (size_t c = 0; c < r.size(); ++c) r[c] += sb * b[c];
+    return r;
+}
+
+}  // namespace
+
+extern "C" int heff_env_plan_create(const heff_layout* env_old, const heff_layout* site, const heff_layout* W,
+                                    const heff_layout* env_new, const double* W_host, int32_t side,
+                                    heff_env_plan** out) {
+    heff::clear_error();
+    if (!env_old || !site || !W || !env_new || !W_host || !out || (side != 0 && side != 1))
+        return fail(HEFF_ERR_INVALID_ARG, "heff_env_plan_create: bad arguments");
+    *out = nullptr;
+    if (env_old->idx.size() != 3 || env_new->idx.size() != 3 || site->idx.size() != 3 || W->idx.size() != 4)
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "orders must be env 3, site 3, W 4");
+    const heff::IndexDesc &sa = site->idx[0], &sp = site->idx[1], &sb = site->idx[2];
+    if (sa.flow != 1 || sp.flow != 1 || sb.flow != -1)
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "site tensor flows must be (+1, +1, -1)");
+    const heff::IndexDesc& bond_in = side == 0 ? sa : sb;    // bond of env_old
+    const heff::IndexDesc& bond_out = side == 0 ? sb : sa;   // bond of env_new
+    const heff::IndexDesc &wi = side == 0 ? W->idx[0] : W->idx[3];    // channels of env_old
+    const heff::IndexDesc &wo = side == 0 ? W->idx[3] : W->idx[0];    // channels of env_new
+    if (!same(env_old->idx[0], bond_in) || !same(env_old->idx[2], bond_in) || !same(env_old->idx[1], wi))
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "env_old must be (bond, channel, bond) on the site's %s bond",
+                    side == 0 ? "left" : "right");
+    if (!same(env_new->idx[0], bond_out) || !same(env_new->idx[2], bond_out) || !same(env_new->idx[1], wo))
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "env_new must be (bond, channel, bond) on the site's %s bond",
+                    side == 0 ? "right" : "left");
+    if (!same(W->idx[1], sp) || !same(W->idx[2], sp))
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "W physical indices must match the site tensor");
+    heff_env_plan* P = new (std::nothrow) heff_env_plan();
+    if (!P) return fail(HEFF_ERR_OOM, "out of host memory");
+    P->side = side;
+    try {
+        const int d = sp.nsec, kw = W->idx[0].nsec, kv = W->idx[3].nsec;
+        auto widx = [&](int w, int t, int s, int v) -> int32_t {
+            int64_t o = W->offset_of({w, t, s, v});
+            return (o >= 0 && W_host[o] != 0.0) ? (int32_t)o : -1;
+        };
+        // site blocks by key
+        auto site_off = [&](int a, int s, int b) { return site->offset_of({a, s, b}); };
+        std::map<std::tuple<int, int, int, int>, int64_t> inter;   // intermediate blocks -> offset
+        int64_t ioff = 0;
+        if (side == 0) {
+            // X(ia, w, s, jd) = L(ia, w, ib) A(ib, s, jd): needed when some W[w, t, s, v] != 0
+            for (size_t bk = 0; bk < env_old->offsets.size(); ++bk) {
+                const int ia = env_old->keys[bk * 3], w = env_old->keys[bk * 3 + 1], ib = env_old->keys[bk * 3 + 2];
+                for (int s = 0; s < d; ++s) {
+                    bool used = false;
+                    for (int t = 0; t < d && !used; ++t)
+                        for (int v = 0; v < kv && !used; ++v) used = widx(w, t, s, v) >= 0;
+                    if (!used) continue;
+                    int jd = sb.find(add(sa.q(ib), sp.q(s)));
+                    if (jd < 0) continue;
+                    int64_t so = site_off(ib, s, jd);
+                    if (so < 0) continue;
+                    const int mia = sa.dims[ia], mib = sa.dims[ib], mjd = sb.dims[jd];
+                    inter[{ia, w, s, jd}] = ioff;
+                    BProd p{};
+                    p.a_off = env_old->offsets[bk]; p.a_rs = mib; p.a_cs = 1;
+                    p.b_off = so; p.b_rs = mjd; p.b_cs = 1;
+                    p.K = mib; p.c1 = -1; p.c2 = -1;
+                    P->step1.add_block(ioff, mjd, mia, mjd, {p});
+                    ioff += (int64_t)mia * mjd;
+                }
+            }
+            // Lnew(jc, v, jd) = sum W[w,t,s,v] A(ia, t, jc)^T X(ia, w, s, jd)
+            for (size_t bk = 0; bk < env_new->offsets.size(); ++bk) {
+                const int jc = env_new->keys[bk * 3], v = env_new->keys[bk * 3 + 1], jd = env_new->keys[bk * 3 + 2];
+                const int mjc = sb.dims[jc], mjd = sb.dims[jd];
+                std::vector<BProd> ps;
+                for (int t = 0; t < d; ++t) {
+                    int ia = sa.find(add(sb.q(jc), sp.q(t), -1));
+                    if (ia < 0) continue;
+                    int64_t so = site_off(ia, t, jc);
+                    if (so < 0) continue;
+                    for (int w = 0; w < kw; ++w)
+                        for (int s = 0; s < d; ++s) {
+                            int32_t c = widx(w, t, s, v);
+                            if (c < 0) continue;
+                            auto it = inter.find({ia, w, s, jd});
+                            if (it == inter.end()) continue;
+                            BProd p{};
+                            p.a_off = so; p.a_rs = 1; p.a_cs = mjc;          // A^T: (c, a) at a*mjc + c
+                            p.b_off = it->second; p.b_rs = mjd; p.b_cs = 1;
+                            p.K = sa.dims[ia]; p.c1 = c; p.c2 = -1;
+                            ps.push_back(p);
+                        }
+                }
+                P->step2.add_block(env_new->offsets[bk], mjd, mjc, mjd, ps);
+            }
+        } else {
+            // Y(ja, v, id, s) = R(ja, v, jb) B(id, s, jb)^T
+            for (size_t bk = 0; bk < env_old->offsets.size(); ++bk) {
+                const int ja = env_old->keys[bk * 3], v = env_old->keys[bk * 3 + 1], jb = env_old->keys[bk * 3 + 2];
+                for (int s = 0; s < d; ++s) {
+                    bool used = false;
+                    for (int t = 0; t < d && !used; ++t)
+                        for (int w = 0; w < kw && !used; ++w) used = widx(w, t, s, v) >= 0;
+                    if (!used) continue;
+                    int id = sa.find(add(sb.q(jb), sp.q(s), -1));
+                    if (id < 0) continue;
+                    int64_t so = site_off(id, s, jb);
+                    if (so < 0) continue;
+                    const int mja = sb.dims[ja], mjb = sb.dims[jb], mid = sa.dims[id];
+                    inter[{ja, v, id, s}] = ioff;
+                    BProd p{};
+                    p.a_off = env_old->offsets[bk]; p.a_rs = mjb; p.a_cs = 1;
+                    p.b_off = so; p.b_rs = 1; p.b_cs = mjb;          // B^T: (b, d) at d*mjb + b
+                    p.K = mjb; p.c1 = -1; p.c2 = -1;
+                    P->step1.add_block(ioff, mid, mja, mid, {p});
+                    ioff += (int64_t)mja * mid;
+                }
+            }
+            // Rnew(ic, w, id) = sum W[w,t,s,v] B(ic, t, ja) Y(ja, v, id, s)
+            for (size_t bk = 0; bk < env_new->offsets.size(); ++bk) {
+                const int ic = env_new->keys[bk * 3], w = env_new->keys[bk * 3 + 1], id = env_new->keys[bk * 3 + 2];
+                const int mic = sa.dims[ic], mid = sa.dims[id];
+                std::vector<BProd> ps;
+                for (int t = 0; t < d; ++t) {
+                    int ja = sb.find(add(sa.q(ic), sp.q(t)));
+                    if (ja < 0) continue;
+                    int64_t so = site_off(ic, t, ja);
+                    if (so < 0) continue;
+                    const int mja = sb.dims[ja];
+                    for (int v = 0; v < kv; ++v)
+                        for (int s = 0; s < d; ++s) {
+                            int32_t c = widx(w, t, s, v);
+                            if (c < 0) continue;
+                            auto it = inter.find({ja, v, id, s});
+                            if (it == inter.end()) continue;
+                            BProd p{};
+                            p.a_off = so; p.a_rs = mja; p.a_cs = 1;
+                            p.b_off = it->second; p.b_rs = mid; p.b_cs = 1;
+                            p.K = mja; p.c1 = c; p.c2 = -1;
+                            ps.push_back(p);
+                        }
+                }
+                P->step2.add_block(env_new->offsets[bk], mid, mic, mid, ps);
+            }
+        }
+        P->ws_elems = ioff;
+        P->ws_bytes = (size_t)((ioff + 31) / 32 * 32) * sizeof(double) + 256;
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(HEFF_ERR_OOM, "out of host memory while planning the environment update");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+        int rc;
+        if ((rc = heff::blist_upload(P->step1)) || (rc = heff::blist_upload(P->step2))) {
+            heff::blist_free(P->step1);
+            heff::blist_free(P->step2);
+            delete P;
+            return rc;
+        }
+        P->uploaded = true;
+    } else {
+        cudaGetLastError();
+    }
+    *out = P;
+    return HEFF_OK;
+}
+
+extern "C" int heff_env_workspace_size(const heff_env_plan* plan, size_t* bytes) {
+    heff::clear_error();
+    if (!plan || !bytes) return fail(HEFF_ERR_INVALID_ARG, "heff_env_workspace_size: null argument");
+    *bytes = plan->ws_bytes;
+    return HEFF_OK;
+}
+
+extern "C" int heff_env_flops(const heff_env_plan* plan, double* flops) {
+    heff::clear_error();
+    if (!plan || !flops) return fail(HEFF_ERR_INVALID_ARG, "heff_env_flops: null argument");
+    *flops = plan->step1.flops + plan->step2.flops;
+    return HEFF_OK;
+}
+
+extern "C" int heff_env_update(heff_env_plan* plan, const double* env_old, const double* site, const double* W,
+                               double* env_new, void* workspace, size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !env_old || !site || !W || !env_new)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_env_update: null argument");
+    if (!plan->uploaded) return fail(HEFF_ERR_UNSUPPORTED, "env plan was created without a CUDA device");
+    if (!workspace || workspace_bytes < plan->ws_bytes || reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(HEFF_ERR_WORKSPACE, "environment workspace of %zu bytes, needs %zu (256-byte aligned)",
+                    workspace_bytes, plan->ws_bytes);
+    double* X = static_cast<double*>(workspace);
+    int rc;
+    if ((rc = heff::launch_bgemm(plan->step1, env_old, site, X, nullptr, nullptr, 1.0, stream))) return rc;
+    return heff::launch_bgemm(plan->step2, site, X, env_new, W, nullptr, 1.0, stream);
+}
+
+extern "C" void heff_env_plan_destroy(heff_env_plan* plan) {
+    if (!plan) return;
+    heff::blist_free(plan->step1);
+    heff::blist_free(plan->step2);
+    delete plan;
+}

@@ -72,6 +72,45 @@ struct KSeg {
     int32_t k0, klen;       // column range shared by A and B (klen multiple of KPAD)
 };
 
+// ---------------------------------------------------------------- block-product engine
+// One output tile C[m x n] (m, n <= 64) = scale * sum over its products of
+//   coef * A[a_off + r * a_rs + k * a_cs] * B[b_off + k * b_rs + c * b_cs],  k < K,
+// coef = (c1 < 0 ? 1 : coef1[c1]) * (c2 < 0 ? 1 : coef2[c2]).  FP64 throughout.
+struct BProd {
+    int64_t a_off, b_off;
+    int32_t a_rs, a_cs, b_rs, b_cs;
+    int32_t K;
+    int32_t c1, c2;
+    int32_t pad_;
+};
+struct BTile {
+    int64_t c_off;
+    int32_t ldc, m, n;
+    int32_t prod_begin, prod_count;
+    int32_t pad_;
+};
+struct BList {
+    std::vector<BTile> tiles;
+    std::vector<BProd> prods;
+    BTile* d_tiles = nullptr;
+    BProd* d_prods = nullptr;
+    double flops = 0;
+    // append the tiles of an m x n output block whose products are given for the block origin
+    void add_block(int64_t c_off, int32_t ldc, int32_t m, int32_t n, const std::vector<BProd>& ps);
+};
+int blist_upload(BList& b);
+void blist_free(BList& b);
+int launch_bgemm(const BList& b, const double* A, const double* B, double* C, const double* coef1,
+                 const double* coef2, double scale, void* stream, const double* inv_scale = nullptr);
+// out[j] = scale * sum over the dots d in [off[j], off[j+1]) of <X[x_off..], Y[y_off..]>
+// (dots sorted by output index; scratch holds one double per dot)
+struct BDot {
+    int64_t x_off, y_off;
+    int64_t len;
+};
+int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const double* X, const double* Y,
+                      double* out, int nout, double* scratch, double scale, void* stream);
+
 constexpr int MAXB = 64;   // batch entries per launch (kernel parameter arrays)
 struct PtrBatch { const void* p[MAXB]; };
 

@@ -64,6 +64,11 @@ _sig = {
     "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
     "heff_apply_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "heff_env_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _P(C.c_double), _i32, _P(_vp)]),
+    "heff_env_workspace_size": (C.c_int, [_vp, _P(_sz)]),
+    "heff_env_flops": (C.c_int, [_vp, _P(C.c_double)]),
+    "heff_env_update": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "heff_env_plan_destroy": (None, [_vp]),
     "heff_lanczos_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
     "heff_lanczos": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
@@ -226,6 +231,35 @@ def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
     ya = (_vp * n)(*[t.data_ptr() for t in ys])
     _check(_lib.heff_apply_batched(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), xa, ya, n, _ptr(ws),
                                    _nbytes(ws), _stream(stream)), "heff_apply_batched")
+
+
+def heff_env_plan_create(env_old, site, W, env_new, W_host, side):
+    w = np.ascontiguousarray(W_host, dtype=np.float64)
+    out = _vp()
+    _check(_lib.heff_env_plan_create(env_old, site, W, env_new, w.ctypes.data_as(_P(C.c_double)),
+                                     0 if side in (0, "left") else 1, C.byref(out)), "heff_env_plan_create")
+    return out
+
+
+def heff_env_workspace_size(plan):
+    b = _sz()
+    _check(_lib.heff_env_workspace_size(plan, C.byref(b)), "heff_env_workspace_size")
+    return b.value
+
+
+def heff_env_flops(plan):
+    f = C.c_double()
+    _check(_lib.heff_env_flops(plan, C.byref(f)), "heff_env_flops")
+    return f.value
+
+
+def heff_env_update(plan, env_old, site, W, env_new, ws, stream=None):
+    _check(_lib.heff_env_update(plan, _ptr(env_old), _ptr(site), _ptr(W), _ptr(env_new), _ptr(ws),
+                                _nbytes(ws), _stream(stream)), "heff_env_update")
+
+
+def heff_env_plan_destroy(plan):
+    _lib.heff_env_plan_destroy(plan)
 
 
 def heff_lanczos_workspace_size(plan, n_iter):

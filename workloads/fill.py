@@ -16,7 +16,12 @@ from .sectors import (binomial_sectors, paper_model_sectors, electron_sectors,
                       spin_phys, electron_phys)
 from .mpo import heisenberg_mpo, hubbard_mpo, chain_pairs, bulk_window
 
-TAG_L, TAG_R, TAG_X = 1, 2, 3
+TAG_L, TAG_R, TAG_X, TAG_SITE = 1, 2, 3, 4
+
+
+def site_block(seed, key, shape):
+    """Gaussian block of an MPS site tensor T[a, s, b] (key = (a, s, b) sectors)."""
+    return gaussian_block(seed, TAG_SITE, key, shape)
 
 
 def gaussian_block(seed, tag, key, shape):
