@@ -209,6 +209,52 @@ int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2,
                  size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes, void* stream);
 
 /*
+ * Environment extension (Section II-C: the left environment A and right environment B
+ * are grown one site at a time as the sweep moves).  FP64 block products on the GPU.
+ *   side 0 (left):  Lnew[c,v,d] = sum A[a,t,c] L[a,w,b] W[w,t,s,v] A[b,s,d]
+ *   side 1 (right): Rnew[c,w,d] = sum B[c,t,a] R[a,v,b] W[w,t,s,v] B[d,s,b]
+ * Layouts: site (a, s, b) flows (+1, +1, -1); W (w, t, s, v) flows (+1, +1, -1, -1);
+ * env_old / env_new (bond, channel, bond) flows (-1, +1, +1) on the site's left / right
+ * bond (side 0) or right / left bond (side 1), channels of W's first / last index.
+ * W_host: host copy of W in its layout; zero entries are dropped from the schedule.
+ * heff_env_update: all tensors are device double buffers; env_new is overwritten;
+ * workspace >= heff_env_workspace_size bytes, 256-byte aligned.  Asynchronous.
+ */
+typedef struct heff_env_plan heff_env_plan;
+int heff_env_plan_create(const heff_layout* env_old, const heff_layout* site, const heff_layout* W,
+                         const heff_layout* env_new, const double* W_host, int32_t side,
+                         heff_env_plan** out);
+int heff_env_workspace_size(const heff_env_plan* plan, size_t* bytes);
+int heff_env_flops(const heff_env_plan* plan, double* flops);
+int heff_env_update(heff_env_plan* plan, const double* env_old, const double* site, const double* W,
+                    double* env_new, void* workspace, size_t workspace_bytes, void* stream);
+void heff_env_plan_destroy(heff_env_plan* plan);
+
+/*
+ * Gradients of the Rayleigh quotient rho = <x|K|x> / <x|x> of the effective Hamiltonian
+ * K (Section II-C): rho is linear in L, R, W1 and W2, so each gradient is the closed-form
+ * contraction of the bra x, the ket x and the other three operators; d rho/dx =
+ * 2 (K x - rho x) / <x|x>.  heff_grad_plan_create builds the block-product schedule for
+ * the five layouts (host MPO copies drop exactly-zero entries from the W1.W2 pattern; the
+ * W gradients are computed for every allowed entry).  heff_backward computes y = K x with
+ * `plan` (any precision; HEFF_DTYPE_F64 tensors) and the rest in FP64:
+ *   rho: device, 1 double; dx, dL, dR, dW1, dW2: device doubles in the layouts of x, L,
+ *   R, W1, W2 (overwritten).  apply_ws: plan workspace; grad_ws >= heff_grad_workspace_size
+ *   bytes, 256-byte aligned.  The gradient with respect to a coupling J that W1, W2
+ *   depend on is sum dW1 * dW1/dJ + sum dW2 * dW2/dJ (L and R held fixed).
+ */
+typedef struct heff_grad_plan heff_grad_plan;
+int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1, const heff_layout* W2,
+                          const heff_layout* R, const heff_layout* x, const double* W1_host,
+                          const double* W2_host, heff_grad_plan** out);
+int heff_grad_workspace_size(const heff_grad_plan* g, size_t* bytes);
+int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L, const double* W1,
+                  const double* W2, const double* R, const double* x, double* rho, double* dx,
+                  double* dL, double* dR, double* dW1, double* dW2, void* apply_ws,
+                  size_t apply_ws_bytes, void* grad_ws, size_t grad_ws_bytes, void* stream);
+void heff_grad_plan_destroy(heff_grad_plan* g);
+
+/*
  * heff_apply_noalloc -- heff_apply without a caller-provided workspace and without any
  * device allocation.  The paper has no counterpart of it: it exists because some callers
  * cannot call cudaMalloc, for example code running under another framework's memory

@@ -64,6 +64,10 @@ _sig = {
     "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
     "heff_apply_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "heff_grad_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _P(C.c_double), _P(_vp)]),
+    "heff_grad_workspace_size": (C.c_int, [_vp, _P(_sz)]),
+    "heff_backward": (C.c_int, [_vp] * 13 + [_vp, _sz, _vp, _sz, _vp]),
+    "heff_grad_plan_destroy": (None, [_vp]),
     "heff_env_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _P(C.c_double), _i32, _P(_vp)]),
     "heff_env_workspace_size": (C.c_int, [_vp, _P(_sz)]),
     "heff_env_flops": (C.c_int, [_vp, _P(C.c_double)]),
@@ -233,6 +237,32 @@ def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
                                    _nbytes(ws), _stream(stream)), "heff_apply_batched")
 
 
+def heff_grad_plan_create(L, W1, W2, R, x, W1_host, W2_host):
+    w1 = np.ascontiguousarray(W1_host, dtype=np.float64)
+    w2 = np.ascontiguousarray(W2_host, dtype=np.float64)
+    out = _vp()
+    _check(_lib.heff_grad_plan_create(L, W1, W2, R, x, w1.ctypes.data_as(_P(C.c_double)),
+                                      w2.ctypes.data_as(_P(C.c_double)), C.byref(out)), "heff_grad_plan_create")
+    return out
+
+
+def heff_grad_workspace_size(g):
+    b = _sz()
+    _check(_lib.heff_grad_workspace_size(g, C.byref(b)), "heff_grad_workspace_size")
+    return b.value
+
+
+def heff_backward(g, plan, L, W1, W2, R, x, rho, dx, dL, dR, dW1, dW2, apply_ws, grad_ws, stream=None):
+    """rho = <x|K|x>/<x|x> (device scalar) and its gradients (device float64 buffers)."""
+    _check(_lib.heff_backward(g, plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(rho), _ptr(dx),
+                              _ptr(dL), _ptr(dR), _ptr(dW1), _ptr(dW2), _ptr(apply_ws), _nbytes(apply_ws),
+                              _ptr(grad_ws), _nbytes(grad_ws), _stream(stream)), "heff_backward")
+
+
+def heff_grad_plan_destroy(g):
+    _lib.heff_grad_plan_destroy(g)
+
+
 def heff_env_plan_create(env_old, site, W, env_new, W_host, side):
     w = np.ascontiguousarray(W_host, dtype=np.float64)
     out = _vp()
@@ -392,3 +422,39 @@ class Plan:
         if getattr(self, "handle", None):
             heff_plan_destroy(self.handle)
             self.handle = None
+
+
+class RayleighQuotient:
+    """torch.autograd.Function for rho(x, L, W1, W2, R) = <x|K|x> / <x|x>.
+
+    ``RayleighQuotient.apply(ctx_obj, x, L, W1, W2, R)`` returns rho as a 0-d tensor; the
+    forward pass runs heff_backward (one apply plus the closed-form gradients, all on the
+    GPU) and the backward pass scales the stored gradients by the incoming gradient.
+    ``ctx_obj`` holds the plans and workspaces: ``(grad_plan, apply_plan, apply_ws, grad_ws)``.
+    """
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, ctx_obj, x, L, W1, W2, R):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x, L, W1, W2, R, holder):
+                    g, plan, aws, gws = holder
+                    rho = torch.empty((), dtype=torch.float64, device=x.device)
+                    grads = [torch.empty_like(t) for t in (x, L, R, W1, W2)]
+                    heff_backward(g, plan, L, W1, W2, R, x, rho, grads[0], grads[1], grads[2], grads[3],
+                                  grads[4], aws, gws)
+                    ctx.save_for_backward(*grads)
+                    return rho
+
+                @staticmethod
+                def backward(ctx, go):
+                    dx, dL, dR, dW1, dW2 = ctx.saved_tensors
+                    return go * dx, go * dL, go * dW1, go * dW2, go * dR, None
+
+            cls._fn = _F
+        return cls._fn.apply(x, L, W1, W2, R, ctx_obj)

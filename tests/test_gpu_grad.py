@@ -1,0 +1,130 @@
+"""GPU Rayleigh-quotient gradients (heff_backward) against the oracle.
+
+The oracle's gradients are pinned by central finite differences, Euler homogeneity and
+the closed form for dx (tests/test_oracle_eig_svd_dmrg_grad.py).  Here the GPU results
+(FP64 apply plan) must equal them to 1e-11 relative; the gradient with respect to the
+tagged J2 coupling (through W1 and W2 only) must equal a central difference of the GPU
+rho; with a BF16x3 apply plan only rho and dx carry the split-precision error.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from workloads.fill import spin_window, SPIN_COUPLINGS
+from oracle import heff as oh, grad as ograd
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2007_05540_gb300 import heff              # noqa: E402
+from tests.helpers import library_problem             # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float64)).to("cuda")
+
+
+class GradRun:
+    def __init__(self, w, prec="fp64"):
+        self.w = w
+        self.lays, self.bufs = library_problem(w)
+        Ll, W1l, W2l, Rl, xl = self.lays
+        self.plan = heff.Plan(Ll, W1l, W2l, Rl, xl, self.bufs["W1"], self.bufs["W2"], prec, "f64")
+        self.g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle,
+                                            self.bufs["W1"], self.bufs["W2"])
+        self.aws = self.plan.workspace()
+        self.gws = torch.empty(heff.heff_grad_workspace_size(self.g), dtype=torch.uint8, device="cuda")
+
+    def run(self, W1=None, W2=None):
+        b = self.bufs
+        d = {k: _dev(b[k]) for k in ("L", "R")}
+        d["W1"] = _dev(b["W1"] if W1 is None else W1)
+        d["W2"] = _dev(b["W2"] if W2 is None else W2)
+        x = _dev(b["x"][0])
+        rho = torch.empty((), dtype=torch.float64, device="cuda")
+        out = [torch.full_like(t, float("nan")) for t in (x, d["L"], d["R"], d["W1"], d["W2"])]
+        heff.heff_backward(self.g, self.plan.handle, d["L"], d["W1"], d["W2"], d["R"], x, rho, *out,
+                           self.aws, self.gws)
+        torch.cuda.synchronize()
+        return float(rho), [t.cpu().numpy() for t in out]
+
+    def __del__(self):
+        heff.heff_grad_plan_destroy(self.g)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name", ["spin_m64", "electron_m96", "spin_m200"])
+def test_backward_matches_oracle(name):
+    w = wl.workload_by_name(name)
+    r = GradRun(w)
+    rho, (dx, dL, dR, dW1, dW2) = r.run()
+    L, W1, W2, R, x = oh.problem_from_workload(w)
+    ref = ograd.grad_all(L, W1, W2, R, x)
+    Ll, W1l, W2l, Rl, xl = r.lays
+    assert abs(rho - ref["rho"]) < 1e-12 * abs(ref["rho"])
+    errs = {
+        "dx": _rel(dx, xl.assemble(lambda k: ref["dx"].blocks[k])),
+        "dL": _rel(dL, Ll.assemble(lambda k: ref["dL"].blocks[k])),
+        "dR": _rel(dR, Rl.assemble(lambda k: ref["dR"].blocks[k])),
+        "dW1": _rel(dW1, W1l.assemble(lambda k: ref["dW1"][k])),
+        "dW2": _rel(dW2, W2l.assemble(lambda k: ref["dW2"][k])),
+    }
+    print(name, {k: f"{v:.1e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < 1e-11, (k, v)
+    # Euler homogeneity on the GPU results: rho is linear in L, R, W1, W2; degree 0 in x
+    b = r.bufs
+    for g_, t_ in ((dL, b["L"]), (dR, b["R"]), (dW1, b["W1"]), (dW2, b["W2"])):
+        assert abs(float(np.dot(g_, t_)) - rho) < 1e-11 * abs(rho)
+    assert abs(float(np.dot(dx, b["x"][0]))) < 1e-11 * abs(rho) * np.linalg.norm(b["x"][0])
+
+
+def test_backward_j2_coupling_central_difference():
+    w = wl.workload_by_name("spin_m64")
+    r = GradRun(w)
+    W1l, W2l = r.lays[1], r.lays[2]
+
+    def Ws(J2):
+        c = list(SPIN_COUPLINGS)
+        c[1] = J2
+        win = spin_window(tuple(c))
+        return W1l.assemble(lambda k: win["W1"][k]), W2l.assemble(lambda k: win["W2"][k])
+    J2, h = SPIN_COUPLINGS[1], 1e-6
+    rho, (dx, dL, dR, dW1, dW2) = r.run()
+    W1p, W2p = Ws(J2 + h)
+    W1m, W2m = Ws(J2 - h)
+    an = float(np.dot(dW1, (W1p - W1m) / (2 * h)) + np.dot(dW2, (W2p - W2m) / (2 * h)))
+    fd = (r.run(W1p, W2p)[0] - r.run(W1m, W2m)[0]) / (2 * h)
+    print(f"d rho / d J2: analytic {an:.10f}  central difference {fd:.10f}")
+    assert abs(an - fd) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_backward_with_split_precision_apply():
+    w = wl.workload_by_name("spin_m200")
+    exact = GradRun(w, "fp64").run()
+    rho, grads = GradRun(w, "bf16x3").run()
+    assert abs(rho - exact[0]) < 1e-4 * abs(exact[0])
+    assert _rel(grads[0], exact[1][0]) < 1e-3                 # dx uses the BF16x3 apply
+    for a, b in zip(grads[1:], exact[1][1:]):                 # L, R, W gradients: FP64 only
+        assert _rel(a, b) < 1e-13
+
+
+def test_autograd_function():
+    w = wl.workload_by_name("spin_m64")
+    r = GradRun(w)
+    b = r.bufs
+    ts = {k: _dev(b[k]).requires_grad_(True) for k in ("L", "W1", "W2", "R")}
+    x = _dev(b["x"][0]).requires_grad_(True)
+    rho = heff.RayleighQuotient.apply((r.g, r.plan.handle, r.aws, r.gws), x, ts["L"], ts["W1"], ts["W2"],
+                                      ts["R"])
+    (3.0 * rho).backward()
+    _, (dx, dL, dR, dW1, dW2) = r.run()
+    assert np.allclose(x.grad.cpu().numpy(), 3.0 * dx, rtol=0, atol=1e-14 * np.abs(dx).max() + 1e-300)
+    assert np.allclose(ts["L"].grad.cpu().numpy(), 3.0 * dL)
+    assert np.allclose(ts["W2"].grad.cpu().numpy(), 3.0 * dW2)
