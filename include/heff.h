@@ -255,6 +255,41 @@ int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L, const dou
 void heff_grad_plan_destroy(heff_grad_plan* g);
 
 /*
+ * Block SVD split of the two-site tensor with truncation (Section IV: the tensor is
+ * wrapped into the matrix (a s1) x (s2 b), one dense block per charge Q = q(a) + q(s1);
+ * Fig. 1e: split into two order-3 tensors, singular values absorbed in the sweep
+ * direction; Section II-C: singular values below a cutoff are removed).  FP64 on the GPU
+ * (one-sided Jacobi per block, rounds of disjoint column-pair rotations); the output
+ * shapes depend on the truncation, so the call sequence is:
+ *   heff_svd_create(x_layout)            host: charge blocks, workspace size
+ *   heff_svd_compute(x_dev, ws)           decomposes every block; SYNCHRONISES (per-sweep
+ *                                         convergence check, singular values to the host)
+ *   heff_svd_truncate(m_max, cutoff, ...) host: on x/||x||, drop s < cutoff, keep at most
+ *                                         m_max largest (ties within 1e-12 s_max ordered by
+ *                                         (|Q|, Q, rank)); returns the new bond (charges
+ *                                         Q in increasing order, dims = kept counts), the
+ *                                         discarded weight sum s^2/||x||^2 and ||x||
+ *   heff_svd_write(A_layout, B_layout)    writes A[a, s1, c] (flows +1, +1, -1) and
+ *                                         B[c, s2, b] (flows +1, +1, -1) on the new bond;
+ *                                         absorb_right = 1: B carries S (A is an isometry),
+ *                                         0: A carries S.  Synchronises.
+ * charges_out: host [nsec * nq] (may be NULL); dims_out: host [nsec] (may be NULL; the
+ * caller can first query nsec with both NULL... pass arrays of at least the number of
+ * charge blocks of x).
+ */
+typedef struct heff_svd heff_svd;
+int heff_svd_create(const heff_layout* x, heff_svd** out);
+int heff_svd_workspace_size(const heff_svd* s, size_t* bytes);
+int heff_svd_compute(heff_svd* s, const double* x, void* workspace, size_t workspace_bytes, void* stream,
+                     int32_t* sweeps_out);
+int heff_svd_truncate(heff_svd* s, int32_t m_max, double cutoff, int32_t* nsec_out, int32_t* charges_out,
+                      int32_t* dims_out, double* discarded_weight, double* norm);
+int heff_svd_singular_values(const heff_svd* s, double* out);
+int heff_svd_write(heff_svd* s, const heff_layout* A_layout, const heff_layout* B_layout, double* A,
+                   double* B, int32_t absorb_right, void* workspace, size_t workspace_bytes, void* stream);
+void heff_svd_destroy(heff_svd* s);
+
+/*
  * heff_apply_noalloc -- heff_apply without a caller-provided workspace and without any
  * device allocation.  The paper has no counterpart of it: it exists because some callers
  * cannot call cudaMalloc, for example code running under another framework's memory

@@ -64,6 +64,14 @@ _sig = {
     "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
     "heff_apply_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "heff_svd_create": (C.c_int, [_vp, _P(_vp)]),
+    "heff_svd_workspace_size": (C.c_int, [_vp, _P(_sz)]),
+    "heff_svd_compute": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _P(_i32)]),
+    "heff_svd_truncate": (C.c_int, [_vp, _i32, C.c_double, _P(_i32), _P(_i32), _P(_i32), _P(C.c_double),
+                                    _P(C.c_double)]),
+    "heff_svd_singular_values": (C.c_int, [_vp, _P(C.c_double)]),
+    "heff_svd_write": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
+    "heff_svd_destroy": (None, [_vp]),
     "heff_grad_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _P(C.c_double), _P(_vp)]),
     "heff_grad_workspace_size": (C.c_int, [_vp, _P(_sz)]),
     "heff_backward": (C.c_int, [_vp] * 13 + [_vp, _sz, _vp, _sz, _vp]),
@@ -235,6 +243,52 @@ def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
     ya = (_vp * n)(*[t.data_ptr() for t in ys])
     _check(_lib.heff_apply_batched(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), xa, ya, n, _ptr(ws),
                                    _nbytes(ws), _stream(stream)), "heff_apply_batched")
+
+
+def heff_svd_create(x_layout):
+    out = _vp()
+    _check(_lib.heff_svd_create(x_layout, C.byref(out)), "heff_svd_create")
+    return out
+
+
+def heff_svd_workspace_size(s):
+    b = _sz()
+    _check(_lib.heff_svd_workspace_size(s, C.byref(b)), "heff_svd_workspace_size")
+    return b.value
+
+
+def heff_svd_compute(s, x, ws, stream=None):
+    sw = _i32()
+    _check(_lib.heff_svd_compute(s, _ptr(x), _ptr(ws), _nbytes(ws), _stream(stream), C.byref(sw)),
+           "heff_svd_compute")
+    return sw.value
+
+
+def heff_svd_truncate(s, m_max, cutoff, nq, max_sectors):
+    """Returns (charges [nsec, nq], dims [nsec], discarded weight, ||x||)."""
+    ns = _i32()
+    q = np.zeros(max_sectors * nq, dtype=np.int32)
+    d = np.zeros(max_sectors, dtype=np.int32)
+    disc, nrm = C.c_double(), C.c_double()
+    _check(_lib.heff_svd_truncate(s, int(m_max), float(cutoff), C.byref(ns), q.ctypes.data_as(_P(_i32)),
+                                  d.ctypes.data_as(_P(_i32)), C.byref(disc), C.byref(nrm)), "heff_svd_truncate")
+    n = ns.value
+    return q[:n * nq].reshape(n, nq), d[:n], disc.value, nrm.value
+
+
+def heff_svd_singular_values(s, n):
+    out = np.zeros(n, dtype=np.float64)
+    _check(_lib.heff_svd_singular_values(s, out.ctypes.data_as(_P(C.c_double))), "heff_svd_singular_values")
+    return out
+
+
+def heff_svd_write(s, A_layout, B_layout, A, B, absorb_right, ws, stream=None):
+    _check(_lib.heff_svd_write(s, A_layout, B_layout, _ptr(A), _ptr(B), 1 if absorb_right else 0, _ptr(ws),
+                               _nbytes(ws), _stream(stream)), "heff_svd_write")
+
+
+def heff_svd_destroy(s):
+    _lib.heff_svd_destroy(s)
 
 
 def heff_grad_plan_create(L, W1, W2, R, x, W1_host, W2_host):
