@@ -73,7 +73,8 @@ def test_svd_split_matches_oracle(name, m_max, cutoff, absorb_right):
         A, B = A.cpu().numpy(), B.cpu().numpy()
         assert not np.isnan(A).any() and not np.isnan(B).any()
         y = _product(A_l, B_l, A, B, x_l)
-        y_o = x_l.assemble(lambda k: omps.two_site(A_o, B_o).blocks[k])
+        x_trunc = omps.two_site(A_o, B_o)
+        y_o = x_l.assemble(lambda k: x_trunc.blocks[k])
         err = np.linalg.norm(y - y_o) / np.linalg.norm(y_o)
         print(f"{name} m_max={m_max}: kept {int(d.sum())}, sweeps {sweeps}, discarded {disc:.3e}, "
               f"product rel err {err:.2e}")
