@@ -311,6 +311,18 @@ int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1, const voi
                        const void* x, void* y, void* stream);
 
 /*
+ * heff_plan_autotune -- choose the output tile width (N = 256 or 128 columns) of each of
+ * the two tensor-core GEMMs by timing both on the given inputs (which must be valid
+ * tensors for the plan; y and the workspace are overwritten) and keep the faster one in
+ * the plan.  tn_out (host, may be NULL) receives the chosen widths {GEMM 1, GEMM 2}.
+ * No-op for the FP64 precision.  Synchronises (event timing); call it before capturing
+ * applies into a CUDA graph.
+ */
+int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                       const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream,
+                       int32_t* tn_out);
+
+/*
  * Phase timers (the time breakdown of Section VI / Fig. 7, on the GPU): when enabled,
  * every compute call records CUDA events on its stream around its phases.
  * heff_plan_timings waits for the last call's final event and writes the milliseconds

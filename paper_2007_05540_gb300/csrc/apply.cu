@@ -242,7 +242,7 @@ int plan_upload(heff_plan* p) {
     if ((rc = upload(p->pack, &p->d_pack)) != HEFF_OK) return rc;
     if ((rc = upload(p->mix, &p->d_mix)) != HEFF_OK) return rc;
     if ((rc = upload(p->terms, &p->d_terms)) != HEFF_OK) return rc;
-    for (GemmList* g : {&p->g1, &p->g2}) {
+    for (GemmList* g : {&p->g1, &p->g2, &p->g1_alt, &p->g2_alt}) {
         if ((rc = upload(g->tasks, &g->d_tasks)) != HEFF_OK) return rc;
         if ((rc = upload(g->segs, &g->d_segs)) != HEFF_OK) return rc;
     }
@@ -259,6 +259,8 @@ void plan_free_device(heff_plan* p) {
         if (p->ev[k]) { cudaEventDestroy(static_cast<cudaEvent_t>(p->ev[k])); p->ev[k] = nullptr; }
     cudaFree(p->d_pack); cudaFree(p->d_mix); cudaFree(p->d_terms);
     cudaFree(p->g1.d_tasks); cudaFree(p->g1.d_segs); cudaFree(p->g2.d_tasks); cudaFree(p->g2.d_segs);
+    cudaFree(p->g1_alt.d_tasks); cudaFree(p->g1_alt.d_segs); cudaFree(p->g2_alt.d_tasks); cudaFree(p->g2_alt.d_segs);
+    p->g1_alt.d_tasks = p->g2_alt.d_tasks = nullptr; p->g1_alt.d_segs = p->g2_alt.d_segs = nullptr;
     p->d_pack = nullptr; p->d_mix = nullptr; p->d_terms = nullptr;
     p->g1.d_tasks = p->g2.d_tasks = nullptr; p->g1.d_segs = p->g2.d_segs = nullptr;
 }
@@ -448,6 +450,56 @@ extern "C" int heff_apply_batched(heff_plan* plan, const void* L, const void* W1
     plan->ev_prepare = true;
     if ((rc = do_prepare(plan, L, W1, W2, R, workspace, stream))) return rc;
     return do_matvec(plan, x, y, nbatch, workspace, stream);
+}
+
+// Tile-shape autotuner: time each GEMM with the N = 256 and N = 128 task lists on the
+// caller's inputs and keep the faster one per GEMM (tensor-core precisions only).
+extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                                  const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream,
+                                  int32_t* tn_out) {
+    heff::clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_autotune: null argument");
+    int rc = check_ws(plan, workspace, workspace_bytes);
+    if (rc) return rc;
+    if (plan->opts.precision != HEFF_PREC_FP64 && !plan->g1_alt.tasks.empty()) {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const void* xs[1] = {x};
+        void* ys[1] = {y};
+        if ((rc = heff::launch_mix(plan, L, W1, W2, R, workspace, stream))) return rc;
+        if ((rc = heff::launch_pack_batch(plan, xs, 1, workspace, stream))) return rc;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int which = 1; which <= 2; ++which) {
+            heff::GemmList& act = which == 1 ? plan->g1 : plan->g2;
+            heff::GemmList& alt = which == 1 ? plan->g1_alt : plan->g2_alt;
+            float ms[2] = {0.f, 0.f};
+            for (int v = 0; v < 2; ++v) {
+                if (v == 1) std::swap(act, alt);
+                if ((rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream))) break;   // warm-up
+                CK(cudaEventRecord(e0, st));
+                for (int r = 0; r < 3 && !rc; ++r) rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream);
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(&ms[v], e0, e1));
+                if (v == 1) std::swap(act, alt);
+            }
+            if (rc) break;
+            if (ms[1] < ms[0]) std::swap(act, alt);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        plan->stats[3] = (int64_t)plan->g1.tasks.size();
+        plan->stats[4] = (int64_t)plan->g2.tasks.size();
+        plan->stats[15] = plan->g1.tn;
+        plan->stats[22] = plan->g2.tn;
+    }
+    if (tn_out) {
+        tn_out[0] = plan->g1.tn;
+        tn_out[1] = plan->g2.tn;
+    }
+    return HEFF_OK;
 }
 
 extern "C" int heff_plan_set_timing(heff_plan* plan, int32_t enable) {

@@ -158,7 +158,8 @@ struct heff_plan {
     heff::PackTile* d_pack = nullptr;
     heff::MixTile* d_mix = nullptr;
     heff::MixTerm* d_terms = nullptr;
-    heff::GemmList g1, g2;
+    heff::GemmList g1, g2;            // active task lists
+    heff::GemmList g1_alt, g2_alt;    // the other tile width (tensor-core paths), see heff_plan_autotune
     int64_t stats[24] = {0};
     // tensor-map cache for the tensor-core path (keyed by workspace pointer)
     void* tmap_ws = nullptr;

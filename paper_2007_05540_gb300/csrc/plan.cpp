@@ -349,11 +349,10 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                                       r0, std::min(MIX_ROWS, rows - r0), tb, (int32_t)sg.terms.size(), 1});
             }
         }
-        // ---- GEMM task lists
-        const bool tc = opts->precision != HEFF_PREC_FP64;
-        const int TM = tc ? 128 : 64, TN = tc ? 256 : 64;
-        P->g1.tm = P->g2.tm = TM;
-        P->g1.tn = P->g2.tn = TN;
+        // ---- GEMM task lists for one tile shape TM x TN
+        auto build_lists = [&](int TM, int TN, heff::GemmList& G1, heff::GemmList& G2) -> bool {
+        G1.tm = G2.tm = TM;
+        G1.tn = G2.tn = TN;
         // GEMM 1: rows of a row group x columns of one e-group, written into T
         for (auto& rg : rgs) {
             const QSec& qs = Q[rg.q];
@@ -363,11 +362,11 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             const CGroup* crow = nullptr;
             for (auto& g : qp.cg) if (g.s == rg.t1 && g.sec == rg.ip) crow = &g;
             if (!crow) continue;
-            int32_t sb = (int32_t)P->g1.segs.size();
+            int32_t sb = (int32_t)G1.segs.size();
             int64_t klen = 0, kuse = 0;
             for (auto& sg : rg.segs) {
                 const CGroup& g = qs.cg[sg.cg];
-                P->g1.segs.push_back({g.col, (int32_t)pad_up(g.dim, KPAD)});
+                G1.segs.push_back({g.col, (int32_t)pad_up(g.dim, KPAD)});
                 klen += pad_up(g.dim, KPAD);
                 kuse += g.dim;
             }
@@ -389,9 +388,9 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                         t.n_zero = (n0 + TN >= ge.dim) ? (int32_t)(pad_up(ge.dim, KPAD) - ge.dim) : 0;
                         t.seg_begin = sb;
                         t.seg_count = sc;
-                        P->g1.tasks.push_back(t);
-                        P->g1.flops += 2.0 * t.m * t.n * klen;
-                        P->g1.useful += 2.0 * t.m * t.n * kuse;
+                        G1.tasks.push_back(t);
+                        G1.flops += 2.0 * t.m * t.n * klen;
+                        G1.useful += 2.0 * t.m * t.n * kuse;
                     }
             }
         }
@@ -400,20 +399,20 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             const QSec& qs = Q[rw.q];
             const CGroup& ge = qs.eg[rw.eg];
             for (auto& gc : qs.cg) {
-                int32_t sb = (int32_t)P->g2.segs.size();
+                int32_t sb = (int32_t)G2.segs.size();
                 int64_t klen = 0, kuse = 0;
                 for (auto& sg : rw.segs) {
                     if (!present(sg.q_src, gc.s, sg.wm)) continue;
                     auto it = qs.toff.find({sg.wm, sg.eg_src});
                     if (it == qs.toff.end()) continue;
                     int32_t len = (int32_t)pad_up(Q[sg.q_src].eg[sg.eg_src].dim, KPAD);
-                    P->g2.segs.push_back({it->second, len});
+                    G2.segs.push_back({it->second, len});
                     klen += len;
                     kuse += Q[sg.q_src].eg[sg.eg_src].dim;
                 }
-                int32_t sc = (int32_t)P->g2.segs.size() - sb;
+                int32_t sc = (int32_t)G2.segs.size() - sb;
                 int64_t yoff = x->offset_of({gc.sec, gc.s, ge.s, ge.sec});
-                if (yoff < 0) { delete P; return fail(HEFF_ERR_CHARGE_MISMATCH, "internal: y block missing"); }
+                if (yoff < 0) return false;
                 for (int m0 = 0; m0 < gc.dim; m0 += TM)
                     for (int n0 = 0; n0 < ge.dim; n0 += TN) {
                         heff::GemmTask t{};
@@ -426,20 +425,21 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                         t.n_zero = 0;
                         t.seg_begin = sb;
                         t.seg_count = sc;
-                        P->g2.tasks.push_back(t);
-                        P->g2.flops += 2.0 * t.m * t.n * klen;
-                        P->g2.useful += 2.0 * t.m * t.n * kuse;
+                        G2.tasks.push_back(t);
+                        G2.flops += 2.0 * t.m * t.n * klen;
+                        G2.useful += 2.0 * t.m * t.n * kuse;
                     }
             }
         }
-        // longest tasks first (LPT order for the persistent kernels)
-        for (heff::GemmList* g : {&P->g1, &P->g2}) {
+        // longest tasks first (LPT order for the persistent kernels); a tile's tensor time
+        // scales with its padded K and its MMA width (n rounded up to 16)
+        for (heff::GemmList* g : {&G1, &G2}) {
             std::vector<int64_t> work(g->tasks.size());
             std::vector<size_t> ord(g->tasks.size());
             for (size_t t = 0; t < g->tasks.size(); ++t) {
                 int64_t k = 0;
                 for (int s = 0; s < g->tasks[t].seg_count; ++s) k += g->segs[g->tasks[t].seg_begin + s].klen;
-                work[t] = k;
+                work[t] = k * ((g->tasks[t].n + 15) / 16 * 16);
                 ord[t] = t;
             }
             std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
@@ -448,6 +448,15 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             for (size_t t : ord) sorted.push_back(g->tasks[t]);
             g->tasks.swap(sorted);
         }
+        return true;
+        };
+        const bool tc = opts->precision != HEFF_PREC_FP64;
+        if (!build_lists(tc ? 128 : 64, tc ? 256 : 64, P->g1, P->g2) ||
+            (tc && !build_lists(128, 128, P->g1_alt, P->g2_alt))) {
+            delete P;
+            return fail(HEFF_ERR_CHARGE_MISMATCH, "internal: y block missing");
+        }
+        const int TM = P->g1.tm, TN = P->g1.tn;
         // ---- workspace layout
         auto al = [](size_t v) { return (v + 255) / 256 * 256; };
         const size_t e = (size_t)P->esize * P->planes;

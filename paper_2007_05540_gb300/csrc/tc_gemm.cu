@@ -377,14 +377,13 @@ int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, u
     return HEFF_OK;
 }
 
-// Kernel configuration: N tile 256 (two TMEM accumulators = 512 columns), 64-byte K
-// blocks, 4-stage ring (4 x 48 KB).
-constexpr int TN_TC = 256;
-constexpr int STAGES_TC = 4;
+// Kernel configurations: 64-byte K blocks; N tile 256 with a 4-stage ring (4 x 48 KB,
+// 512 TMEM columns) or N tile 128 with a 6-stage ring (6 x 32 KB, 256 TMEM columns).
 constexpr int SWZ_TC = 64;
 
-template <int PREC>
+template <int PREC, int TN_TC>
 int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
+    constexpr int STAGES_TC = TN_TC == 256 ? 4 : 6;
     using S = Smem<TN_TC, STAGES_TC, SWZ_TC>;
     auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES_TC, SWZ_TC>;
     static bool attr = false;
@@ -454,8 +453,12 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
 
 int launch_tc_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (p->opts.precision == HEFF_PREC_BF16X3) return launch_tc_t<HEFF_PREC_BF16X3>(p, which, ws, y, nbatch, st);
-    return launch_tc_t<HEFF_PREC_TF32X3>(p, which, ws, y, nbatch, st);
+    const bool wide = (which == 1 ? p->g1.tn : p->g2.tn) == 256;
+    if (p->opts.precision == HEFF_PREC_BF16X3)
+        return wide ? launch_tc_t<HEFF_PREC_BF16X3, 256>(p, which, ws, y, nbatch, st)
+                    : launch_tc_t<HEFF_PREC_BF16X3, 128>(p, which, ws, y, nbatch, st);
+    return wide ? launch_tc_t<HEFF_PREC_TF32X3, 256>(p, which, ws, y, nbatch, st)
+                : launch_tc_t<HEFF_PREC_TF32X3, 128>(p, which, ws, y, nbatch, st);
 }
 
 }  // namespace heff

@@ -83,6 +83,7 @@ _sig = {
     "heff_env_plan_destroy": (None, [_vp]),
     "heff_lanczos_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
     "heff_lanczos": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
+    "heff_plan_autotune": (C.c_int, [_vp] * 8 + [_sz, _vp, _P(_i32)]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
     "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
     "heff_last_error": (C.c_char_p, []),
@@ -368,6 +369,14 @@ def heff_apply_noalloc(plan, L, W1, W2, R, x, y, stream=None):
     calls that overlap on the GPU race on that shared workspace."""
     _check(_lib.heff_apply_noalloc(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y),
                                    _stream(stream)), "heff_apply_noalloc")
+
+
+def heff_plan_autotune(plan, L, W1, W2, R, x, y, ws, stream=None):
+    """Pick the faster N tile (256 or 128) per GEMM on these inputs; returns (tn1, tn2)."""
+    tn = (_i32 * 2)()
+    _check(_lib.heff_plan_autotune(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y), _ptr(ws),
+                                   _nbytes(ws), _stream(stream), tn), "heff_plan_autotune")
+    return int(tn[0]), int(tn[1])
 
 
 def heff_plan_set_timing(plan, enable=True):

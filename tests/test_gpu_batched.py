@@ -1,0 +1,103 @@
+"""Batched applies (many x sharing L, W1, W2, R), the tile autotuner and CUDA-graph capture.
+
+* heff_plan_autotune picks a tile width per GEMM; the results are bitwise unchanged (a
+  tile's K accumulation order does not depend on the N tiling);
+* heff_apply_batched captured once in a CUDA graph and replayed gives bitwise the
+  results of the uncaptured call, and each batch entry matches the oracle;
+* the same at the electron workload's full size with 32 vectors (sampled sectors).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import heff as oh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2007_05540_gb300 import heff              # noqa: E402
+from tests.helpers import library_problem, oracle_flat  # noqa: E402
+
+
+def _setup(name, nb, prec="bf16x3"):
+    w = wl.workload_by_name(name)
+    lays, bufs = library_problem(w, batches=tuple(range(nb)))
+    plan = heff.Plan(*lays, bufs["W1"], bufs["W2"], prec, "f32", max_batch=nb)
+    d = {k: torch.from_numpy(np.asarray(bufs[k])).to("cuda", torch.float32) for k in ("L", "W1", "W2", "R")}
+    xs = [torch.from_numpy(x).to("cuda", torch.float32) for x in bufs["x"]]
+    return w, lays, plan, d, xs
+
+
+def _batched(plan, d, xs, ws):
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    heff.heff_apply_batched(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs, ys, ws)
+    torch.cuda.synchronize()
+    return ys
+
+
+def test_autotune_keeps_results_bitwise():
+    w, lays, plan, d, xs = _setup("spin_m1024", 1)
+    ws = plan.workspace()
+    before = _batched(plan, d, xs, ws)[0].cpu().numpy()
+    y = torch.empty_like(xs[0])
+    tn = heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs[0], y, ws)
+    assert all(t in (128, 256) for t in tn)
+    after = _batched(plan, d, xs, ws)[0].cpu().numpy()
+    print("autotuned tile widths", tn)
+    assert np.array_equal(before, after)
+
+
+def test_batched_graph_capture_matches_eager_and_oracle():
+    nb = 4
+    w, lays, plan, d, xs = _setup("electron_m256", nb)
+    ws = plan.workspace()
+    y = torch.empty_like(xs[0])
+    heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs[0], y, ws)
+    eager = [t.cpu().numpy() for t in _batched(plan, d, xs, ws)]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):      # warm-up on the capture stream
+        heff.heff_apply_batched(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs, ys, ws, stream)
+    torch.cuda.current_stream().wait_stream(stream)
+    torch.cuda.synchronize()
+    for t in ys:
+        t.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        heff.heff_apply_batched(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs, ys, ws, stream)
+    for _ in range(2):
+        for t in ys:
+            t.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for b in range(nb):
+            assert np.array_equal(ys[b].cpu().numpy(), eager[b])
+    for b in range(nb):
+        L, W1, W2, R, x = oh.problem_from_workload(w, b)
+        ref = oracle_flat(lays[4], oh.heff_apply(L, W1, W2, R, x))
+        err = np.linalg.norm(eager[b] - ref) / np.linalg.norm(ref)
+        assert err < 1e-3, err
+
+
+def test_electron_full_size_batch_of_32_sampled():
+    nb = 32
+    w, lays, plan, d, xs = _setup("electron_m2048", nb)
+    ws = plan.workspace()
+    ys = _batched(plan, d, xs, ws)
+    keep = {0, 30, 60}
+    mask = np.zeros(lays[4].nelem, dtype=bool)
+    for key, off, size in lays[4].blocks():
+        if key[0] in keep:
+            mask[off:off + size] = True
+    for b in (0, 17, 31):
+        L, W1, W2, R, x = oh.problem_from_workload(w, b)
+        ref = oracle_flat(lays[4], oh.heff_apply(L, W1, W2, R, x, left_sectors=keep))
+        yb = ys[b].double().cpu().numpy()
+        assert not np.isnan(yb).any()
+        err = np.linalg.norm(yb[mask] - ref[mask]) / np.linalg.norm(ref[mask])
+        print(f"electron m=2048 batch entry {b}: rel err {err:.2e}")
+        assert err < 1e-3
