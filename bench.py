@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the planner's default tile widths (for profiling: serialised launches under a "
+                         "profiler would time the candidates differently)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (other precisions, eigensolver, SVD, batched graph)")
     return ap.parse_args()
 
 
@@ -154,6 +159,128 @@ def cpu_baseline(name, seconds, batch=0):
             "tflops": rate / 1e12}
 
 
+# ------------------------------------------------------------------ secondary measurements
+def _events_ms(fn, n, stream, flush=None):
+    """Mean CUDA-event time of fn() on `stream` over n runs (L2 flushed before each)."""
+    import torch
+    ts = []
+    for _ in range(n):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
+def extras(args, w, lays, bufs, dev, stream, flush, value):
+    """Same workload in the other precisions, the eigensolver step around the apply, the
+    SVD truncation, and the batched electron workload replayed from a captured graph."""
+    import torch
+    from paper_2007_05540_gb300 import heff
+    Ll, W1l, W2l, Rl, xl = lays
+    out = {}
+    # other matvec precisions on the same inputs
+    rates = {args.precision: value}
+    for prec in ("bf16x3", "tf32x3", "fp64"):
+        if prec in rates:
+            continue
+        io = "f64" if prec == "fp64" else "f32"
+        dt = torch.float64 if io == "f64" else torch.float32
+        P = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, io)
+        d = {k: torch.from_numpy(np.asarray(v)).to(dev, dt) for k, v in bufs.items()}
+        ws = P.workspace(dev)
+        y = torch.empty_like(d["x"])
+        if prec != "fp64":
+            heff.heff_plan_autotune(P.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
+
+        def f(P=P, d=d, y=y, ws=ws):
+            heff.heff_apply(P.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
+        n = 3 if prec == "fp64" else 10
+        for _ in range(2):
+            f()
+        rates[prec] = 1000.0 / _events_ms(f, n, stream, flush)
+        del P, d, ws, y
+    out["applies_per_s"] = rates
+    out["speedup_vs_fp64_gpu"] = {p: rates[p] / rates["fp64"] for p in rates if p != "fp64"}
+
+    # eigensolver step: FP64 Lanczos (30 iterations) with BF16x3 and with FP64 matvecs,
+    # the FP64 Rayleigh quotient of the mixed Ritz vector, then the block SVD truncation
+    n_iter = 30
+    d64 = {k: torch.from_numpy(np.asarray(bufs[k])).to(dev, torch.float64) for k in ("L", "W1", "W2", "R")}
+    x0 = torch.from_numpy(np.asarray(bufs["x"])).to(dev, torch.float64)
+    res = {}
+    for prec in ("bf16x3", "fp64"):
+        P = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, "f64")
+        ws = P.workspace(dev)
+        lz = torch.empty(heff.heff_lanczos_workspace_size(P.handle, n_iter), dtype=torch.uint8, device=dev)
+        xv = torch.empty_like(x0)
+        r = torch.zeros(3 + 2 * (n_iter + 1), dtype=torch.float64, device=dev)
+
+        def f(P=P, ws=ws, lz=lz, xv=xv, r=r):
+            heff.heff_lanczos(P.handle, d64["L"], d64["W1"], d64["W2"], d64["R"], x0, n_iter, xv, r, ws, lz, stream)
+        f()
+        ms = _events_ms(f, 1 if prec == "fp64" else 3, stream)
+        res[prec] = (ms, float(r[0].item()), xv, P, ws)
+    ms_b, th_b, xb, _, _ = res["bf16x3"]
+    ms_f, th_f, _, P64, ws64 = res["fp64"]
+    y = torch.empty_like(xb)
+    heff.heff_apply(P64.handle, d64["L"], d64["W1"], d64["W2"], d64["R"], xb, y, ws64, stream)
+    torch.cuda.synchronize()
+    th_rq = float(torch.dot(xb, y) / torch.dot(xb, xb))
+    out["lanczos30"] = {
+        "ms_bf16x3": ms_b, "ms_fp64": ms_f, "speedup": ms_f / ms_b,
+        "ritz_bf16x3": th_b, "ritz_fp64": th_f, "rq_fp64_of_bf16x3_vector": th_rq,
+        "rel_diff_ritz": abs(th_b - th_f) / abs(th_f), "rel_diff_refined": abs(th_rq - th_f) / abs(th_f),
+        "note": "same start vector; FP64 orthogonalisation and tridiagonal eigensolver in both"}
+    del res, y
+    s = heff.heff_svd_create(xl.handle)
+    sws = torch.empty(heff.heff_svd_workspace_size(s), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sweeps = heff.heff_svd_compute(s, xb, sws, stream)
+    q, dims, disc, nrm = heff.heff_svd_truncate(s, int(w.alpha_d.sum()), 1e-12, w.nq, 4096)
+    torch.cuda.synchronize()
+    out["svd_truncation"] = {"ms": (time.perf_counter() - t0) * 1e3, "jacobi_sweeps": int(sweeps),
+                             "kept": int(np.sum(dims)), "sectors": int(len(dims)), "discarded_weight": float(disc),
+                             "note": "FP64 one-sided Jacobi per charge block, host wall time incl. the sync"}
+    heff.heff_svd_destroy(s)
+    del sws, xb, d64, x0
+
+    # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles)
+    nb = 32
+    we, le, be = make_problem("electron_m2048", 0)
+    xs_host = [le[4].assemble(lambda k: we.x_block(k, b)) for b in range(nb)]
+    Pe = heff.Plan(*le, be["W1"], be["W2"], "bf16x3", "f32", max_batch=nb)
+    de = {k: torch.from_numpy(np.asarray(be[k])).to(dev, torch.float32) for k in ("L", "W1", "W2", "R")}
+    xs = [torch.from_numpy(v).to(dev, torch.float32) for v in xs_host]
+    ys = [torch.empty_like(v) for v in xs]
+    wse = Pe.workspace(dev)
+    tn = heff.heff_plan_autotune(Pe.handle, de["L"], de["W1"], de["W2"], de["R"], xs[0], ys[0], wse, stream)
+    cs = torch.cuda.Stream(device=dev)
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cs):
+        heff.heff_apply_batched(Pe.handle, de["L"], de["W1"], de["W2"], de["R"], xs, ys, wse, cs)
+    torch.cuda.current_stream().wait_stream(cs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cs):
+        heff.heff_apply_batched(Pe.handle, de["L"], de["W1"], de["W2"], de["R"], xs, ys, wse, cs)
+    for _ in range(3):
+        g.replay()
+    ms = _events_ms(g.replay, 10, torch.cuda.current_stream(), flush)
+    fl = Pe.flops_canonical
+    out["electron_m2048_batch32_graph"] = {
+        "applies_per_s": nb * 1000.0 / ms, "ms_per_batch": ms, "tile_n": list(tn),
+        "tflops_canonical": nb * fl / (ms * 1e-3) / 1e12, "flops_per_apply": fl,
+        "sectors": int(len(we.alpha_d)), "max_block": int(we.alpha_d.max()), "mpo_k": int(we.W1.shape[0])}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -184,7 +311,10 @@ def run_ours(args):
         heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
 
     # one-time plan setup (outside the timed region): tile width per GEMM by measurement
-    tile_n = heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
+    if args.no_autotune:
+        tile_n = (int(st[15]), int(st[22]) or int(st[15]))
+    else:
+        tile_n = heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
     st = plan.stats = heff.heff_plan_stats(plan.handle)
     heff.heff_plan_set_timing(plan.handle, True)
     for _ in range(max(args.warmup, 3)):
@@ -289,6 +419,8 @@ def run_ours(args):
         "roofline": roof,
         "clocks": ck,
     }
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "spin_m4096":
+        out["extras"] = extras(args, w, lays, bufs, dev, stream, flush, value)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
     if rank == 0:

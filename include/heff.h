@@ -136,9 +136,10 @@ int heff_plan_flops(const heff_plan* plan, double* canonical, double* executed);
  * Plan statistics for diagnostics, stats[24]: [0] charge sectors, [1] LW row groups,
  * [2] RW row groups, [3] GEMM-1 tasks, [4] GEMM-2 tasks, [5] pack tiles, [6] mix tiles,
  * [7] mix terms, [8] XT rows, [9] XT/LW pitch, [10] LW rows, [11] T rows, [12] T/RW
- * pitch, [13] RW rows, [14] tile M, [15] tile N, [16] canonical flops of the first
+ * pitch, [13] RW rows, [14] tile M, [15] GEMM-1 tile N, [16] canonical flops of the first
  * contraction, [17] of the second, [18] GEMM-1 flops over valid rows, columns and
- * unpadded K, [19] the same for GEMM 2, [20] GEMM-1 issued flops (padded K), [21] GEMM 2.
+ * unpadded K, [19] the same for GEMM 2, [20] GEMM-1 issued flops (padded K), [21] GEMM 2,
+ * [22] GEMM-2 tile N.
  */
 int heff_plan_stats(const heff_plan* plan, int64_t* stats /* [24] */);
 
@@ -242,11 +243,19 @@ void heff_env_plan_destroy(heff_env_plan* plan);
  *   R, W1, W2 (overwritten).  apply_ws: plan workspace; grad_ws >= heff_grad_workspace_size
  *   bytes, 256-byte aligned.  The gradient with respect to a coupling J that W1, W2
  *   depend on is sum dW1 * dW1/dJ + sum dW2 * dW2/dJ (L and R held fixed).
+ * Intermediates: U = x.R and T1 = L.x (each about k d^2 times the size of x).  ws_limit = 0
+ * keeps them whole; ws_limit > 0 bounds the gradient workspace: the left sectors a' of x
+ * are split into chunks of consecutive sectors, and each chunk's U and T1 blocks are
+ * formed, consumed (dL of those sectors completely; dR and the W gradients as partial sums
+ * added in chunk order) and overwritten by the next chunk, so nothing is computed twice.
+ * A limit below the largest single sector's need (plus the small fixed part) fails with
+ * HEFF_ERR_WORKSPACE naming the minimum.  heff_grad_chunks reports the chunk count.
  */
 typedef struct heff_grad_plan heff_grad_plan;
 int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1, const heff_layout* W2,
                           const heff_layout* R, const heff_layout* x, const double* W1_host,
-                          const double* W2_host, heff_grad_plan** out);
+                          const double* W2_host, size_t ws_limit, heff_grad_plan** out);
+int heff_grad_chunks(const heff_grad_plan* g, int32_t* nchunks);
 int heff_grad_workspace_size(const heff_grad_plan* g, size_t* bytes);
 int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L, const double* W1,
                   const double* W2, const double* R, const double* x, double* rho, double* dx,

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const BTile* __restrict__ ti
                                                     const double* __restrict__ A, const double* __restrict__ B,
                                                     double* __restrict__ C, const double* __restrict__ coef1,
                                                     const double* __restrict__ coef2, double scale,
-                                                    const double* __restrict__ inv_scale) {
+                                                    const double* __restrict__ inv_scale, int accumulate) {
     __shared__ double As[16][64 + 1];
     if (inv_scale) scale /= inv_scale[0];
     __shared__ double Bs[16][64 + 1];
@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const BTile* __restrict__ ti
         if (r >= t.m) continue;
         for (int j = 0; j < 4; ++j) {
             const int c = tx * 4 + j;
-            if (c < t.n) C[t.c_off + (int64_t)r * t.ldc + c] = scale * acc[i][j];
+            if (c >= t.n) continue;
+            double* cp = C + t.c_off + (int64_t)r * t.ldc + c;
+            *cp = accumulate ? *cp + scale * acc[i][j] : scale * acc[i][j];
         }
     }
 }
@@ -127,11 +129,11 @@ __global__ void __launch_bounds__(256) block_dot_kernel(const BDot* __restrict__
 // out[j] = scale * sum of partial[d] for d in [off[j], off[j+1]) (dots sorted by output;
 // fixed order, deterministic)
 __global__ void gather_dots_kernel(const int32_t* __restrict__ off, const double* __restrict__ partial,
-                                   double* __restrict__ out, int nout, double scale) {
+                                   double* __restrict__ out, int nout, double scale, int accumulate) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int d = off[j]; d < off[j + 1]; ++d) s += partial[d];
-        out[j] = scale * s;
+        out[j] = accumulate ? out[j] + scale * s : scale * s;
     }
 }
 
@@ -141,7 +143,7 @@ int launch_bgemm(const BList& b, const double* A, const double* B, double* C, co
                  const double* coef2, double scale, void* stream, const double* inv_scale) {
     if (b.tiles.empty()) return HEFF_OK;
     bgemm_kernel<<<(unsigned)b.tiles.size(), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        b.d_tiles, b.d_prods, A, B, C, coef1, coef2, scale, inv_scale);
+        b.d_tiles, b.d_prods, A, B, C, coef1, coef2, scale, inv_scale, b.accumulate ? 1 : 0);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "bgemm launch: %s", cudaGetErrorString(e));
@@ -149,13 +151,13 @@ int launch_bgemm(const BList& b, const double* A, const double* B, double* C, co
 }
 
 int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const double* X, const double* Y,
-                      double* out, int nout, double* scratch, double scale, void* stream) {
+                      double* out, int nout, double* scratch, double scale, void* stream, bool accumulate) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (ndots > 0) {
         block_dot_kernel<<<ndots, 256, 0, st>>>(d_dots, X, Y, scratch);
         count_launches(1);
     }
-    gather_dots_kernel<<<(nout + 255) / 256, 256, 0, st>>>(d_off, scratch, out, nout, scale);
+    gather_dots_kernel<<<(nout + 255) / 256, 256, 0, st>>>(d_off, scratch, out, nout, scale, accumulate ? 1 : 0);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "block dots launch: %s", cudaGetErrorString(e));

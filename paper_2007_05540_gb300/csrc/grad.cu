@@ -24,22 +24,31 @@ using heff::BList;
 using heff::BProd;
 using heff::fail;
 
-struct heff_grad_plan {
+// One chunk of consecutive left sectors a' of x: its U and T1 blocks are formed, consumed
+// (dL of those sectors completely, dR and G partially) and discarded before the next
+// chunk, so the intermediates are never held whole when a workspace limit is set.
+struct GradChunk {
     BList U, T1, dL, dR;
     std::vector<BDot> gdots;
     std::vector<int32_t> goff;        // CSR over dense G indices
+    int64_t t_base = 0;               // T1 offset within the shared intermediate region
+    BDot* d_gdots = nullptr;
+    int32_t* d_goff = nullptr;
+};
+
+struct heff_grad_plan {
+    std::vector<GradChunk> chunks;
     std::vector<BDot> xdots;          // chunks of x for <x, x> and <x, y>
     std::vector<int32_t> xoff;
     std::vector<int32_t> w12_off;     // CSR over dense W12 indices: pairs (W1 idx, W2 idx)
     std::vector<int32_t> w12_terms;
     std::vector<int32_t> dw1_off, dw1_terms;   // per W1 entry: pairs (G idx, W2 idx)
     std::vector<int32_t> dw2_off, dw2_terms;   // per W2 entry: pairs (G idx, W1 idx)
-    int64_t nx = 0, nW1 = 0, nW2 = 0, ng = 0;
-    int64_t off_U = 0, off_T1 = 0, off_W12 = 0, off_G = 0, off_sc = 0, off_part = 0;
+    int64_t nx = 0, nR = 0, nW1 = 0, nW2 = 0, ng = 0;
+    int64_t off_U = 0, off_W12 = 0, off_G = 0, off_sc = 0, off_part = 0;
     size_t ws_bytes = 0;
     int64_t npart = 0;
     // device copies
-    BDot* d_gdots = nullptr; int32_t* d_goff = nullptr;
     BDot* d_xdots = nullptr; int32_t* d_xoff = nullptr;
     int32_t *d_w12_off = nullptr, *d_w12_terms = nullptr;
     int32_t *d_dw1_off = nullptr, *d_dw1_terms = nullptr, *d_dw2_off = nullptr, *d_dw2_terms = nullptr;
@@ -86,8 +95,12 @@ int up(const std::vector<T>& v, T** d) {
 }
 
 void free_all(heff_grad_plan* g) {
-    heff::blist_free(g->U); heff::blist_free(g->T1); heff::blist_free(g->dL); heff::blist_free(g->dR);
-    cudaFree(g->d_gdots); cudaFree(g->d_goff); cudaFree(g->d_xdots); cudaFree(g->d_xoff);
+    for (GradChunk& c : g->chunks) {
+        heff::blist_free(c.U); heff::blist_free(c.T1); heff::blist_free(c.dL); heff::blist_free(c.dR);
+        cudaFree(c.d_gdots); cudaFree(c.d_goff);
+        c.d_gdots = nullptr; c.d_goff = nullptr;
+    }
+    cudaFree(g->d_xdots); cudaFree(g->d_xoff);
     cudaFree(g->d_w12_off); cudaFree(g->d_w12_terms);
     cudaFree(g->d_dw1_off); cudaFree(g->d_dw1_terms); cudaFree(g->d_dw2_off); cudaFree(g->d_dw2_terms);
 }
@@ -96,7 +109,7 @@ void free_all(heff_grad_plan* g) {
 
 extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1, const heff_layout* W2,
                                      const heff_layout* R, const heff_layout* x, const double* W1_host,
-                                     const double* W2_host, heff_grad_plan** out) {
+                                     const double* W2_host, size_t ws_limit, heff_grad_plan** out) {
     heff::clear_error();
     if (!L || !W1 || !W2 || !R || !x || !W1_host || !W2_host || !out)
         return fail(HEFF_ERR_INVALID_ARG, "heff_grad_plan_create: null argument");
@@ -162,8 +175,12 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
             x_by_a[x->keys[b * 4]].push_back(b);
             x_by_b[x->keys[b * 4 + 3]].push_back(b);
         }
-        std::map<std::tuple<int, int, int, int, int>, int64_t> Uoff, Toff;   // block key -> offset
-        int64_t u = 0, t = 0;
+        using Key5 = std::tuple<int, int, int, int, int>;
+        struct Pending { Key5 key; int32_t ldc, m, n; BProd p; };
+        std::vector<Pending> ublk, tblk;
+        const int nsa = alpha.nsec;
+        std::vector<int64_t> need(nsa, 0);                        // U + T1 doubles per left sector
+        std::map<std::pair<int, int>, std::pair<int64_t, int64_t>> cnt;   // (a', b) -> (#T1, #U) blocks
         // U(i', t1, t2, wr, j) = x(i', t1, t2, j') R(j', wr, j)
         for (size_t rb = 0; rb < R->offsets.size(); ++rb) {
             const int jp = R->keys[rb * 3], wr = R->keys[rb * 3 + 1], j = R->keys[rb * 3 + 2];
@@ -172,13 +189,13 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
             for (size_t xb : it->second) {
                 const int ip = x->keys[xb * 4], t1 = x->keys[xb * 4 + 1], t2 = x->keys[xb * 4 + 2];
                 const int mi = alpha.dims[ip], mjp = beta.dims[jp], mj = beta.dims[j];
-                Uoff[{ip, t1, t2, wr, j}] = u;
                 BProd p{};
                 p.a_off = x->offsets[xb]; p.a_rs = mjp; p.a_cs = 1;
                 p.b_off = R->offsets[rb]; p.b_rs = mj; p.b_cs = 1;
                 p.K = mjp; p.c1 = -1; p.c2 = -1;
-                g->U.add_block(u, mj, mi, mj, {p});
-                u += (int64_t)mi * mj;
+                ublk.push_back({Key5{ip, t1, t2, wr, j}, mj, mi, mj, p});
+                need[ip] += (int64_t)mi * mj;
+                cnt[{ip, j}].second++;
             }
         }
         // T1(i', wl, s1, s2, j) = L(i', wl, i) x(i, s1, s2, j)
@@ -189,16 +206,61 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
             for (size_t xb : it->second) {
                 const int s1 = x->keys[xb * 4 + 1], s2 = x->keys[xb * 4 + 2], j = x->keys[xb * 4 + 3];
                 const int mip = alpha.dims[ip], mi = alpha.dims[i], mj = beta.dims[j];
-                Toff[{ip, wl, s1, s2, j}] = t;
                 BProd p{};
                 p.a_off = L->offsets[lb]; p.a_rs = mi; p.a_cs = 1;
                 p.b_off = x->offsets[xb]; p.b_rs = mj; p.b_cs = 1;
                 p.K = mi; p.c1 = -1; p.c2 = -1;
-                g->T1.add_block(t, mj, mip, mj, {p});
-                t += (int64_t)mip * mj;
+                tblk.push_back({Key5{ip, wl, s1, s2, j}, mj, mip, mj, p});
+                need[ip] += (int64_t)mip * mj;
+                cnt[{ip, j}].first++;
             }
         }
-        // dL(i', wl, i) = sum W12 U(i', t1, t2, wr, j) x(i, s1, s2, j)^T
+        // Chunks of consecutive left sectors whose U and T1 fit the limit (0: one chunk)
+        auto al = [](int64_t v) { return (v + 31) / 32 * 32; };
+        const int64_t CH = 1 << 16;
+        const int64_t nxd = (x->nelem + CH - 1) / CH;
+        int64_t total_g = 0;
+        for (auto& kv : cnt) total_g += kv.second.first * kv.second.second;
+        const int64_t fixed = 2 * al(g->ng) + 32 + al(std::max<int64_t>(total_g, nxd));
+        std::vector<int> chunk_of(nsa, 0);
+        int nchunk = 1;
+        if (ws_limit > 0) {
+            const int64_t avail = (int64_t)(ws_limit / sizeof(double)) - fixed - 64;
+            int64_t biggest = 0;
+            for (int q = 0; q < nsa; ++q) biggest = std::max(biggest, need[q]);
+            if (biggest > avail) {
+                delete g;
+                return fail(HEFF_ERR_WORKSPACE, "gradient workspace limit %zu bytes is below the minimum %lld bytes",
+                            ws_limit, (long long)((biggest + fixed + 64) * (int64_t)sizeof(double)));
+            }
+            int64_t cur = 0;
+            for (int q = 0; q < nsa; ++q) {
+                if (cur + need[q] > avail) { ++nchunk; cur = 0; }
+                chunk_of[q] = nchunk - 1;
+                cur += need[q];
+            }
+        }
+        g->chunks.resize(nchunk);
+        const bool streamed = nchunk > 1;
+        std::vector<int64_t> uo(nchunk, 0), to(nchunk, 0);
+        std::map<Key5, int64_t> Uoff, Toff;   // block key -> offset within its chunk's region
+        for (const Pending& pb : ublk) {
+            const int c = chunk_of[std::get<0>(pb.key)];
+            Uoff[pb.key] = uo[c];
+            g->chunks[c].U.add_block(uo[c], pb.ldc, pb.m, pb.n, {pb.p});
+            uo[c] += (int64_t)pb.m * pb.n;
+        }
+        for (int c = 0; c < nchunk; ++c) g->chunks[c].t_base = al(uo[c]);
+        for (const Pending& pb : tblk) {
+            const int c = chunk_of[std::get<0>(pb.key)];
+            Toff[pb.key] = g->chunks[c].t_base + to[c];
+            g->chunks[c].T1.add_block(g->chunks[c].t_base + to[c], pb.ldc, pb.m, pb.n, {pb.p});
+            to[c] += (int64_t)pb.m * pb.n;
+        }
+        int64_t region = 0;
+        for (int c = 0; c < nchunk; ++c) region = std::max(region, g->chunks[c].t_base + al(to[c]));
+        // dL(i', wl, i) = sum W12 U(i', t1, t2, wr, j) x(i, s1, s2, j)^T: complete within the
+        // chunk of i'
         for (size_t lb = 0; lb < L->offsets.size(); ++lb) {
             const int ip = L->keys[lb * 3], wl = L->keys[lb * 3 + 1], i = L->keys[lb * 3 + 2];
             std::vector<BProd> ps;
@@ -212,21 +274,22 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
                             for (int wr = 0; wr < kr; ++wr) {
                                 const int64_t e = gidx(wl, t1, t2, s1, s2, wr);
                                 if (w12[e].empty()) continue;
-                                auto uo = Uoff.find({ip, t1, t2, wr, j});
-                                if (uo == Uoff.end()) continue;
+                                auto uo_it = Uoff.find({ip, t1, t2, wr, j});
+                                if (uo_it == Uoff.end()) continue;
                                 BProd p{};
-                                p.a_off = uo->second; p.a_rs = mj; p.a_cs = 1;
+                                p.a_off = uo_it->second; p.a_rs = mj; p.a_cs = 1;
                                 p.b_off = x->offsets[xb]; p.b_rs = 1; p.b_cs = mj;   // x^T
                                 p.K = mj; p.c1 = (int32_t)e; p.c2 = -1;
                                 ps.push_back(p);
                             }
                 }
-            g->dL.add_block(L->offsets[lb], alpha.dims[i], alpha.dims[ip], alpha.dims[i], ps);
+            g->chunks[chunk_of[ip]].dL.add_block(L->offsets[lb], alpha.dims[i], alpha.dims[ip], alpha.dims[i], ps);
         }
-        // dR(j', wr, j) = sum W12 x(i', t1, t2, j')^T T1(i', wl, s1, s2, j)
+        // dR(j', wr, j) = sum W12 x(i', t1, t2, j')^T T1(i', wl, s1, s2, j): a sum over the
+        // chunks of i' (accumulated into a zeroed dR when there is more than one chunk)
         for (size_t rb = 0; rb < R->offsets.size(); ++rb) {
             const int jp = R->keys[rb * 3], wr = R->keys[rb * 3 + 1], j = R->keys[rb * 3 + 2];
-            std::vector<BProd> ps;
+            std::vector<std::vector<BProd>> ps(nchunk);
             auto it = x_by_b.find(jp);
             if (it != x_by_b.end())
                 for (size_t xb : it->second) {
@@ -237,19 +300,21 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
                             for (int s2 = 0; s2 < d2; ++s2) {
                                 const int64_t e = gidx(wl, t1, t2, s1, s2, wr);
                                 if (w12[e].empty()) continue;
-                                auto to = Toff.find({ip, wl, s1, s2, j});
-                                if (to == Toff.end()) continue;
+                                auto to_it = Toff.find({ip, wl, s1, s2, j});
+                                if (to_it == Toff.end()) continue;
                                 BProd p{};
                                 p.a_off = x->offsets[xb]; p.a_rs = 1; p.a_cs = mjp;   // x^T
-                                p.b_off = to->second; p.b_rs = mj; p.b_cs = 1;
+                                p.b_off = to_it->second; p.b_rs = mj; p.b_cs = 1;
                                 p.K = alpha.dims[ip]; p.c1 = (int32_t)e; p.c2 = -1;
-                                ps.push_back(p);
+                                ps[chunk_of[ip]].push_back(p);
                             }
                 }
-            g->dR.add_block(R->offsets[rb], beta.dims[j], beta.dims[jp], beta.dims[j], ps);
+            for (int c = 0; c < nchunk; ++c)
+                if (!streamed || !ps[c].empty())
+                    g->chunks[c].dR.add_block(R->offsets[rb], beta.dims[j], beta.dims[jp], beta.dims[j], ps[c]);
         }
-        // G dots: T1(i', wl, s1, s2, j) with U(i', t1, t2, wr, j), grouped by G index
-        std::vector<std::vector<BDot>> gd(g->ng);
+        for (GradChunk& c : g->chunks) c.dR.accumulate = streamed;
+        // G dots: T1(i', wl, s1, s2, j) with U(i', t1, t2, wr, j), grouped by chunk and G index
         std::map<std::pair<int, int>, std::vector<std::pair<std::tuple<int, int, int>, int64_t>>> Tby, Uby;
         for (auto& kv : Toff)
             Tby[{std::get<0>(kv.first), std::get<4>(kv.first)}].push_back(
@@ -257,36 +322,41 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
         for (auto& kv : Uoff)
             Uby[{std::get<0>(kv.first), std::get<4>(kv.first)}].push_back(
                 {{std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first)}, kv.second});
-        for (auto& kv : Tby) {
-            auto uit = Uby.find(kv.first);
-            if (uit == Uby.end()) continue;
-            const int64_t len = (int64_t)alpha.dims[kv.first.first] * beta.dims[kv.first.second];
-            for (auto& tb : kv.second)
-                for (auto& ub : uit->second) {
-                    const int wl = std::get<0>(tb.first), s1 = std::get<1>(tb.first), s2 = std::get<2>(tb.first);
-                    const int t1 = std::get<0>(ub.first), t2 = std::get<1>(ub.first), wr = std::get<2>(ub.first);
-                    gd[gidx(wl, t1, t2, s1, s2, wr)].push_back({tb.second, ub.second, len});
-                }
-        }
-        g->goff.push_back(0);
-        for (auto& v : gd) {
-            g->gdots.insert(g->gdots.end(), v.begin(), v.end());
-            g->goff.push_back((int32_t)g->gdots.size());
+        int64_t max_gd = 0;
+        for (int c = 0; c < nchunk; ++c) {
+            std::vector<std::vector<BDot>> gd(g->ng);
+            for (auto& kv : Tby) {
+                if (chunk_of[kv.first.first] != c) continue;
+                auto uit = Uby.find(kv.first);
+                if (uit == Uby.end()) continue;
+                const int64_t len = (int64_t)alpha.dims[kv.first.first] * beta.dims[kv.first.second];
+                for (auto& tb : kv.second)
+                    for (auto& ub : uit->second) {
+                        const int wl = std::get<0>(tb.first), s1 = std::get<1>(tb.first), s2 = std::get<2>(tb.first);
+                        const int t1 = std::get<0>(ub.first), t2 = std::get<1>(ub.first), wr = std::get<2>(ub.first);
+                        gd[gidx(wl, t1, t2, s1, s2, wr)].push_back({tb.second, ub.second, len});
+                    }
+            }
+            GradChunk& ch = g->chunks[c];
+            ch.goff.push_back(0);
+            for (auto& v : gd) {
+                ch.gdots.insert(ch.gdots.end(), v.begin(), v.end());
+                ch.goff.push_back((int32_t)ch.gdots.size());
+            }
+            max_gd = std::max<int64_t>(max_gd, (int64_t)ch.gdots.size());
         }
         // x chunks for the scalars
-        const int64_t CH = 1 << 16;
         g->xoff.push_back(0);
         for (int64_t o = 0; o < x->nelem; o += CH) g->xdots.push_back({o, o, std::min(CH, x->nelem - o)});
         g->xoff.push_back((int32_t)g->xdots.size());
-        // workspace layout (doubles)
-        auto al = [](int64_t v) { return (v + 31) / 32 * 32; };
+        g->nR = R->nelem;
+        // workspace layout (doubles): shared U/T1 region, W12, G, scalars, dot partials
         int64_t o = 0;
-        g->off_U = o; o += al(u);
-        g->off_T1 = o; o += al(t);
+        g->off_U = o; o += region;
         g->off_W12 = o; o += al(g->ng);
         g->off_G = o; o += al(g->ng);
         g->off_sc = o; o += 32;
-        g->npart = std::max<int64_t>((int64_t)g->gdots.size(), (int64_t)g->xdots.size());
+        g->npart = std::max<int64_t>(max_gd, (int64_t)g->xdots.size());
         g->off_part = o; o += al(g->npart);
         g->ws_bytes = (size_t)o * sizeof(double);
     } catch (const std::bad_alloc&) {
@@ -296,10 +366,12 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
         int rc = HEFF_OK;
-        for (BList* b : {&g->U, &g->T1, &g->dL, &g->dR})
-            if (!rc) rc = heff::blist_upload(*b);
-        if (!rc) rc = up(g->gdots, &g->d_gdots);
-        if (!rc) rc = up(g->goff, &g->d_goff);
+        for (GradChunk& c : g->chunks) {
+            for (BList* b : {&c.U, &c.T1, &c.dL, &c.dR})
+                if (!rc) rc = heff::blist_upload(*b);
+            if (!rc) rc = up(c.gdots, &c.d_gdots);
+            if (!rc) rc = up(c.goff, &c.d_goff);
+        }
         if (!rc) rc = up(g->xdots, &g->d_xdots);
         if (!rc) rc = up(g->xoff, &g->d_xoff);
         if (!rc) rc = up(g->w12_off, &g->d_w12_off);
@@ -318,6 +390,13 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
         cudaGetLastError();
     }
     *out = g;
+    return HEFF_OK;
+}
+
+extern "C" int heff_grad_chunks(const heff_grad_plan* g, int32_t* nchunks) {
+    heff::clear_error();
+    if (!g || !nchunks) return fail(HEFF_ERR_INVALID_ARG, "heff_grad_chunks: null argument");
+    *nchunks = (int32_t)g->chunks.size();
     return HEFF_OK;
 }
 
@@ -344,7 +423,7 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
                     grad_ws_bytes, g->ws_bytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* ws = static_cast<double*>(grad_ws);
-    double *U = ws + g->off_U, *T1 = ws + g->off_T1, *W12 = ws + g->off_W12, *G = ws + g->off_G;
+    double *Ureg = ws + g->off_U, *W12 = ws + g->off_W12, *G = ws + g->off_G;
     double *sc = ws + g->off_sc, *part = ws + g->off_part;
     // y = K x into dx (dx is overwritten by the gradient below)
     int rc = heff_apply(plan, L, W1, W2, R, x, dx, apply_ws, apply_ws_bytes, stream);
@@ -360,14 +439,24 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
     // W12 on the device from the current MPO values
     pair_sum_kernel<<<(int)((g->ng + 255) / 256), 256, 0, st>>>(g->d_w12_off, g->d_w12_terms, W1, W2, W12, g->ng);
     heff::count_launches(1);
-    if ((rc = heff::launch_bgemm(g->U, x, R, U, nullptr, nullptr, 1.0, stream))) return rc;
-    if ((rc = heff::launch_bgemm(g->T1, L, x, T1, nullptr, nullptr, 1.0, stream))) return rc;
-    if ((rc = heff::launch_bgemm(g->dL, U, x, dL, W12, nullptr, 1.0, stream, sc))) return rc;
-    if ((rc = heff::launch_bgemm(g->dR, x, T1, dR, W12, nullptr, 1.0, stream, sc))) return rc;
-    // G (scaled by 1/n afterwards through the pair sums: fold 1/n into G here)
-    if ((rc = heff::launch_block_dots(g->d_gdots, (int)g->gdots.size(), g->d_goff, T1, U, G, (int)g->ng, part, 1.0,
-                                      stream)))
-        return rc;
+    const bool streamed = g->chunks.size() > 1;
+    if (streamed) {   // dR and G are sums over the chunks
+        if (cudaMemsetAsync(dR, 0, (size_t)g->nR * sizeof(double), st) != cudaSuccess ||
+            cudaMemsetAsync(G, 0, (size_t)g->ng * sizeof(double), st) != cudaSuccess)
+            return fail(HEFF_ERR_CUDA, "heff_backward: memset failed");
+    }
+    for (const GradChunk& c : g->chunks) {
+        // U at the start of the shared region, T1 at the chunk's t_base: the lists hold
+        // offsets within the region
+        double *U = Ureg, *T1 = Ureg;
+        if ((rc = heff::launch_bgemm(c.U, x, R, U, nullptr, nullptr, 1.0, stream))) return rc;
+        if ((rc = heff::launch_bgemm(c.T1, L, x, T1, nullptr, nullptr, 1.0, stream))) return rc;
+        if ((rc = heff::launch_bgemm(c.dL, U, x, dL, W12, nullptr, 1.0, stream, sc))) return rc;
+        if ((rc = heff::launch_bgemm(c.dR, x, T1, dR, W12, nullptr, 1.0, stream, sc))) return rc;
+        if ((rc = heff::launch_block_dots(c.d_gdots, (int)c.gdots.size(), c.d_goff, T1, U, G, (int)g->ng, part, 1.0,
+                                          stream, streamed)))
+            return rc;
+    }
     // dW1 = G . W2, dW2 = G . W1 (then divided by n)
     pair_sum_kernel<<<(int)((g->nW1 + 255) / 256), 256, 0, st>>>(g->d_dw1_off, g->d_dw1_terms, G, W2, dW1, g->nW1);
     pair_sum_kernel<<<(int)((g->nW2 + 255) / 256), 256, 0, st>>>(g->d_dw2_off, g->d_dw2_terms, G, W1, dW2, g->nW2);

@@ -96,6 +96,7 @@ struct BList {
     BTile* d_tiles = nullptr;
     BProd* d_prods = nullptr;
     double flops = 0;
+    bool accumulate = false;   // C += result instead of C = result
     // append the tiles of an m x n output block whose products are given for the block origin
     void add_block(int64_t c_off, int32_t ldc, int32_t m, int32_t n, const std::vector<BProd>& ps);
 };
@@ -109,8 +110,9 @@ struct BDot {
     int64_t x_off, y_off;
     int64_t len;
 };
+// (accumulate: out[j] += instead of out[j] =)
 int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const double* X, const double* Y,
-                      double* out, int nout, double* scratch, double scale, void* stream);
+                      double* out, int nout, double* scratch, double scale, void* stream, bool accumulate = false);
 
 constexpr int MAXB = 64;   // batch entries per launch (kernel parameter arrays)
 struct PtrBatch { const void* p[MAXB]; };

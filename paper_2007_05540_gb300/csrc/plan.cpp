@@ -472,7 +472,7 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         st[3] = (int64_t)P->g1.tasks.size(); st[4] = (int64_t)P->g2.tasks.size();
         st[5] = (int64_t)P->pack.size(); st[6] = (int64_t)P->mix.size(); st[7] = (int64_t)P->terms.size();
         st[8] = P->rows_x; st[9] = P->ld_x; st[10] = P->rows_lw; st[11] = P->rows_t; st[12] = P->ld_t;
-        st[13] = P->rows_rw; st[14] = TM; st[15] = TN;
+        st[13] = P->rows_rw; st[14] = TM; st[15] = TN; st[22] = TN;
         st[18] = (int64_t)P->g1.useful; st[19] = (int64_t)P->g2.useful;
         st[20] = (int64_t)P->g1.flops; st[21] = (int64_t)P->g2.flops;
     } catch (const std::bad_alloc&) {

@@ -72,7 +72,8 @@ _sig = {
     "heff_svd_singular_values": (C.c_int, [_vp, _P(C.c_double)]),
     "heff_svd_write": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
     "heff_svd_destroy": (None, [_vp]),
-    "heff_grad_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _P(C.c_double), _P(_vp)]),
+    "heff_grad_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _P(C.c_double), _sz, _P(_vp)]),
+    "heff_grad_chunks": (C.c_int, [_vp, _P(C.c_int32)]),
     "heff_grad_workspace_size": (C.c_int, [_vp, _P(_sz)]),
     "heff_backward": (C.c_int, [_vp] * 13 + [_vp, _sz, _vp, _sz, _vp]),
     "heff_grad_plan_destroy": (None, [_vp]),
@@ -292,13 +293,21 @@ def heff_svd_destroy(s):
     _lib.heff_svd_destroy(s)
 
 
-def heff_grad_plan_create(L, W1, W2, R, x, W1_host, W2_host):
+def heff_grad_plan_create(L, W1, W2, R, x, W1_host, W2_host, ws_limit=0):
+    """Gradient plan; ws_limit > 0 bounds the workspace by streaming left-sector chunks."""
     w1 = np.ascontiguousarray(W1_host, dtype=np.float64)
     w2 = np.ascontiguousarray(W2_host, dtype=np.float64)
     out = _vp()
     _check(_lib.heff_grad_plan_create(L, W1, W2, R, x, w1.ctypes.data_as(_P(C.c_double)),
-                                      w2.ctypes.data_as(_P(C.c_double)), C.byref(out)), "heff_grad_plan_create")
+                                      w2.ctypes.data_as(_P(C.c_double)), int(ws_limit), C.byref(out)),
+           "heff_grad_plan_create")
     return out
+
+
+def heff_grad_chunks(g):
+    n = C.c_int32()
+    _check(_lib.heff_grad_chunks(g, C.byref(n)), "heff_grad_chunks")
+    return n.value
 
 
 def heff_grad_workspace_size(g):

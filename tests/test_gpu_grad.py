@@ -4,7 +4,10 @@ The oracle's gradients are pinned by central finite differences, Euler homogenei
 the closed form for dx (tests/test_oracle_eig_svd_dmrg_grad.py).  Here the GPU results
 (FP64 apply plan) must equal them to 1e-11 relative; the gradient with respect to the
 tagged J2 coupling (through W1 and W2 only) must equal a central difference of the GPU
-rho; with a BF16x3 apply plan only rho and dx carry the split-precision error.
+rho; with a BF16x3 apply plan only rho and dx carry the split-precision error.  With a
+workspace limit the intermediates are streamed in left-sector chunks: the results equal the
+unchunked ones (rho, dx and dL bitwise; dR and the W gradients, sums over the chunks, to
+1e-13), including at m = 4096, where the oracle's rho and Euler homogeneity also hold.
 """
 import numpy as np
 import pytest
@@ -28,13 +31,14 @@ def _dev(a):
 
 
 class GradRun:
-    def __init__(self, w, prec="fp64"):
+    def __init__(self, w, prec="fp64", ws_limit=0, problem=None, plan=None):
         self.w = w
-        self.lays, self.bufs = library_problem(w)
+        self.lays, self.bufs = problem if problem is not None else library_problem(w)
         Ll, W1l, W2l, Rl, xl = self.lays
-        self.plan = heff.Plan(Ll, W1l, W2l, Rl, xl, self.bufs["W1"], self.bufs["W2"], prec, "f64")
+        self.plan = plan if plan is not None else heff.Plan(Ll, W1l, W2l, Rl, xl, self.bufs["W1"], self.bufs["W2"],
+                                                            prec, "f64")
         self.g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle,
-                                            self.bufs["W1"], self.bufs["W2"])
+                                            self.bufs["W1"], self.bufs["W2"], ws_limit)
         self.aws = self.plan.workspace()
         self.gws = torch.empty(heff.heff_grad_workspace_size(self.g), dtype=torch.uint8, device="cuda")
 
@@ -128,3 +132,71 @@ def test_autograd_function():
     assert np.allclose(x.grad.cpu().numpy(), 3.0 * dx, rtol=0, atol=1e-14 * np.abs(dx).max() + 1e-300)
     assert np.allclose(ts["L"].grad.cpu().numpy(), 3.0 * dL)
     assert np.allclose(ts["W2"].grad.cpu().numpy(), 3.0 * dW2)
+
+
+def _chunked_limit(r_whole):
+    """The smallest accepted workspace limit on a 0.8x ladder below the whole size (the
+    most chunks); at least two chunks are required."""
+    lays, bufs = r_whole.lays, r_whole.bufs
+    Ll, W1l, W2l, Rl, xl = lays
+    lim = heff.heff_grad_workspace_size(r_whole.g)
+    best = None
+    while lim > 0:
+        lim = int(lim * 0.8)
+        try:
+            g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle,
+                                           bufs["W1"], bufs["W2"], lim)
+        except heff.HeffError as e:
+            assert e.code == -7
+            break
+        if heff.heff_grad_chunks(g) >= 2:
+            best = lim
+        heff.heff_grad_plan_destroy(g)
+    assert best is not None, "no limit gives two chunks"
+    return best
+
+
+def _compare_streamed(whole, streamed):
+    rho0, g0 = whole
+    rho1, g1 = streamed
+    assert rho1 == rho0
+    assert np.array_equal(g1[0], g0[0])                        # dx
+    assert np.array_equal(g1[1], g0[1])                        # dL: complete within a chunk
+    for k, a, b in zip(("dR", "dW1", "dW2"), g1[2:], g0[2:]):  # sums over the chunks
+        assert _rel(a, b) < 1e-13, (k, _rel(a, b))
+
+
+@pytest.mark.parametrize("name", ["spin_m200", "electron_m256"])
+def test_backward_streamed_chunks_equal_whole(name):
+    w = wl.workload_by_name(name)
+    whole = GradRun(w)
+    lim = _chunked_limit(whole)
+    st = GradRun(w, ws_limit=lim, problem=(whole.lays, whole.bufs), plan=whole.plan)
+    n = heff.heff_grad_chunks(st.g)
+    assert n >= 2 and heff.heff_grad_workspace_size(st.g) <= lim
+    print(name, "chunks", n, "workspace", heff.heff_grad_workspace_size(st.g), "of", heff.heff_grad_workspace_size(whole.g))
+    _compare_streamed(whole.run(), st.run())
+
+
+def test_backward_streamed_at_m4096():
+    w = wl.workload_by_name("spin_m4096")
+    whole = GradRun(w)
+    st = GradRun(w, ws_limit=256 << 20, problem=(whole.lays, whole.bufs), plan=whole.plan)
+    n = heff.heff_grad_chunks(st.g)
+    ws0, ws1 = heff.heff_grad_workspace_size(whole.g), heff.heff_grad_workspace_size(st.g)
+    print(f"m=4096 gradients: {n} chunks, workspace {ws1 / 1e6:.0f} MB instead of {ws0 / 1e6:.0f} MB")
+    assert n >= 2 and ws1 <= 256 << 20
+    r0, r1 = whole.run(), st.run()
+    _compare_streamed(r0, r1)
+    rho, (dx, dL, dR, dW1, dW2) = r1
+    b = whole.bufs
+    for g_, t_ in ((dL, b["L"]), (dR, b["R"]), (dW1, b["W1"]), (dW2, b["W2"])):
+        assert abs(float(np.dot(g_, t_)) - rho) < 1e-11 * abs(rho)
+    x0 = b["x"][0]
+    assert abs(float(np.dot(dx, x0))) < 1e-11 * abs(rho) * np.linalg.norm(x0)
+    L, W1, W2, R, x = oh.problem_from_workload(w)
+    y = oh.heff_apply(L, W1, W2, R, x)
+    rho_o = sum(float(np.vdot(x.blocks[k], y.blocks[k])) for k in x.blocks) / \
+        sum(float(np.vdot(v, v)) for v in x.blocks.values())
+    print(f"m=4096 rho {rho:.15f} oracle {rho_o:.15f}")
+    assert abs(rho - rho_o) < 1e-11 * abs(rho_o)

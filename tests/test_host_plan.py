@@ -109,3 +109,30 @@ def test_host_only_plan_refuses_compute():
     rc = heff._lib.heff_apply_prepared(P.handle, heff._ptr(t), heff._ptr(t + 1), heff._ptr(t), 128, None)
     assert rc == -3
     assert "without a CUDA device" in heff.heff_last_error()
+
+
+def test_gradient_workspace_limit_splits_left_sectors():
+    """A workspace limit streams the gradient intermediates in left-sector chunks; the
+    workspace stays within the limit, and a limit below one sector's need is refused."""
+    w = wl.workload_by_name("spin_m200")
+    lays, bufs = library_problem(w)
+    hs = [t.handle for t in lays]
+
+    def make(limit):
+        return heff.heff_grad_plan_create(*hs, bufs["W1"], bufs["W2"], limit)
+    g = make(0)
+    whole = heff.heff_grad_workspace_size(g)
+    assert heff.heff_grad_chunks(g) == 1
+    heff.heff_grad_plan_destroy(g)
+    last = 1
+    for frac in (0.75, 0.5, 0.4):
+        g = make(int(whole * frac))
+        n = heff.heff_grad_chunks(g)
+        assert heff.heff_grad_workspace_size(g) <= int(whole * frac)
+        assert n >= last and n >= 2
+        last = n
+        heff.heff_grad_plan_destroy(g)
+    with pytest.raises(heff.HeffError) as e:
+        make(int(whole * 0.05))
+    assert e.value.code == -7
+    assert "minimum" in heff.heff_last_error()
