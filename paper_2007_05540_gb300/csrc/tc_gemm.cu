@@ -14,6 +14,10 @@
 //   warp 1      allocates TMEM (2 x TN columns); one thread issues the MMAs
 //   warps 2..5  epilogue: TMEM -> registers -> global (T as hi/lo planes, or y)
 // Accumulators are double buffered so a tile's epilogue overlaps the next tile's MMAs.
+// T (GEMM 1) leaves through TMA: each warp splits 32 rows x 32 columns into hi/lo in
+// registers, writes them to a swizzled shared-memory box and issues bulk tensor stores;
+// quarters with fewer than 32 valid rows, and y (GEMM 2, per-block pitch), are stored
+// by the threads through a padded transpose.
 // Every mbarrier wait is bounded (about a second); on expiry the CTA raises the
 // workspace error flag, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
@@ -34,22 +38,26 @@ constexpr int TM = 128;
 constexpr long long WAIT_CYCLES = 3ll << 30;   // ~1.5 s at 2 GHz
 
 // Shared-memory ring: STAGES x {A_hi, A_lo (128 rows), B_hi, B_lo (TN rows)}, each row SWZ
-// bytes of one K block (SWZ = 64: 32 bf16 / 16 fp32; SWZ = 128: 64 bf16 / 32 fp32).
+// bytes of one K block (SWZ = 64: 32 bf16 / 16 fp32; SWZ = 128: 64 bf16 / 32 fp32), then
+// 8 KB per epilogue warp (TMA store boxes, or the 32 x 33 float transpose), then barriers.
 template <int TN, int STAGES, int SWZ>
 struct Smem {
     static constexpr int A_BYTES = TM * SWZ;
     static constexpr int B_BYTES = TN * SWZ;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
-    static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;    // epilogue transpose buffers
-    static constexpr int TOTAL = BAR_OFF + 256 + EPI_BYTES + 1024;   // + barriers, alignment slack
+    static constexpr int EPI_OFF = STAGES * STAGE_BYTES;  // 1024-byte aligned
+    static constexpr int EPI_WARP = 8192;
+    static constexpr int BAR_OFF = EPI_OFF + 4 * EPI_WARP;
+    static constexpr int TOTAL = BAR_OFF + 256 + 1024;    // + barriers, alignment slack
 };
+static_assert(32 * 33 * 4 <= 8192, "transpose buffer fits the epilogue slot");
 
 // TMA maps of one GEMM: the A operand with 64- and 128-row boxes, the B operand with 64-,
 // 128- and 256-row boxes (a tile loads the smallest box that covers its valid rows).
 struct TcMaps {
     CUtensorMap a[2];
     CUtensorMap b[3];
+    CUtensorMap c;      // T store map: 32 x 32 boxes (GEMM 1 only)
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -143,6 +151,24 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// Bulk tensor store of one shared-memory box; completion tracked by bulk async-groups.
+__device__ __forceinline__ void tma_store(const CUtensorMap* map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
@@ -167,6 +193,7 @@ struct TcArgs {
     int64_t a_batch_rows, b_batch_rows;   // row offset per batch entry
     char* C;                              // mode 0: T (hi plane base)
     int64_t c_batch_elems, c_plane_elems;
+    int c_batch_rows, c_plane_rows;       // the same in rows of the T store map
     PtrBatch y;                           // mode 1: outputs per batch entry
     int mode;                             // 0: write T planes, 1: write y
     int y_f64;                            // y element type (mode 1)
@@ -275,12 +302,19 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         }
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
-        // Each warp drains its 32 TMEM lanes (tile rows) 32 columns at a time: tcgen05.ld
-        // (thread = row), transpose through a padded 32 x 33 shared buffer, then store
-        // row by row with consecutive lanes on consecutive columns (full-sector writes).
+        // Each warp drains its 32 TMEM lanes (tile rows) 32 columns at a time (tcgen05.ld:
+        // thread = row).  T, full quarters: hi/lo split in registers, swizzled box in shared
+        // memory, two bulk tensor stores (hi plane, lo plane), double buffered for BF16X3.
+        // Otherwise: transpose through a padded 32 x 33 buffer and store row by row with
+        // consecutive lanes on consecutive columns.
+        using E = typename std::conditional<PREC == HEFF_PREC_BF16X3, __nv_bfloat16, float>::type;
+        constexpr int BOX = 32 * 32 * (int)sizeof(E);              // one plane of a 32 x 32 box
+        constexpr int NBUF = PREC == HEFF_PREC_BF16X3 ? 2 : 1;      // boxes in the 8 KB slot
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        float (*stage)[33] = reinterpret_cast<float (*)[33]>(smem + S::BAR_OFF + 256 + q * 32 * 33 * 4);
-        uint32_t tcount = 0;
+        uint8_t* slot = smem + S::EPI_OFF + q * S::EPI_WARP;
+        float (*stage)[33] = reinterpret_cast<float (*)[33]>(slot);
+        const uint32_t slot_s = su32(slot);
+        uint32_t tcount = 0, nstore = 0;
         for (long gi = blockIdx.x; gi < total; gi += gridDim.x, ++tcount) {
             const GemmTask t = g.tasks[gi % g.ntasks];
             const int brel = (int)(gi / g.ntasks), b = g.b0 + brel;
@@ -289,6 +323,12 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             tc_fence_after();
             const int ncols = t.n + t.n_zero;
             const int rows = t.m - q * 32 < 32 ? t.m - q * 32 : 32;   // valid rows of this warp
+            const bool boxed = g.mode == 0 && rows == 32;              // warp-uniform
+            int x0 = 0, yh = 0;
+            if (boxed) {
+                x0 = (int)(t.c_off % t.ldc);
+                yh = (int)(t.c_off / t.ldc) + q * 32 + b * g.c_batch_rows;
+            }
             for (int c0 = 0; c0 < ncols; c0 += 32) {
                 uint32_t raw[32];
                 if (t.seg_count > 0) {
@@ -298,12 +338,68 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     for (int i = 0; i < 32; ++i) raw[i] = 0u;
                 }
                 if (rows <= 0) continue;                       // warp-uniform
+                if (boxed) {
+                    // this buffer's previous bulk store must have finished reading it
+                    if (lane == 0) bulk_wait_read<NBUF - 1>();
+                    __syncwarp();
+                    const uint32_t hb = slot_s + (nstore % NBUF) * 2 * BOX, lb = hb + BOX;
+                    const int nv = t.n - c0;                   // valid columns in this chunk
+                    if constexpr (PREC == HEFF_PREC_BF16X3) {
+                        // row = lane: 64 bytes per plane, 16-byte chunk j at j ^ ((row >> 1) & 3)
+                        uint32_t h2[16], l2[16];
+#pragma unroll
+                        for (int p = 0; p < 16; ++p) {
+                            const float f0 = 2 * p < nv ? __uint_as_float(raw[2 * p]) : 0.f;
+                            const float f1 = 2 * p + 1 < nv ? __uint_as_float(raw[2 * p + 1]) : 0.f;
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+                            const __nv_bfloat162 l = __floats2bfloat162_rn(f0 - __low2float(h), f1 - __high2float(h));
+                            h2[p] = *reinterpret_cast<const uint32_t*>(&h);
+                            l2[p] = *reinterpret_cast<const uint32_t*>(&l);
+                        }
+                        const uint32_t ro = (uint32_t)lane * 64;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t o = ro + ((uint32_t)(j ^ ((lane >> 1) & 3)) << 4);
+                            st_shared_v4(hb + o, h2[4 * j], h2[4 * j + 1], h2[4 * j + 2], h2[4 * j + 3]);
+                            st_shared_v4(lb + o, l2[4 * j], l2[4 * j + 1], l2[4 * j + 2], l2[4 * j + 3]);
+                        }
+                    } else {
+                        // row = lane: 128 bytes per plane, 16-byte chunk j at j ^ (row & 7)
+                        uint32_t hv[32], lv[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float f = i < nv ? __uint_as_float(raw[i]) : 0.f;
+                            // round-to-nearest TF32 hi and lo (both exact for the MMA)
+                            const uint32_t h = (__float_as_uint(f) + 0x1000u) & 0xffffe000u;
+                            hv[i] = h;
+                            lv[i] = (__float_as_uint(f - __uint_as_float(h)) + 0x1000u) & 0xffffe000u;
+                        }
+                        const uint32_t ro = (uint32_t)lane * 128;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint32_t o = ro + ((uint32_t)(j ^ (lane & 7)) << 4);
+                            st_shared_v4(hb + o, hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
+                            st_shared_v4(lb + o, lv[4 * j], lv[4 * j + 1], lv[4 * j + 2], lv[4 * j + 3]);
+                        }
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store(&maps.c, hb, x0 + c0, yh);
+                        tma_store(&maps.c, lb, x0 + c0, yh + g.c_plane_rows);
+                        bulk_commit();
+                    }
+                    ++nstore;
+                    continue;
+                }
+                // the transpose buffer overlaps the store boxes: no store may still read them
+                if (lane == 0) bulk_wait_read<0>();
+                __syncwarp();
 #pragma unroll
                 for (int i = 0; i < 32; ++i) stage[lane][i] = __uint_as_float(raw[i]);
                 __syncwarp();
                 const int c = c0 + lane;                       // this lane's column
                 if (g.mode == 0) {
-                    using E = typename std::conditional<PREC == HEFF_PREC_BF16X3, __nv_bfloat16, float>::type;
                     E* hi = reinterpret_cast<E*>(g.C) + t.c_off + (int64_t)b * g.c_batch_elems + c;
                     E* lo = hi + g.c_plane_elems;
                     if (c < ncols) {
@@ -315,7 +411,6 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                                 hi[o] = h;
                                 lo[o] = __float2bfloat16_rn(f - __bfloat162float(h));
                             } else {
-                                // round-to-nearest TF32 hi and lo (both exact for the MMA)
                                 const float h = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xffffe000u);
                                 hi[o] = h;
                                 lo[o] = __uint_as_float((__float_as_uint(f - h) + 0x1000u) & 0xffffe000u);
@@ -338,6 +433,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
         }
+        if (lane == 0) bulk_wait_all();      // T complete before the CTA (and its boxes) go away
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -397,6 +494,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps);
     if (p->tmap_ws != ws) {
         // [0,1] LW (64, 128 rows)  [2,3,4] XT (64, 128, 256)  [5,6] T (64, 128)  [7,8,9] RW (64, 128, 256)
+        // [10] T store boxes: 32 rows x 32 elements (64-byte swizzle for bf16, 128-byte for fp32)
         struct { char* base; int64_t rows, ld; int slot, nbox; } ops[4] = {
             {w + p->off_lw, 2 * p->rows_lw, p->ld_x, 0, 2},
             {w + p->off_xt, 2 * B * p->rows_x, p->ld_x, 2, 3},
@@ -407,6 +505,9 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
                 int rc = make_map(&m[o.slot + k], o.base, PREC, (uint64_t)o.rows, (uint64_t)o.ld, 64u << k, SWZ_TC);
                 if (rc) return rc;
             }
+        int rc = make_map(&m[10], w + p->off_t, PREC, (uint64_t)(2 * B * p->rows_t), (uint64_t)p->ld_t, 32u,
+                          PREC == HEFF_PREC_BF16X3 ? 64 : 128);
+        if (rc) return rc;
         p->tmap_ws = ws;
     }
     const GemmList& gl = which == 1 ? p->g1 : p->g2;
@@ -415,6 +516,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
     const int sa = which == 1 ? 0 : 5, sb = which == 1 ? 2 : 7;
     maps.a[0] = m[sa]; maps.a[1] = m[sa + 1];
     maps.b[0] = m[sb]; maps.b[1] = m[sb + 1]; maps.b[2] = m[sb + 2];
+    maps.c = m[10];
     for (int b0 = 0; b0 < nbatch; b0 += MAXB) {
         const int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
         TcArgs g{};
@@ -430,6 +532,8 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
             g.C = w + p->off_t;
             g.c_batch_elems = p->rows_t * p->ld_t;
             g.c_plane_elems = B * p->rows_t * p->ld_t;
+            g.c_batch_rows = (int)p->rows_t;
+            g.c_plane_rows = (int)(B * p->rows_t);
             g.mode = 0;
         } else {
             g.a_plane_rows = B * p->rows_t; g.b_plane_rows = p->rows_rw;
