@@ -276,11 +276,18 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     sweeps = heff.heff_svd_compute(s, xb, sws, stream)
     q, dims, disc, nrm = heff.heff_svd_truncate(s, int(w.alpha_d.sum()), 1e-12, w.nq, 4096)
     torch.cuda.synchronize()
-    out["svd_truncation"] = {"ms": (time.perf_counter() - t0) * 1e3, "jacobi_sweeps": int(sweeps),
+    sw32, sw64 = heff.heff_svd_info(s)
+    out["svd_truncation"] = {"ms": (time.perf_counter() - t0) * 1e3, "jacobi_sweeps": {"fp32": sw32, "fp64": sw64},
                              "kept": int(np.sum(dims)), "sectors": int(len(dims)), "discarded_weight": float(disc),
-                             "note": "FP64 one-sided Jacobi per charge block, host wall time incl. the sync"}
+                             "note": "one-sided Jacobi per charge block: FP32 preconditioning sweeps, FP64 orthonormalisation and FP64 sweeps; host wall time incl. the sync"}
     heff.heff_svd_destroy(s)
     del sws, xb, d64, x0
+
+    # environment update (left side) onto a new bond of the same size with even charges,
+    # FP64 block products
+    out["env_update"] = env_update_timing(w, dev, stream)
+    # Rayleigh-quotient gradients: whole intermediates at m = 1024, streamed at m = 4096
+    out["backward"] = backward_timing(dev, stream)
 
     # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles)
     nb = 32
@@ -310,6 +317,72 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
         "tflops_canonical": nb * fl / (ms * 1e-3) / 1e12, "flops_per_apply": fl,
         "sectors": int(len(we.alpha_d)), "max_block": int(we.alpha_d.max()), "mpo_k": int(we.W1.shape[0])}
     return out
+
+
+def env_update_timing(w, dev, stream):
+    import torch
+    import workloads as wl
+    from workloads.fill import site_block
+    from paper_2007_05540_gb300 import heff
+    ones = lambda n: np.ones(n, dtype=np.int32)
+    m_new, nsec_new = int(w.alpha_d.sum()), int(len(w.alpha_d)) + 1
+    gq, gd = wl.binomial_sectors(m_new, nsec_new, 31, parity=0)
+    ph = w.phys
+    site_l = heff.Layout([(w.alpha_q, w.alpha_d, 1), (ph, ones(len(ph)), 1), (gq, gd, -1)])
+    W_l = heff.Layout([(w.ql, ones(w.W1.shape[0]), 1), (ph, ones(len(ph)), 1), (ph, ones(len(ph)), -1),
+                       (w.qm, ones(w.W1.shape[3]), -1)])
+    old_l = heff.Layout([(w.alpha_q, w.alpha_d, -1), (w.ql, ones(len(w.ql)), 1), (w.alpha_q, w.alpha_d, 1)])
+    new_l = heff.Layout([(gq, gd, -1), (w.qm, ones(len(w.qm)), 1), (gq, gd, 1)])
+    site = site_l.assemble(lambda k: site_block(36, k, (int(w.alpha_d[k[0]]), int(gd[k[2]]))))
+    Wv = W_l.assemble(lambda k: w.W1[k])
+    old = old_l.assemble(lambda k: w.L_block(k))
+    plan = heff.heff_env_plan_create(old_l.handle, site_l.handle, W_l.handle, new_l.handle, Wv, "left")
+    try:
+        ws = torch.empty(heff.heff_env_workspace_size(plan), dtype=torch.uint8, device=dev)
+        d = [torch.from_numpy(v).to(dev) for v in (old, site, Wv)]
+        env = torch.empty(new_l.nelem, dtype=torch.float64, device=dev)
+
+        def f():
+            heff.heff_env_update(plan, d[0], d[1], d[2], env, ws, stream)
+        f()
+        ms = _events_ms(f, 3, stream)
+        fl = heff.heff_env_flops(plan)
+    finally:
+        heff.heff_env_plan_destroy(plan)
+    return {"ms": ms, "flops": fl, "tflops": fl / (ms * 1e-3) / 1e12, "m_old": m_new, "m_new": m_new,
+            "note": "left environment L[a',w,a] extended by one site (FP64 block products on CUDA cores)"}
+
+
+def backward_timing(dev, stream):
+    import torch
+    import workloads as wl
+    from paper_2007_05540_gb300 import heff
+    res = {}
+    for name, limit in (("spin_m1024", 0), ("spin_m4096", 256 << 20)):
+        w, lays, bufs = make_problem(name, 0)
+        Ll, W1l, W2l, Rl, xl = lays
+        plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], "fp64", "f64")
+        g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle, bufs["W1"],
+                                       bufs["W2"], limit)
+        try:
+            aws = plan.workspace(dev)
+            gws = torch.empty(heff.heff_grad_workspace_size(g), dtype=torch.uint8, device=dev)
+            d = {k: torch.from_numpy(np.asarray(v)).to(dev) for k, v in bufs.items()}
+            rho = torch.empty((), dtype=torch.float64, device=dev)
+            outs = [torch.empty_like(d[k]) for k in ("x", "L", "R", "W1", "W2")]
+
+            def f():
+                heff.heff_backward(g, plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], rho, *outs, aws,
+                                   gws, stream)
+            f()
+            ms = _events_ms(f, 2, stream)
+            res[name] = {"ms": ms, "chunks": heff.heff_grad_chunks(g),
+                         "grad_workspace_MB": heff.heff_grad_workspace_size(g) / 1e6,
+                         "apply": "fp64", "rho": float(rho)}
+        finally:
+            heff.heff_grad_plan_destroy(g)
+        del plan
+    return res
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -345,7 +418,9 @@ def run_ours(args):
     if args.no_autotune:
         tile_n = (int(st[15]), int(st[22]) or int(st[15]))
     else:
-        tile_n = heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
+        tune_ms = []
+        tile_n = heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream,
+                                         times=tune_ms)
     st = plan.stats = heff.heff_plan_stats(plan.handle)
     heff.heff_plan_set_timing(plan.handle, True)
     for _ in range(max(args.warmup, 3)):
@@ -430,6 +505,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "m": int(w.alpha_d.sum()), "sectors": int(len(w.alpha_d)),
                    "mpo_k": int(w.W1.shape[0]), "d": int(w.W1.shape[1]), "precision": prec, "io_dtype": io,
                    "tile_n": list(tile_n),
+                   "autotune_ms": [round(v, 4) for v in tune_ms] if not args.no_autotune else None,
                    "l2": "flushed (512 MB write) between timed steps; working set > L2",
                    "parallelism": f"independent problems per rank x{world}"},
         "tflops_canonical": canonical * value / 1e12,

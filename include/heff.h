@@ -80,10 +80,12 @@ typedef struct heff_layout heff_layout;
 typedef struct heff_plan heff_plan;
 
 typedef struct heff_plan_opts {
-    int32_t precision; /* HEFF_PREC_*                                            */
-    int32_t io_dtype;  /* HEFF_DTYPE_*; FP64 precision requires HEFF_DTYPE_F64    */
-    int32_t max_batch; /* largest nbatch passed to heff_apply_batched (>= 1)      */
-    int32_t reserved[5];
+    int32_t precision;   /* HEFF_PREC_*                                            */
+    int32_t io_dtype;    /* HEFF_DTYPE_*; FP64 precision requires HEFF_DTYPE_F64    */
+    int32_t max_batch;   /* largest nbatch passed to heff_apply_batched (>= 1)      */
+    int32_t shard_count; /* 0 or 1: the whole y; S > 1: one of S row shards        */
+    int32_t shard_index; /* 0 .. S-1 (0 when not sharded)                          */
+    int32_t reserved[3]; /* zero                                                   */
 } heff_plan_opts;
 
 /*
@@ -116,10 +118,24 @@ void heff_layout_destroy(heff_layout* lay);
  * layouts (double); an entry equal to 0.0 is dropped from the schedule, so later calls
  * must pass device MPO tensors that are zero there too.  Synchronises once (table
  * upload).  Errors: INVALID_ARG, CHARGE_MISMATCH, UNSUPPORTED, OOM, CUDA.
+ *
+ * Row shards (one apply spread over S GPUs): every y block belongs to the left sector
+ * a' of its first index, and its value needs all of x and R but only the L blocks of
+ * that a'.  With opts->shard_count = S > 1 the left sectors are assigned to S shards by
+ * longest-processing-time over their GEMM flops (deterministic, the same assignment for
+ * every shard_index), and the plan computes only the y blocks of the sectors of shard
+ * opts->shard_index: the GEMM tasks of those rows and the LW preparation for them (RW,
+ * the packed x and the workspace layout stay those of the whole problem).  The other y
+ * blocks are not written, so the sum of the S shards' outputs written into zeroed
+ * buffers (an all-reduce) is y.  heff_plan_flops reports the shard's share.
  */
 int heff_plan_create(const heff_layout* L, const heff_layout* W1, const heff_layout* W2,
                      const heff_layout* R, const heff_layout* x, const double* W1_host,
                      const double* W2_host, const heff_plan_opts* opts, heff_plan** out);
+
+/* Left sectors a' (indices into x's first index) whose y blocks this plan computes, in
+ * increasing order; sectors may be NULL to query the count. */
+int heff_plan_shard_sectors(const heff_plan* plan, int32_t* sectors, int32_t* count);
 
 /* Workspace bytes needed by every call on this plan (for nbatch = max_batch). */
 int heff_plan_workspace_size(const heff_plan* plan, size_t* bytes);
@@ -232,6 +248,21 @@ int heff_env_update(heff_env_plan* plan, const double* env_old, const double* si
 void heff_env_plan_destroy(heff_env_plan* plan);
 
 /*
+ * Two-site tensor of the MPS (Fig. 1d; the starting vector of a bond's eigensolve in the
+ * two-site sweep of Section II-C): x[a, s1, s2, b] = sum_c A[a, s1, c] B[c, s2, b].
+ * A and B have flows (+1, +1, -1) and share the bond c; x is the (a, s1, s2, b) layout of
+ * the bond's problem (flows +1, +1, +1, -1).  heff_two_site_apply writes every x block
+ * (zeros where no (A, B) block pair matches); device doubles, asynchronous on `stream`.
+ * Errors: INVALID_ARG, CHARGE_MISMATCH (indices disagree), UNSUPPORTED (plan made
+ * without a device), CUDA.
+ */
+typedef struct heff_two_site heff_two_site;
+int heff_two_site_create(const heff_layout* A, const heff_layout* B, const heff_layout* x,
+                         heff_two_site** out);
+int heff_two_site_apply(heff_two_site* plan, const double* A, const double* B, double* x, void* stream);
+void heff_two_site_destroy(heff_two_site* plan);
+
+/*
  * Gradients of the Rayleigh quotient rho = <x|K|x> / <x|x> of the effective Hamiltonian
  * K (Section II-C): rho is linear in L, R, W1 and W2, so each gradient is the closed-form
  * contraction of the bra x, the ket x and the other three operators; d rho/dx =
@@ -267,9 +298,11 @@ void heff_grad_plan_destroy(heff_grad_plan* g);
  * Block SVD split of the two-site tensor with truncation (Section IV: the tensor is
  * wrapped into the matrix (a s1) x (s2 b), one dense block per charge Q = q(a) + q(s1);
  * Fig. 1e: split into two order-3 tensors, singular values absorbed in the sweep
- * direction; Section II-C: singular values below a cutoff are removed).  FP64 on the GPU
- * (one-sided Jacobi per block, rounds of disjoint column-pair rotations); the output
- * shapes depend on the truncation, so the call sequence is:
+ * direction; Section II-C: singular values below a cutoff are removed).  FP64 result on
+ * the GPU: one-sided Jacobi per block (rounds of disjoint column-pair rotations), started
+ * by FP32 sweeps on a copy, whose rotations are made orthonormal in FP64 (Newton-Schulz)
+ * and applied in FP64 before FP64 sweeps finish; the output shapes depend on the
+ * truncation, so the call sequence is:
  *   heff_svd_create(x_layout)            host: charge blocks, workspace size
  *   heff_svd_compute(x_dev, ws)           decomposes every block; SYNCHRONISES (per-sweep
  *                                         convergence check, singular values to the host)
@@ -291,6 +324,9 @@ int heff_svd_create(const heff_layout* x, heff_svd** out);
 int heff_svd_workspace_size(const heff_svd* s, size_t* bytes);
 int heff_svd_compute(heff_svd* s, const double* x, void* workspace, size_t workspace_bytes, void* stream,
                      int32_t* sweeps_out);
+/* Sweeps of the last heff_svd_compute: FP32 preconditioning sweeps and FP64 sweeps (the
+ * latter is heff_svd_compute's sweeps_out); either pointer may be NULL. */
+int heff_svd_info(const heff_svd* s, int32_t* fp32_sweeps, int32_t* fp64_sweeps);
 int heff_svd_truncate(heff_svd* s, int32_t m_max, double cutoff, int32_t* nsec_out, int32_t* charges_out,
                       int32_t* dims_out, double* discarded_weight, double* norm);
 int heff_svd_singular_values(const heff_svd* s, double* out);
@@ -323,13 +359,23 @@ int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1, const voi
  * heff_plan_autotune -- choose the output tile width (N = 256 or 128 columns) of each of
  * the two tensor-core GEMMs by timing both on the given inputs (which must be valid
  * tensors for the plan; y and the workspace are overwritten) and keep the faster one in
- * the plan.  tn_out (host, may be NULL) receives the chosen widths {GEMM 1, GEMM 2}.
+ * the plan (each candidate: one warm-up launch, then the median of five timed launches).
+ * tn_out (host, may be NULL) receives the chosen widths {GEMM 1, GEMM 2}; ms_out (host,
+ * may be NULL) the median times {GEMM 1 at 256, at 128, GEMM 2 at 256, at 128} in ms.
  * No-op for the FP64 precision.  Synchronises (event timing); call it before capturing
  * applies into a CUDA graph.
  */
 int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                        const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream,
-                       int32_t* tn_out);
+                       int32_t* tn_out, float* ms_out);
+
+/*
+ * Select the tile width (N of a tensor-core tile: 256 or 128) of GEMM 1 and GEMM 2
+ * without measuring (0 keeps the current choice); heff_plan_autotune picks by timing.
+ * Results do not depend on the choice.  Errors: INVALID_ARG (width not built for this
+ * plan, or an FP64 plan).
+ */
+int heff_plan_select_tiles(heff_plan* plan, int32_t tn1, int32_t tn2);
 
 /*
  * Phase timers (the time breakdown of Section VI / Fig. 7, on the GPU): when enabled,

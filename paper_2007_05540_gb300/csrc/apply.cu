@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 
@@ -95,6 +96,9 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ 
 }
 
 // ------------------------------------------------------------------ LW / RW preparation
+#ifndef HEFF_MIX_UNROLL
+#define HEFF_MIX_UNROLL 2      // column pairs per lane and pass
+#endif
 template <typename In, int PREC>
 __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ tiles,
                                                   const MixTerm* __restrict__ terms,
@@ -122,34 +126,54 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ ti
     const int64_t ld = t.which ? ld_rw : ld_lw;
     E* lo = hi + (t.which ? rw_plane : lw_plane);
     // warps over rows, lanes over column pairs: each thread writes two adjacent columns
-    // (dst_col0 and cols_pad are multiples of 64, so the pair stores are aligned)
+    // (dst_col0 and cols_pad are multiples of 32, so the pair stores are aligned), four
+    // pairs 64 columns apart per pass, with all loads of a term issued before its FMAs
+    // (eight loads in flight per thread: the kernel is bound by HBM latency x bytes in flight)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int U = HEFF_MIX_UNROLL;
     for (int rr = warp; rr < t.nrows; rr += blockDim.x >> 5) {
         const int r = t.r0 + rr;
         const int64_t rc0 = (int64_t)r * t.cols;
         E* hrow = hi + (t.dst_row0 + r) * ld + t.dst_col0;
         E* lrow = lo + (t.dst_row0 + r) * ld + t.dst_col0;
-        for (int c = 2 * lane; c < t.cols_pad; c += 64) {
-            Acc a0 = 0, a1 = 0;
-            const bool v0 = c < t.cols, v1 = c + 1 < t.cols;
-            if (v0) {
-                for (int k = 0; k < nt; ++k) {
-                    const In* s = src + srco[k] + rc0 + c;
-                    a0 += coef[k] * (Acc)s[0];
-                    if (v1) a1 += coef[k] * (Acc)s[1];
+        for (int cb = 2 * lane; cb < t.cols_pad; cb += 64 * U) {
+            Acc a0[U], a1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) { a0[u] = 0; a1[u] = 0; }
+            for (int k = 0; k < t.term_count; ++k) {
+                const In* s;
+                Acc cf;
+                if (k < nt) {
+                    s = src + srco[k] + rc0;
+                    cf = coef[k];
+                } else {                                      // rare: more than 64 terms
+                    const MixTerm m = terms[t.term_begin + k];
+                    s = src + m.src_off + rc0;
+                    cf = (Acc)W[m.w_idx];
                 }
-                for (int k = 64; k < t.term_count; ++k) {     // rare: more than 64 terms
-                    MixTerm m = terms[t.term_begin + k];
-                    const In* s = src + m.src_off + rc0 + c;
-                    a0 += (Acc)W[m.w_idx] * (Acc)s[0];
-                    if (v1) a1 += (Acc)W[m.w_idx] * (Acc)s[1];
+                In v0[U], v1[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int c = cb + 64 * u;
+                    v0[u] = c < t.cols ? s[c] : (In)0;
+                    v1[u] = c + 1 < t.cols ? s[c + 1] : (In)0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    a0[u] += cf * (Acc)v0[u];
+                    a1[u] += cf * (Acc)v1[u];
                 }
             }
-            E h0, l0, h1, l1;
-            Plane<PREC>::split(a0, h0, l0);
-            Plane<PREC>::split(a1, h1, l1);
-            Plane<PREC>::store2(hrow + c, h0, h1);
-            if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lrow + c, l0, l1);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int c = cb + 64 * u;
+                if (c >= t.cols_pad) break;
+                E h0, l0, h1, l1;
+                Plane<PREC>::split(a0[u], h0, l0);
+                Plane<PREC>::split(a1[u], h1, l1);
+                Plane<PREC>::store2(hrow + c, h0, h1);
+                if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lrow + c, l0, l1);
+            }
         }
     }
 }
@@ -456,7 +480,7 @@ extern "C" int heff_apply_batched(heff_plan* plan, const void* L, const void* W1
 // caller's inputs and keep the faster one per GEMM (tensor-core precisions only).
 extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                                   const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream,
-                                  int32_t* tn_out) {
+                                  int32_t* tn_out, float* ms_out) {
     heff::clear_error();
     if (!plan || !L || !W1 || !W2 || !R || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_autotune: null argument");
     int rc = check_ws(plan, workspace, workspace_bytes);
@@ -467,28 +491,35 @@ extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1
         void* ys[1] = {y};
         if ((rc = heff::launch_mix(plan, L, W1, W2, R, workspace, stream))) return rc;
         if ((rc = heff::launch_pack_batch(plan, xs, 1, workspace, stream))) return rc;
-        cudaEvent_t e0, e1;
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        for (int which = 1; which <= 2; ++which) {
+        // each candidate: one warm-up launch, then the median of 5 separately timed launches
+        cudaEvent_t e[6];
+        for (auto& ev : e) CK(cudaEventCreate(&ev));
+        for (int which = 1; which <= 2 && !rc; ++which) {
             heff::GemmList& act = which == 1 ? plan->g1 : plan->g2;
             heff::GemmList& alt = which == 1 ? plan->g1_alt : plan->g2_alt;
             float ms[2] = {0.f, 0.f};
-            for (int v = 0; v < 2; ++v) {
+            for (int v = 0; v < 2 && !rc; ++v) {
                 if (v == 1) std::swap(act, alt);
-                if ((rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream))) break;   // warm-up
-                CK(cudaEventRecord(e0, st));
-                for (int r = 0; r < 3 && !rc; ++r) rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream);
-                CK(cudaEventRecord(e1, st));
-                CK(cudaEventSynchronize(e1));
-                CK(cudaEventElapsedTime(&ms[v], e0, e1));
+                rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream);
+                CK(cudaEventRecord(e[0], st));
+                for (int r = 0; r < 5 && !rc; ++r) {
+                    rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream);
+                    CK(cudaEventRecord(e[r + 1], st));
+                }
+                if (!rc) {
+                    CK(cudaEventSynchronize(e[5]));
+                    float t[5];
+                    for (int r = 0; r < 5; ++r) CK(cudaEventElapsedTime(&t[r], e[r], e[r + 1]));
+                    std::sort(t, t + 5);
+                    ms[v] = t[2];
+                }
                 if (v == 1) std::swap(act, alt);
             }
             if (rc) break;
+            if (ms_out) { ms_out[2 * (which - 1)] = ms[0]; ms_out[2 * (which - 1) + 1] = ms[1]; }
             if (ms[1] < ms[0]) std::swap(act, alt);
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        for (auto& ev : e) cudaEventDestroy(ev);
         if (rc) return rc;
         plan->stats[3] = (int64_t)plan->g1.tasks.size();
         plan->stats[4] = (int64_t)plan->g2.tasks.size();
@@ -499,6 +530,26 @@ extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1
         tn_out[0] = plan->g1.tn;
         tn_out[1] = plan->g2.tn;
     }
+    return HEFF_OK;
+}
+
+extern "C" int heff_plan_select_tiles(heff_plan* plan, int32_t tn1, int32_t tn2) {
+    heff::clear_error();
+    if (!plan) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_select_tiles: null plan");
+    const int tn[2] = {tn1, tn2};
+    for (int which = 1; which <= 2; ++which) {
+        heff::GemmList& act = which == 1 ? plan->g1 : plan->g2;
+        heff::GemmList& alt = which == 1 ? plan->g1_alt : plan->g2_alt;
+        const int want = tn[which - 1];
+        if (want == 0 || want == act.tn) continue;
+        if (alt.tn != want || plan->opts.precision == HEFF_PREC_FP64)
+            return fail(HEFF_ERR_INVALID_ARG, "tile width %d is not available for GEMM %d", want, which);
+        std::swap(act, alt);
+    }
+    plan->stats[3] = (int64_t)plan->g1.tasks.size();
+    plan->stats[4] = (int64_t)plan->g2.tasks.size();
+    plan->stats[15] = plan->g1.tn;
+    plan->stats[22] = plan->g2.tn;
     return HEFF_OK;
 }
 

@@ -236,3 +236,84 @@ extern "C" void heff_env_plan_destroy(heff_env_plan* plan) {
     heff::blist_free(plan->step2);
     delete plan;
 }
+
+// ---------------------------------------------------------------- two-site tensor
+// x[a, s1, s2, b] = sum_c A[a, s1, c] B[c, s2, b] (Fig. 1d: the two MPS sites joined over
+// their shared bond, the starting vector of a bond's eigensolve).  One block product per
+// charge-matched (A block, B block) pair, summed per x block; x blocks without a matching
+// pair are written as zeros.
+struct heff_two_site {
+    BList prods;
+    bool uploaded = false;
+};
+
+extern "C" int heff_two_site_create(const heff_layout* A, const heff_layout* B, const heff_layout* x,
+                                    heff_two_site** out) {
+    heff::clear_error();
+    if (!A || !B || !x || !out) return fail(HEFF_ERR_INVALID_ARG, "heff_two_site_create: null argument");
+    *out = nullptr;
+    if (A->idx.size() != 3 || B->idx.size() != 3 || x->idx.size() != 4)
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "orders must be A 3, B 3, x 4");
+    const heff::IndexDesc &aa = A->idx[0], &ap = A->idx[1], &ac = A->idx[2];
+    const heff::IndexDesc &bc = B->idx[0], &bp = B->idx[1], &bb = B->idx[2];
+    if (aa.flow != 1 || ap.flow != 1 || ac.flow != -1 || bc.flow != 1 || bp.flow != 1 || bb.flow != -1)
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "A and B flows must be (+1, +1, -1)");
+    if (!same(ac, bc) || !same(aa, x->idx[0]) || !same(ap, x->idx[1]) || !same(bp, x->idx[2]) ||
+        !same(bb, x->idx[3]))
+        return fail(HEFF_ERR_CHARGE_MISMATCH, "A (a, s1, c), B (c, s2, b) and x (a, s1, s2, b) indices disagree");
+    heff_two_site* P = new (std::nothrow) heff_two_site();
+    if (!P) return fail(HEFF_ERR_OOM, "out of host memory");
+    try {
+        std::map<std::pair<int, int>, std::vector<std::pair<int, int64_t>>> a_by;   // (a, s1) -> (c, offset)
+        for (size_t k = 0; k < A->offsets.size(); ++k)
+            a_by[{A->keys[k * 3], A->keys[k * 3 + 1]}].push_back({A->keys[k * 3 + 2], A->offsets[k]});
+        for (size_t k = 0; k < x->offsets.size(); ++k) {
+            const int a = x->keys[k * 4], s1 = x->keys[k * 4 + 1], s2 = x->keys[k * 4 + 2], b = x->keys[k * 4 + 3];
+            const int ma = aa.dims[a], mb = bb.dims[b];
+            std::vector<BProd> ps;
+            auto it = a_by.find({a, s1});
+            if (it != a_by.end())
+                for (auto& co : it->second) {
+                    const int64_t boff = B->offset_of({co.first, s2, b});
+                    if (boff < 0) continue;
+                    const int mc = ac.dims[co.first];
+                    BProd p{};
+                    p.a_off = co.second; p.a_rs = mc; p.a_cs = 1;
+                    p.b_off = boff; p.b_rs = mb; p.b_cs = 1;
+                    p.K = mc; p.c1 = -1; p.c2 = -1;
+                    ps.push_back(p);
+                }
+            P->prods.add_block(x->offsets[k], mb, ma, mb, ps);
+        }
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(HEFF_ERR_OOM, "out of host memory while planning the two-site tensor");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+        int rc = heff::blist_upload(P->prods);
+        if (rc) {
+            heff::blist_free(P->prods);
+            delete P;
+            return rc;
+        }
+        P->uploaded = true;
+    } else {
+        cudaGetLastError();
+    }
+    *out = P;
+    return HEFF_OK;
+}
+
+extern "C" int heff_two_site_apply(heff_two_site* P, const double* A, const double* B, double* x, void* stream) {
+    heff::clear_error();
+    if (!P || !A || !B || !x) return fail(HEFF_ERR_INVALID_ARG, "heff_two_site_apply: null argument");
+    if (!P->uploaded) return fail(HEFF_ERR_UNSUPPORTED, "two-site plan was created without a CUDA device");
+    return heff::launch_bgemm(P->prods, A, B, x, nullptr, nullptr, 1.0, stream);
+}
+
+extern "C" void heff_two_site_destroy(heff_two_site* P) {
+    if (!P) return;
+    heff::blist_free(P->prods);
+    delete P;
+}

@@ -68,6 +68,8 @@ struct GemmTask {
     int32_t ldc;            // output row pitch (elements)
     int32_t n_zero;         // columns [n, n + n_zero) of the tile are written as 0 (padding)
     int32_t seg_begin, seg_count;
+    int32_t ktotal;         // sum of the segments' klen (padded contraction length)
+    int32_t pad_;
 };
 struct KSeg {
     int32_t k0, klen;       // column range shared by A and B (klen multiple of KPAD)
@@ -125,6 +127,9 @@ struct GemmList {
     int tm = 0, tn = 0;
     double flops = 0;       // executed (valid m, n; padded K)
     double useful = 0;      // valid m, n and unpadded K
+    // host only, one entry per task: output left sector a' and the task's flop counts
+    std::vector<int32_t> owner;
+    std::vector<double> task_flops, task_useful;
 };
 
 }  // namespace heff
@@ -153,6 +158,7 @@ struct heff_plan {
     // workspace byte offsets
     size_t off_xt = 0, off_lw = 0, off_t = 0, off_rw = 0, off_flags = 0, ws_bytes = 0;
     double flops_canonical = 0;
+    std::vector<int32_t> shard_sectors;   // left sectors a' of y this plan computes
     // device tables
     std::vector<heff::PackTile> pack;
     std::vector<heff::MixTile> mix;

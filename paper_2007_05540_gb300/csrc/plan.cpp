@@ -31,6 +31,11 @@ using heff::KPAD;
 using heff::pad_up;
 using Charge = std::vector<int32_t>;
 
+// 1: order the task lists as an LPT assignment for the kernels' static round-robin
+#ifndef HEFF_LPT_SCHEDULE
+#define HEFF_LPT_SCHEDULE 1
+#endif
+
 namespace {
 
 Charge add(const Charge& a, const Charge& b, int sb = 1) {
@@ -87,6 +92,10 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         return fail(HEFF_ERR_UNSUPPORTED, "the FP64 path needs HEFF_DTYPE_F64 tensors");
     if (opts->max_batch < 1 || opts->max_batch > 4096)
         return fail(HEFF_ERR_INVALID_ARG, "max_batch must be 1..4096");
+    if (opts->shard_count < 0 || opts->shard_count > 4096 || opts->shard_index < 0 ||
+        opts->shard_index >= (opts->shard_count > 1 ? opts->shard_count : 1))
+        return fail(HEFF_ERR_INVALID_ARG, "shard_index %d outside 0..shard_count-1 (shard_count %d)",
+                    opts->shard_index, opts->shard_count);
     if (x->idx.size() != 4 || L->idx.size() != 3 || R->idx.size() != 3 || W1->idx.size() != 4 ||
         W2->idx.size() != 4)
         return fail(HEFF_ERR_CHARGE_MISMATCH, "tensor orders must be x:4 L:3 R:3 W1:4 W2:4");
@@ -184,7 +193,9 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         auto W1i = [&](int a, int t, int s, int m) { return w1i[((a * d1 + t) * d1 + s) * km + m]; };
         auto W2i = [&](int m, int t, int s, int r) { return w2i[((m * d2 + t) * d2 + s) * kr + r]; };
 
-        // ---- canonical flop count (the oracle's two-contraction list algorithm)
+        // ---- canonical flop count (the oracle's two-contraction list algorithm), also per
+        // output left sector a' (for the row shards)
+        std::vector<double> canon1_ip, canon2_ip;
         {
             // structural pattern of W12 = sum_wm W1 W2 : feeds[(wl,s1,s2)] -> set (t1,t2,wr)
             std::map<std::tuple<int, int, int>, std::set<std::tuple<int, int, int>>> feeds;
@@ -201,6 +212,8 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             for (size_t b = 0; b < R->offsets.size(); ++b)
                 R_by_ket[{R->keys[b * 3 + 1], R->keys[b * 3 + 2]}].push_back(R->keys[b * 3 + 0]);
             double g1 = 0, g2 = 0;
+            canon1_ip.assign(na, 0.0);
+            canon2_ip.assign(na, 0.0);
             std::set<std::tuple<int, int, int, int, int>> zkeys;
             for (size_t b = 0; b < x->offsets.size(); ++b) {
                 int i = x->keys[b * 4], s1 = x->keys[b * 4 + 1], s2 = x->keys[b * 4 + 2], j = x->keys[b * 4 + 3];
@@ -210,6 +223,7 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                     auto f = feeds.find({pw.second, s1, s2});
                     if (f == feeds.end() || f->second.empty()) continue;
                     g1 += 2.0 * alpha.dims[pw.first] * alpha.dims[i] * beta.dims[j];
+                    canon1_ip[pw.first] += 2.0 * alpha.dims[pw.first] * alpha.dims[i] * beta.dims[j];
                     for (auto& t : f->second)
                         zkeys.insert({pw.first, std::get<0>(t), std::get<1>(t), std::get<2>(t), j});
                 }
@@ -217,8 +231,11 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             for (auto& z : zkeys) {
                 auto rk = R_by_ket.find({std::get<3>(z), std::get<4>(z)});
                 if (rk == R_by_ket.end()) continue;
-                for (int jp : rk->second)
-                    g2 += 2.0 * alpha.dims[std::get<0>(z)] * beta.dims[std::get<4>(z)] * beta.dims[jp];
+                for (int jp : rk->second) {
+                    const double f = 2.0 * alpha.dims[std::get<0>(z)] * beta.dims[std::get<4>(z)] * beta.dims[jp];
+                    g2 += f;
+                    canon2_ip[std::get<0>(z)] += f;
+                }
             }
             P->flops_canonical = g1 + g2;
             P->stats[16] = (int64_t)g1;
@@ -349,6 +366,15 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                                       r0, std::min(MIX_ROWS, rows - r0), tb, (int32_t)sg.terms.size(), 1});
             }
         }
+        // ---- SMs of the current device (the persistent kernels' width; 148 without one)
+        int nsm = 148;
+        {
+            int ndev = 0, dev = 0, v = 0;
+            if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0 && cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+                nsm = v;
+            cudaGetLastError();
+        }
         // ---- GEMM task lists for one tile shape TM x TN
         auto build_lists = [&](int TM, int TN, heff::GemmList& G1, heff::GemmList& G2) -> bool {
         G1.tm = G2.tm = TM;
@@ -388,9 +414,11 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                         t.n_zero = (n0 + TN >= ge.dim) ? (int32_t)(pad_up(ge.dim, KPAD) - ge.dim) : 0;
                         t.seg_begin = sb;
                         t.seg_count = sc;
+                        t.ktotal = (int32_t)klen;
                         G1.tasks.push_back(t);
-                        G1.flops += 2.0 * t.m * t.n * klen;
-                        G1.useful += 2.0 * t.m * t.n * kuse;
+                        G1.owner.push_back(rg.ip);
+                        G1.task_flops.push_back(2.0 * t.m * t.n * klen);
+                        G1.task_useful.push_back(2.0 * t.m * t.n * kuse);
                     }
             }
         }
@@ -425,9 +453,11 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                         t.n_zero = 0;
                         t.seg_begin = sb;
                         t.seg_count = sc;
+                        t.ktotal = (int32_t)klen;
                         G2.tasks.push_back(t);
-                        G2.flops += 2.0 * t.m * t.n * klen;
-                        G2.useful += 2.0 * t.m * t.n * kuse;
+                        G2.owner.push_back(gc.sec);
+                        G2.task_flops.push_back(2.0 * t.m * t.n * klen);
+                        G2.task_useful.push_back(2.0 * t.m * t.n * kuse);
                     }
             }
         }
@@ -443,12 +473,36 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                 ord[t] = t;
             }
             std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
-            std::vector<heff::GemmTask> sorted;
-            sorted.reserve(ord.size());
-            for (size_t t : ord) sorted.push_back(g->tasks[t]);
-            g->tasks.swap(sorted);
+            heff::GemmList s;
+            for (size_t t : ord) {
+                s.tasks.push_back(g->tasks[t]);
+                s.owner.push_back(g->owner[t]);
+                s.task_flops.push_back(g->task_flops[t]);
+                s.task_useful.push_back(g->task_useful[t]);
+            }
+            g->tasks.swap(s.tasks);
+            g->owner.swap(s.owner);
+            g->task_flops.swap(s.task_flops);
+            g->task_useful.swap(s.task_useful);
         }
         return true;
+        };
+        // keep the tasks of the owned left sectors and total their flops
+        auto keep_owned = [&](heff::GemmList& G, const std::vector<char>& owned) {
+            heff::GemmList s;
+            for (size_t t = 0; t < G.tasks.size(); ++t) {
+                if (!owned[G.owner[t]]) continue;
+                s.tasks.push_back(G.tasks[t]);
+                s.owner.push_back(G.owner[t]);
+                s.task_flops.push_back(G.task_flops[t]);
+                s.task_useful.push_back(G.task_useful[t]);
+            }
+            G.tasks.swap(s.tasks);
+            G.owner.swap(s.owner);
+            G.task_flops.swap(s.task_flops);
+            G.task_useful.swap(s.task_useful);
+            G.flops = G.useful = 0;
+            for (size_t t = 0; t < G.tasks.size(); ++t) { G.flops += G.task_flops[t]; G.useful += G.task_useful[t]; }
         };
         const bool tc = opts->precision != HEFF_PREC_FP64;
         if (!build_lists(tc ? 128 : 64, tc ? 256 : 64, P->g1, P->g2) ||
@@ -456,6 +510,91 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             delete P;
             return fail(HEFF_ERR_CHARGE_MISMATCH, "internal: y block missing");
         }
+        // ---- row shards: left sectors a' of y assigned to shards by longest-processing-time
+        // over their executed GEMM flops (ties: lower sector, then lower shard), identical for
+        // every shard index; this plan keeps the work of its own sectors
+        std::vector<char> owned(na, 1);
+        if (opts->shard_count > 1) {
+            std::vector<double> work(na, 0.0);
+            for (const heff::GemmList* G : {&P->g1, &P->g2})
+                for (size_t t = 0; t < G->tasks.size(); ++t) work[G->owner[t]] += G->task_flops[t];
+            std::vector<int> ord(na);
+            for (int i = 0; i < na; ++i) ord[i] = i;
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work[a] > work[b]; });
+            std::vector<double> load(opts->shard_count, 0.0);
+            for (int i : ord) {
+                int best = 0;
+                for (int r = 1; r < opts->shard_count; ++r) if (load[r] < load[best]) best = r;
+                load[best] += work[i];
+                owned[i] = best == opts->shard_index;
+            }
+            std::set<int64_t> lw_rows;   // LW row groups of owned sectors
+            for (auto& rg : rgs) if (owned[rg.ip]) lw_rows.insert(rg.lw_row0);
+            std::vector<heff::MixTile> mix;
+            for (auto& mt : P->mix)
+                if (mt.which != 0 || lw_rows.count(mt.dst_row0)) mix.push_back(mt);
+            P->mix.swap(mix);
+            double c1 = 0, c2 = 0;
+            for (int i = 0; i < na; ++i) if (owned[i]) { c1 += canon1_ip[i]; c2 += canon2_ip[i]; }
+            P->flops_canonical = c1 + c2;
+            P->stats[16] = (int64_t)c1;
+            P->stats[17] = (int64_t)c2;
+        }
+        for (heff::GemmList* G : {&P->g1, &P->g2, &P->g1_alt, &P->g2_alt}) keep_owned(*G, owned);
+        // ---- static schedule of the persistent tensor-core kernels: CTA c of a grid of
+        // min(nsm, tasks) runs tasks c, c + grid, c + 2 grid, ...  Assign the tasks by
+        // longest-processing-time (each to the least loaded CTA, longest first; a tile's
+        // time ~ (K blocks + a fixed overhead) x MMA width) and interleave the per-CTA lists
+        // in that pattern, padding short lists with empty tasks (no rows, no segments).
+        if (tc && HEFF_LPT_SCHEDULE) {
+            for (heff::GemmList* G : {&P->g1, &P->g2, &P->g1_alt, &P->g2_alt}) {
+                const size_t nt = G->tasks.size();
+                if (nt == 0) continue;
+                const int grid = (int)std::min<size_t>((size_t)nsm, nt);
+                std::vector<double> work(nt);
+                for (size_t t = 0; t < nt; ++t) {
+                    int64_t k = 0;
+                    for (int s2 = 0; s2 < G->tasks[t].seg_count; ++s2) k += G->segs[G->tasks[t].seg_begin + s2].klen;
+                    work[t] = (double)(k / KPAD + 4) * ((G->tasks[t].n + 15) / 16 * 16);
+                }
+                std::vector<size_t> ord(nt);
+                for (size_t t = 0; t < nt; ++t) ord[t] = t;
+                std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+                std::vector<double> load(grid, 0.0);
+                std::vector<std::vector<size_t>> per(grid);
+                for (size_t t : ord) {
+                    int best = 0;
+                    for (int c = 1; c < grid; ++c) if (load[c] < load[best]) best = c;
+                    load[best] += work[t];
+                    per[best].push_back(t);
+                }
+                size_t depth = 0;
+                for (auto& v : per) depth = std::max(depth, v.size());
+                heff::GemmList s2;
+                for (size_t j = 0; j < depth; ++j)
+                    for (int c = 0; c < grid; ++c) {
+                        if (j < per[c].size()) {
+                            const size_t t = per[c][j];
+                            s2.tasks.push_back(G->tasks[t]);
+                            s2.owner.push_back(G->owner[t]);
+                            s2.task_flops.push_back(G->task_flops[t]);
+                            s2.task_useful.push_back(G->task_useful[t]);
+                        } else {
+                            heff::GemmTask e{};
+                            e.ldc = 1;
+                            s2.tasks.push_back(e);
+                            s2.owner.push_back(-1);
+                            s2.task_flops.push_back(0.0);
+                            s2.task_useful.push_back(0.0);
+                        }
+                    }
+                G->tasks.swap(s2.tasks);
+                G->owner.swap(s2.owner);
+                G->task_flops.swap(s2.task_flops);
+                G->task_useful.swap(s2.task_useful);
+            }
+        }
+        for (int i = 0; i < na; ++i) if (owned[i]) P->shard_sectors.push_back(i);
         const int TM = P->g1.tm, TN = P->g1.tn;
         // ---- workspace layout
         auto al = [](size_t v) { return (v + 255) / 256 * 256; };
@@ -489,6 +628,14 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         return rc;
     }
     *out = P;
+    return HEFF_OK;
+}
+
+extern "C" int heff_plan_shard_sectors(const heff_plan* plan, int32_t* sectors, int32_t* count) {
+    heff::clear_error();
+    if (!plan || !count) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_shard_sectors: null argument");
+    if (sectors) std::memcpy(sectors, plan->shard_sectors.data(), plan->shard_sectors.size() * sizeof(int32_t));
+    *count = (int32_t)plan->shard_sectors.size();
     return HEFF_OK;
 }
 

@@ -6,10 +6,18 @@
 // Each charge block M_Q (rows (s1, i, a), columns (s2, j, b)) is decomposed by one-sided
 // Jacobi rotations (Hestenes): the columns of J = M_Q (or M_Q^T when M_Q is wide) are made
 // mutually orthogonal by plane rotations applied in a round-robin order, so every round
-// rotates k/2 disjoint column pairs in parallel (one warp per pair, all sectors in one
-// launch); V accumulates the rotations.  On convergence the column norms are the singular
+// rotates k/2 disjoint column pairs in parallel (one thread block per pair, all sectors in
+// one launch); V accumulates the rotations.  On convergence the column norms are the singular
 // values.  The truncation rule runs on the host on the singular values; the kept singular
 // triplets are then written into the caller's left (a, s1, c) and right (c, s2, b) tensors.
+//
+// Precision: the GB300's FP64 rate is low, and a full FP64 Jacobi run needs ~18 sweeps of
+// ~12 r k^2 flops.  The sweeps therefore start on an FP32 copy (J32, V32) until the
+// columns are orthogonal to FP32 accuracy; V32 is made orthonormal in FP64 by two
+// Newton-Schulz steps (V <- V (3 I - V^T V) / 2, each squaring the orthogonality error),
+// J <- J V in FP64, and FP64 Jacobi sweeps, accumulating into V, finish the
+// decomposition (quadratic convergence from the preconditioned start: 2-3 sweeps).  The
+// result is the FP64 one-sided Jacobi SVD of J; the FP32 phase only supplies the start.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +36,8 @@ namespace {
 
 struct SvdSector {           // device-side description of one charge block
     int64_t j_off, v_off;    // column-major J (r x k) and V (k x k) in the workspace
+    int64_t g_off, w_off;    // FP64 scratch: G (k x k), W (r x k)
+    int64_t j32_off, v32_off;    // FP32 copies (offsets in floats from the FP32 region)
     int32_t r, k;            // rows, columns of J (k <= r)
     int32_t transposed;      // 1 when J = M_Q^T
     int32_t s_off;           // first singular value of this sector in the s array
@@ -53,12 +63,18 @@ struct heff_svd {
     std::vector<std::vector<int64_t>> xoff;    // per sector: x block offsets [row group][col group]
     std::vector<int32_t> mrows, ncols;         // M_Q shape
     int64_t ws_doubles = 0;
+    size_t off_slots = 0;                      // byte offset of the per-pair convergence slots
+    int64_t nslots = 0, slot_ld = 0;
     size_t ws_bytes = 0;
     int64_t s_total = 0;
     std::vector<double> s;                     // singular values (per sector, unsorted)
     std::vector<std::vector<int32_t>> kept;    // per sector: kept column indices of J, s descending
     double norm = 0, discarded = 0;
     SvdSector* d_sec = nullptr;
+    size_t off_f32 = 0;                        // byte offset of the FP32 region
+    heff::BList gram, vg, jv;                  // G = V^T V, W = V G, W = J V (all sectors)
+    bool lists_uploaded = false;
+    int fp32_sweeps = 0, fp64_sweeps = 0;
     int max_k = 0;
     bool computed = false;
     int alpha_nsec = 0, beta_nsec = 0;
@@ -92,57 +108,128 @@ __global__ void svd_load_kernel(const SvdSector* __restrict__ secs, const int64_
     }
 }
 
-__global__ void svd_init_v_kernel(const SvdSector* __restrict__ secs, double* __restrict__ ws) {
-    const SvdSector s = secs[blockIdx.y];
-    double* V = ws + s.v_off;
-    const int64_t n = (int64_t)s.k * s.k;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        V[e] = (e % (s.k + 1) == 0) ? 1.0 : 0.0;
+
+// one round of the round-robin ordering: block x of the launch rotates pair x of sector y.
+// A whole block per pair (columns of up to a few thousand doubles): the three dot products
+// are block reductions in a fixed order, then every thread rotates its elements of the two
+// columns of J and of V.
+constexpr int SVD_NT = 256;
+
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& g, double (*sh)[3]) {
+    a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[w][0] = a; sh[w][1] = b; sh[w][2] = g; }
+    __syncthreads();
+    a = b = g = 0.0;
+    for (int i = 0; i < SVD_NT / 32; ++i) { a += sh[i][0]; b += sh[i][1]; g += sh[i][2]; }
 }
 
-// one round of the round-robin ordering: warp w of the launch rotates pair i of sector y
-__global__ void __launch_bounds__(128) svd_round_kernel(const SvdSector* __restrict__ secs, double* __restrict__ ws,
-                                                        int round, unsigned int* __restrict__ off_max) {
+// off: one slot per (sector, pair position) holding the largest off-diagonal measure seen in
+// this sweep; each slot has one writer per round (its block), so no atomics.  T = double
+// works on (J, V) in the FP64 region, T = float on (J32, V32) in the FP32 region.
+template <typename T>
+__global__ void __launch_bounds__(SVD_NT) svd_round_kernel(const SvdSector* __restrict__ secs, T* __restrict__ base,
+                                                           int round, float* __restrict__ off, int off_ld) {
+    __shared__ double sh[SVD_NT / 32][3];
+    constexpr bool F32 = sizeof(T) == 4;
     const SvdSector s = secs[blockIdx.y];
     const int kk = s.k + (s.k & 1);                   // padded to even (dummy column = k)
     if (kk < 2 || round >= kk - 1) return;
-    const int pair = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int pair = blockIdx.x;
     if (pair >= kk / 2) return;
     auto pos = [&](int j) { return j == 0 ? 0 : 1 + (j - 1 + round) % (kk - 1); };
     int p = pos(pair), q = pos(kk - 1 - pair);
     if (p >= s.k || q >= s.k) return;                 // pair with the dummy column
     if (p > q) { const int t = p; p = q; q = t; }
-    double* J = ws + s.j_off;
-    double* cp = J + (int64_t)p * s.r;
-    double* cq = J + (int64_t)q * s.r;
-    double a = 0, b = 0, g = 0;
-    for (int i = lane; i < s.r; i += 32) {
-        const double u = cp[i], v = cq[i];
+    T* J = base + (F32 ? s.j32_off : s.j_off);
+    T* cp = J + (int64_t)p * s.r;
+    T* cq = J + (int64_t)q * s.r;
+    T a = 0, b = 0, g = 0;
+    for (int i = threadIdx.x; i < s.r; i += SVD_NT) {
+        const T u = cp[i], v = cq[i];
         a = fma(u, u, a);
         b = fma(v, v, b);
         g = fma(u, v, g);
     }
-    a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
-    if (g == 0.0 || a == 0.0 || b == 0.0) return;
-    const double meas = fabs(g) / sqrt(a * b);
-    if (lane == 0) atomicMax(off_max, __float_as_uint((float)meas));
-    if (meas < 1e-15) return;
-    const double zeta = (b - a) / (2.0 * g);
+    double da = a, db = b, dg = g;
+    block_sum3(da, db, dg, sh);
+    if (dg == 0.0 || da == 0.0 || db == 0.0) return;  // block-uniform
+    const double meas = fabs(dg) / sqrt(da * db);
+    if (threadIdx.x == 0) {
+        float* o = off + (int64_t)blockIdx.y * off_ld + pair;
+        *o = fmaxf(*o, (float)meas);
+    }
+    if (meas < (F32 ? 1e-7 : 1e-15)) return;
+    const double zeta = (db - da) / (2.0 * dg);
     const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-    for (int i = lane; i < s.r; i += 32) {
-        const double u = cp[i], v = cq[i];
+    const double cd = 1.0 / sqrt(1.0 + t * t);
+    const T c = (T)cd, sn = (T)(cd * t);
+    for (int i = threadIdx.x; i < s.r; i += SVD_NT) {
+        const T u = cp[i], v = cq[i];
         cp[i] = c * u - sn * v;
         cq[i] = sn * u + c * v;
     }
-    double* V = ws + s.v_off;
-    double* vp = V + (int64_t)p * s.k;
-    double* vq = V + (int64_t)q * s.k;
-    for (int i = lane; i < s.k; i += 32) {
-        const double u = vp[i], v = vq[i];
+    T* V = base + (F32 ? s.v32_off : s.v_off);
+    T* vp = V + (int64_t)p * s.k;
+    T* vq = V + (int64_t)q * s.k;
+    for (int i = threadIdx.x; i < s.k; i += SVD_NT) {
+        const T u = vp[i], v = vq[i];
         vp[i] = c * u - sn * v;
         vq[i] = sn * u + c * v;
     }
+}
+
+// J32 = float(J), V32 = I
+__global__ void svd_to_f32_kernel(const SvdSector* __restrict__ secs, const double* __restrict__ ws,
+                                  float* __restrict__ f32) {
+    const SvdSector s = secs[blockIdx.y];
+    const int64_t nj = (int64_t)s.r * s.k, nv = (int64_t)s.k * s.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nj + nv; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < nj) f32[s.j32_off + e] = (float)ws[s.j_off + e];
+        else {
+            const int64_t v = e - nj;
+            f32[s.v32_off + v] = (v % (s.k + 1) == 0) ? 1.f : 0.f;
+        }
+    }
+}
+
+// V = double(V32)
+__global__ void svd_v_to_f64_kernel(const SvdSector* __restrict__ secs, const float* __restrict__ f32,
+                                    double* __restrict__ ws) {
+    const SvdSector s = secs[blockIdx.y];
+    const int64_t nv = (int64_t)s.k * s.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (int64_t)gridDim.x * blockDim.x)
+        ws[s.v_off + e] = (double)f32[s.v32_off + e];
+}
+
+// Newton-Schulz combine: V = 1.5 V + W, with W = -0.5 V G already formed
+__global__ void svd_ns_kernel(const SvdSector* __restrict__ secs, double* __restrict__ ws) {
+    const SvdSector s = secs[blockIdx.y];
+    const int64_t nv = (int64_t)s.k * s.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (int64_t)gridDim.x * blockDim.x)
+        ws[s.v_off + e] = 1.5 * ws[s.v_off + e] + ws[s.w_off + e];
+}
+
+// J = W (the product J V)
+__global__ void svd_copy_w_kernel(const SvdSector* __restrict__ secs, double* __restrict__ ws) {
+    const SvdSector s = secs[blockIdx.y];
+    const int64_t nj = (int64_t)s.r * s.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nj; e += (int64_t)gridDim.x * blockDim.x)
+        ws[s.j_off + e] = ws[s.w_off + e];
+}
+
+// largest slot value -> out[0] (one block; fixed order)
+__global__ void __launch_bounds__(256) svd_offmax_kernel(const float* __restrict__ off, int n, float* __restrict__ out) {
+    __shared__ float sh[256];
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) m = fmaxf(m, off[i]);
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
 }
 
 // column norms of J = singular values
@@ -232,7 +319,7 @@ extern "C" int heff_svd_create(const heff_layout* x, heff_svd** out) {
         const int nsec = (int)S->Q.size();
         S->mrows.assign(nsec, 0);
         S->ncols.assign(nsec, 0);
-        int64_t o = 0, so = 0;
+        int64_t o = 0, so = 0, o32 = 0;
         for (int q = 0; q < nsec; ++q) {
             std::sort(S->rows[q].begin(), S->rows[q].end());
             std::sort(S->cols[q].begin(), S->cols[q].end());
@@ -248,8 +335,37 @@ extern "C" int heff_svd_create(const heff_layout* x, heff_svd** out) {
             sc.k = sc.transposed ? r : c;
             sc.j_off = o; o += (int64_t)sc.r * sc.k;
             sc.v_off = o; o += (int64_t)sc.k * sc.k;
+            sc.g_off = o; o += (int64_t)sc.k * sc.k;
+            sc.w_off = o; o += (int64_t)sc.r * sc.k;
+            sc.j32_off = o32; o32 += (int64_t)sc.r * sc.k;
+            sc.v32_off = o32; o32 += (int64_t)sc.k * sc.k;
             sc.s_off = (int32_t)so; so += sc.k;
             S->sec.push_back(sc);
+            // FP64 GEMMs on column-major matrices, as row-major products of transposes:
+            // G[i][j] = sum_l V[l,i] V[l,j]
+            {
+                heff::BProd p{};
+                p.a_off = sc.v_off; p.a_rs = sc.k; p.a_cs = 1;
+                p.b_off = sc.v_off; p.b_rs = 1; p.b_cs = sc.k;
+                p.K = sc.k; p.c1 = -1; p.c2 = -1;
+                S->gram.add_block(sc.g_off, sc.k, sc.k, sc.k, {p});
+            }
+            // W = V G (column-major W[i,j] = row j, column i of W^T): W^T[j][i] = sum_l G[l,j] V[i,l]
+            {
+                heff::BProd p{};
+                p.a_off = sc.g_off; p.a_rs = sc.k; p.a_cs = 1;
+                p.b_off = sc.v_off; p.b_rs = sc.k; p.b_cs = 1;
+                p.K = sc.k; p.c1 = -1; p.c2 = -1;
+                S->vg.add_block(sc.w_off, sc.k, sc.k, sc.k, {p});
+            }
+            // W = J V (r x k): W^T[j][i] = sum_l V[l,j] J[i,l]
+            {
+                heff::BProd p{};
+                p.a_off = sc.v_off; p.a_rs = sc.k; p.a_cs = 1;
+                p.b_off = sc.j_off; p.b_rs = sc.r; p.b_cs = 1;
+                p.K = sc.k; p.c1 = -1; p.c2 = -1;
+                S->jv.add_block(sc.w_off, sc.r, sc.k, sc.r, {p});
+            }
             S->max_k = std::max(S->max_k, sc.k);
         }
         S->s_total = so;
@@ -265,7 +381,12 @@ extern "C" int heff_svd_create(const heff_layout* x, heff_svd** out) {
         }
         S->xoff.assign(1, tab);   // stash the load table (one entry)
         S->ws_doubles = o + so + 64;
-        S->ws_bytes = (size_t)S->ws_doubles * sizeof(double) + tab.size() * sizeof(int64_t) + 1024;
+        const int kk = S->max_k + (S->max_k & 1);
+        S->slot_ld = std::max(1, kk / 2);
+        S->nslots = (int64_t)nsec * S->slot_ld;
+        S->off_slots = ((size_t)S->ws_doubles * sizeof(double) + tab.size() * sizeof(int64_t) + 255) / 256 * 256;
+        S->off_f32 = (S->off_slots + (size_t)(S->nslots + 64) * sizeof(float) + 255) / 256 * 256;
+        S->ws_bytes = S->off_f32 + (size_t)o32 * sizeof(float) + 1024;
     } catch (const std::bad_alloc&) {
         delete S;
         return fail(HEFF_ERR_OOM, "out of host memory in heff_svd_create");
@@ -296,7 +417,8 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* ws = static_cast<double*>(workspace);
     double* sv = ws + (S->ws_doubles - S->s_total - 64);
-    unsigned int* offmax = reinterpret_cast<unsigned int*>(ws + S->ws_doubles - 8);
+    float* slots = reinterpret_cast<float*>(static_cast<char*>(workspace) + S->off_slots);
+    float* offmax = slots + S->nslots;
     const std::vector<int64_t>& tab = S->xoff[0];
     int64_t* d_tab = reinterpret_cast<int64_t*>(ws + S->ws_doubles);
     const int nsec = (int)S->sec.size();
@@ -304,24 +426,55 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
     SVD_CK(cudaMemcpyAsync(S->d_sec, S->sec.data(), S->sec.size() * sizeof(SvdSector), cudaMemcpyHostToDevice, st));
     SVD_CK(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     const int ntab = (int)(tab.size() / 6);
+    float* f32 = reinterpret_cast<float*>(static_cast<char*>(workspace) + S->off_f32);
     if (ntab) svd_load_kernel<<<std::min(ntab, 4096), 256, 0, st>>>(S->d_sec, d_tab, ntab, x, ws);
-    svd_init_v_kernel<<<dim3(64, nsec), 256, 0, st>>>(S->d_sec, ws);
+    svd_to_f32_kernel<<<dim3(128, nsec), 256, 0, st>>>(S->d_sec, ws, f32);
     heff::count_launches(2);
-    const int kk = S->max_k + (S->max_k & 1);
-    const int gx = (kk / 2 + 3) / 4;
-    int sweep = 0;
-    for (; sweep < 40 && kk >= 2; ++sweep) {
-        SVD_CK(cudaMemsetAsync(offmax, 0, sizeof(unsigned int), st));
-        for (int r = 0; r < kk - 1; ++r)
-            svd_round_kernel<<<dim3(std::max(gx, 1), nsec), 128, 0, st>>>(S->d_sec, ws, r, offmax);
-        heff::count_launches(kk - 1);
-        unsigned int h = 0;
-        SVD_CK(cudaMemcpyAsync(&h, offmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-        SVD_CK(cudaStreamSynchronize(st));
-        float m;
-        std::memcpy(&m, &h, sizeof(float));
-        if (m < 1e-14f) { ++sweep; break; }
+    if (!S->lists_uploaded) {
+        int rc = HEFF_OK;
+        for (heff::BList* b : {&S->gram, &S->vg, &S->jv})
+            if (!rc) rc = heff::blist_upload(*b);
+        if (rc) return rc;
+        S->lists_uploaded = true;
     }
+    // Jacobi sweeps until the largest off-diagonal measure is below tol: every round is one
+    // launch over all sectors (a sector whose own rounds are done returns at once)
+    const int kk_all = S->max_k + (S->max_k & 1);
+    auto sweeps = [&](auto* base, float tol, int max_sweeps, int& out) -> int {
+        out = 0;
+        const int gx = std::max(1, kk_all / 2);
+        while (out < max_sweeps && kk_all >= 2) {
+            SVD_CK(cudaMemsetAsync(slots, 0, (size_t)S->nslots * sizeof(float), st));
+            for (int r = 0; r < kk_all - 1; ++r)
+                svd_round_kernel<<<dim3(gx, nsec), SVD_NT, 0, st>>>(S->d_sec, base, r, slots, (int)S->slot_ld);
+            svd_offmax_kernel<<<1, 256, 0, st>>>(slots, (int)S->nslots, offmax);
+            heff::count_launches(kk_all);
+            float m = 0.f;
+            SVD_CK(cudaMemcpyAsync(&m, offmax, sizeof(float), cudaMemcpyDeviceToHost, st));
+            SVD_CK(cudaStreamSynchronize(st));
+            ++out;
+            if (m < tol) break;
+        }
+        return HEFF_OK;
+    };
+    int rc;
+    // FP32 preconditioning sweeps (to FP32 accuracy of the dot products)
+    if ((rc = sweeps(f32, 1e-5f, 30, S->fp32_sweeps))) return rc;
+    // V = orthonormalised double(V32), J = J V
+    svd_v_to_f64_kernel<<<dim3(128, nsec), 256, 0, st>>>(S->d_sec, f32, ws);
+    heff::count_launches(1);
+    for (int it = 0; it < 2; ++it) {
+        if ((rc = heff::launch_bgemm(S->gram, ws, ws, ws, nullptr, nullptr, 1.0, stream))) return rc;
+        if ((rc = heff::launch_bgemm(S->vg, ws, ws, ws, nullptr, nullptr, -0.5, stream))) return rc;
+        svd_ns_kernel<<<dim3(128, nsec), 256, 0, st>>>(S->d_sec, ws);
+        heff::count_launches(1);
+    }
+    if ((rc = heff::launch_bgemm(S->jv, ws, ws, ws, nullptr, nullptr, 1.0, stream))) return rc;
+    svd_copy_w_kernel<<<dim3(128, nsec), 256, 0, st>>>(S->d_sec, ws);
+    heff::count_launches(1);
+    // FP64 sweeps to convergence
+    if ((rc = sweeps(ws, 1e-14f, 40, S->fp64_sweeps))) return rc;
+    const int sweep = S->fp64_sweeps;
     svd_norms_kernel<<<dim3((S->max_k + 3) / 4 + 1, nsec), 128, 0, st>>>(S->d_sec, ws, sv);
     heff::count_launches(1);
     S->s.assign(S->s_total, 0.0);
@@ -331,6 +484,14 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
     if (sweeps_out) *sweeps_out = sweep;
     S->computed = true;
     S->kept.clear();
+    return HEFF_OK;
+}
+
+extern "C" int heff_svd_info(const heff_svd* S, int32_t* fp32_sweeps, int32_t* fp64_sweeps) {
+    heff::clear_error();
+    if (!S) return fail(HEFF_ERR_INVALID_ARG, "heff_svd_info: null argument");
+    if (fp32_sweeps) *fp32_sweeps = S->fp32_sweeps;
+    if (fp64_sweeps) *fp64_sweeps = S->fp64_sweeps;
     return HEFF_OK;
 }
 
@@ -454,12 +615,9 @@ extern "C" int heff_svd_write(heff_svd* S, const heff_layout* A_layout, const he
             ents.push_back({off, nkeep, S->beta_dims[std::get<1>(t)], (int32_t)q, std::get<2>(t), koff[q], 0});
         }
     }
-    // tables after the load table in the workspace tail
-    char* tail = reinterpret_cast<char*>(ws + S->ws_doubles) + S->xoff[0].size() * sizeof(int64_t);
-    // the write tables need their own room: use a temporary device buffer owned by the plan
+    // the write tables (sized by the truncation) go to temporary device buffers
     WriteEntry* d_ent = nullptr;
     int32_t* d_kept = nullptr;
-    (void)tail;
     SVD_CK(cudaMalloc((void**)&d_ent, std::max<size_t>(1, ents.size()) * sizeof(WriteEntry)));
     SVD_CK(cudaMalloc((void**)&d_kept, std::max<size_t>(1, keptflat.size()) * sizeof(int32_t)));
     SVD_CK(cudaMemcpyAsync(d_ent, ents.data(), ents.size() * sizeof(WriteEntry), cudaMemcpyHostToDevice, st));
@@ -477,5 +635,8 @@ extern "C" int heff_svd_write(heff_svd* S, const heff_layout* A_layout, const he
 extern "C" void heff_svd_destroy(heff_svd* S) {
     if (!S) return;
     cudaFree(S->d_sec);
+    heff::blist_free(S->gram);
+    heff::blist_free(S->vg);
+    heff::blist_free(S->jv);
     delete S;
 }

@@ -14,6 +14,11 @@
 //   warp 1      allocates TMEM (2 x TN columns); one thread issues the MMAs
 //   warps 2..5  epilogue: TMEM -> registers -> global (T as hi/lo planes, or y)
 // Accumulators are double buffered so a tile's epilogue overlaps the next tile's MMAs.
+// Long contractions (GEMM 2) are accumulated in chunks of kchunk K blocks: each chunk
+// starts a fresh accumulator and the epilogue adds the chunks into y in a fixed order with
+// round-to-nearest adds.  The tensor cores' FP32 accumulation drops low bits at every step,
+// which biases a long sum toward zero (relative bias growing with the number of steps);
+// chunking bounds the steps per accumulator.
 // T (GEMM 1) leaves through TMA: each warp splits 32 rows x 32 columns into hi/lo in
 // registers, writes them to a swizzled shared-memory box and issues bulk tensor stores;
 // quarters with fewer than 32 valid rows, and y (GEMM 2, per-block pitch), are stored
@@ -196,6 +201,7 @@ struct TcArgs {
     int c_batch_rows, c_plane_rows;       // the same in rows of the T store map
     PtrBatch y;                           // mode 1: outputs per batch entry
     int mode;                             // 0: write T planes, 1: write y
+    int kchunk;                           // K blocks per accumulation chunk (0: whole tile)
     int y_f64;                            // y element type (mode 1)
     int b0;                               // first batch entry of this launch
     int* err;                             // sticky error flag in the workspace
@@ -264,20 +270,34 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
         constexpr uint32_t FMT = PREC == HEFF_PREC_BF16X3 ? 1u : 2u;
-        uint32_t it = 0, tcount = 0;
+        const int CH = g.kchunk > 0 ? g.kchunk : 0x7fffffff;
+        uint32_t it = 0, ccount = 0;           // ring position, accumulator chunk counter
         bool ok = true;
-        for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x, ++tcount) {
+        for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x) {
             const GemmTask t = g.tasks[gi % g.ntasks];
-            const uint32_t acc = tcount & 1, use = tcount >> 1;
-            if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
-            tc_fence_after();
-            const uint32_t d = tmem + acc * TN;
+            if (t.seg_count == 0) {            // nothing to contract: the epilogue writes zeros
+                const uint32_t acc = ccount & 1, use = ccount >> 1;
+                if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
+                mbar_arrive(&tfull[acc]);
+                ++ccount;
+                continue;
+            }
+            const int nkb = t.ktotal / KB;
             const uint32_t nmma = t.n <= 16 ? 16u : (uint32_t)((t.n + 15) & ~15);
             const uint32_t id = idesc(FMT, TM, nmma);
-            uint32_t first = 1;
+            uint32_t first = 1, acc = 0, d = 0;
+            int kb = 0;
             for (int s = 0; s < t.seg_count && ok; ++s) {
                 const KSeg sg = g.segs[t.seg_begin + s];
                 for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
+                    if (kb % CH == 0) {        // a new accumulation chunk
+                        acc = ccount & 1;
+                        const uint32_t use = ccount >> 1;
+                        if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
+                        tc_fence_after();
+                        d = tmem + acc * TN;
+                        first = 1;
+                    }
                     const int st = it % STAGES;
                     if (!(ok = mbar_wait(&full[st], (it / STAGES) & 1, abort_flag, g.err))) break;
                     tc_fence_after();
@@ -294,11 +314,12 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                         first = 0;
                     }
                     umma_commit(&empty[st]);
+                    if (++kb % CH == 0 || kb == nkb) {
+                        umma_commit(&tfull[acc]);
+                        ++ccount;
+                    }
                 }
             }
-            if (!ok) break;
-            if (t.seg_count == 0) mbar_arrive(&tfull[acc]);
-            else umma_commit(&tfull[acc]);
         }
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
@@ -314,12 +335,16 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         uint8_t* slot = smem + S::EPI_OFF + q * S::EPI_WARP;
         float (*stage)[33] = reinterpret_cast<float (*)[33]>(slot);
         const uint32_t slot_s = su32(slot);
-        uint32_t tcount = 0, nstore = 0;
-        for (long gi = blockIdx.x; gi < total; gi += gridDim.x, ++tcount) {
+        const int CH = g.kchunk > 0 ? g.kchunk : 0x7fffffff;
+        uint32_t ccount = 0, nstore = 0;
+        bool live = true;
+        for (long gi = blockIdx.x; gi < total && live; gi += gridDim.x) {
             const GemmTask t = g.tasks[gi % g.ntasks];
             const int brel = (int)(gi / g.ntasks), b = g.b0 + brel;
-            const uint32_t acc = tcount & 1, use = tcount >> 1;
-            if (!mbar_wait(&tfull[acc], use & 1, abort_flag, g.err)) break;
+            const int nch = (t.seg_count > 0 && CH != 0x7fffffff) ? (t.ktotal / KB + CH - 1) / CH : 1;
+          for (int ch = 0; ch < nch; ++ch) {
+            const uint32_t acc = ccount & 1, use = ccount >> 1;
+            if (!mbar_wait(&tfull[acc], use & 1, abort_flag, g.err)) { live = false; break; }
             tc_fence_after();
             const int ncols = t.n + t.n_zero;
             const int rows = t.m - q * 32 < 32 ? t.m - q * 32 : 32;   // valid rows of this warp
@@ -418,13 +443,28 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                         }
                     }
                 } else if (c < t.n) {
+                    // chunk 0 stores, later chunks add (same thread, same order: deterministic);
+                    // the previous values of all 32 rows are loaded before any store so the
+                    // loads overlap
                     const int64_t o0 = t.c_off + c;
                     if (g.y_f64) {
                         double* y = static_cast<double*>(const_cast<void*>(g.y.p[brel])) + o0;
-                        for (int rr = 0; rr < rows; ++rr) y[(int64_t)(q * 32 + rr) * t.ldc] = (double)stage[rr][lane];
+                        double old[32];
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr)
+                            old[rr] = (ch && rr < rows) ? y[(int64_t)(q * 32 + rr) * t.ldc] : 0.0;
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr)
+                            if (rr < rows) y[(int64_t)(q * 32 + rr) * t.ldc] = old[rr] + (double)stage[rr][lane];
                     } else {
                         float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o0;
-                        for (int rr = 0; rr < rows; ++rr) y[(int64_t)(q * 32 + rr) * t.ldc] = stage[rr][lane];
+                        float old[32];
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr)
+                            old[rr] = (ch && rr < rows) ? y[(int64_t)(q * 32 + rr) * t.ldc] : 0.f;
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr)
+                            if (rr < rows) y[(int64_t)(q * 32 + rr) * t.ldc] = old[rr] + stage[rr][lane];
                     }
                 }
                 __syncwarp();
@@ -432,6 +472,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
+            ++ccount;
+          }
         }
         if (lane == 0) bulk_wait_all();      // T complete before the CTA (and its boxes) go away
         __syncwarp();
@@ -477,6 +519,18 @@ int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, u
 // Kernel configurations: 64-byte K blocks; N tile 256 with a 4-stage ring (4 x 48 KB,
 // 512 TMEM columns) or N tile 128 with a 6-stage ring (6 x 32 KB, 256 TMEM columns).
 constexpr int SWZ_TC = 64;
+// K blocks per accumulation chunk in GEMM 2 (32 bf16 / 16 tf32 elements per block): long
+// enough that a chunk's MMAs (about 0.5 us per block at N = 256) hide the epilogue's
+// read-add-write of the previous chunk, short enough to bound the accumulation bias
+// (measured at m = 4096: norm-wise error of y 1.4e-5 -> 5e-6 (bf16x3), 2.6e-5 -> 3e-6 (tf32x3))
+#ifndef HEFF_KCHUNK_BF16
+#define HEFF_KCHUNK_BF16 128
+#endif
+#ifndef HEFF_KCHUNK_TF32
+#define HEFF_KCHUNK_TF32 32
+#endif
+constexpr int KCHUNK_BF16 = HEFF_KCHUNK_BF16;
+constexpr int KCHUNK_TF32 = HEFF_KCHUNK_TF32;
 
 template <int PREC, int TN_TC>
 int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
@@ -540,6 +594,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
             g.a_batch_rows = p->rows_t; g.b_batch_rows = 0;
             for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
             g.mode = 1;
+            g.kchunk = PREC == HEFF_PREC_TF32X3 ? KCHUNK_TF32 : KCHUNK_BF16;
             g.y_f64 = p->opts.io_dtype == HEFF_DTYPE_F64;
         }
         const long total = (long)g.ntasks * nb;

@@ -42,7 +42,7 @@ class _Index(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("io_dtype", C.c_int32), ("max_batch", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("shard_count", C.c_int32), ("shard_index", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 _vp, _i32, _i64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
@@ -55,6 +55,12 @@ _sig = {
     "heff_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_double), _P(C.c_double),
                                    _P(_Opts), _P(_vp)]),
     "heff_plan_workspace_size": (C.c_int, [_vp, _P(_sz)]),
+    "heff_plan_shard_sectors": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_int32)]),
+    "heff_plan_select_tiles": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "heff_two_site_create": (C.c_int, [_vp, _vp, _vp, _P(_vp)]),
+    "heff_svd_info": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_int32)]),
+    "heff_two_site_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "heff_two_site_destroy": (None, [_vp]),
     "heff_plan_flops": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double)]),
     "heff_plan_stats": (C.c_int, [_vp, _P(_i64)]),
     "heff_plan_export": (C.c_int, [_vp, _i32, _vp, _P(_i64)]),
@@ -84,7 +90,7 @@ _sig = {
     "heff_env_plan_destroy": (None, [_vp]),
     "heff_lanczos_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
     "heff_lanczos": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
-    "heff_plan_autotune": (C.c_int, [_vp] * 8 + [_sz, _vp, _P(_i32)]),
+    "heff_plan_autotune": (C.c_int, [_vp] * 8 + [_sz, _vp, _P(_i32), _P(C.c_float)]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
     "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
     "heff_last_error": (C.c_char_p, []),
@@ -161,15 +167,31 @@ def heff_layout_destroy(lay):
 
 
 def heff_plan_create(L, W1, W2, R, x, W1_host, W2_host, precision="bf16x3", io_dtype="f32",
-                     max_batch=1):
+                     max_batch=1, shard=None):
+    """shard = (index, count) builds the plan of one row shard (left sectors of y)."""
     w1 = np.ascontiguousarray(W1_host, dtype=np.float64)
     w2 = np.ascontiguousarray(W2_host, dtype=np.float64)
-    opts = _Opts(PREC[precision], DTYPE[io_dtype], int(max_batch))
+    si, sc = (0, 0) if shard is None else (int(shard[0]), int(shard[1]))
+    opts = _Opts(PREC[precision], DTYPE[io_dtype], int(max_batch), sc, si)
     out = _vp()
     _check(_lib.heff_plan_create(L, W1, W2, R, x, w1.ctypes.data_as(_P(C.c_double)),
                                  w2.ctypes.data_as(_P(C.c_double)), C.byref(opts), C.byref(out)),
            "heff_plan_create")
     return out
+
+
+def heff_plan_shard_sectors(plan):
+    n = C.c_int32()
+    _check(_lib.heff_plan_shard_sectors(plan, None, C.byref(n)), "heff_plan_shard_sectors")
+    out = np.zeros(n.value, dtype=np.int32)
+    if n.value:
+        _check(_lib.heff_plan_shard_sectors(plan, out.ctypes.data_as(_P(C.c_int32)), C.byref(n)),
+               "heff_plan_shard_sectors")
+    return out
+
+
+def heff_plan_select_tiles(plan, tn1=0, tn2=0):
+    _check(_lib.heff_plan_select_tiles(plan, int(tn1), int(tn2)), "heff_plan_select_tiles")
 
 
 def heff_plan_workspace_size(plan):
@@ -203,7 +225,8 @@ TABLE_DTYPES = {
                  ("term_count", "<i4"), ("which", "<i4"), ("_pad", "<i4")]),
     2: np.dtype([("src_off", "<i8"), ("w_idx", "<i4"), ("_pad", "<i4")]),
     3: np.dtype([("a_row", "<i8"), ("b_row", "<i8"), ("c_off", "<i8"), ("m", "<i4"), ("n", "<i4"),
-                 ("ldc", "<i4"), ("n_zero", "<i4"), ("seg_begin", "<i4"), ("seg_count", "<i4")]),
+                 ("ldc", "<i4"), ("n_zero", "<i4"), ("seg_begin", "<i4"), ("seg_count", "<i4"),
+                 ("ktotal", "<i4"), ("_pad", "<i4")]),
     4: np.dtype([("k0", "<i4"), ("klen", "<i4")]),
 }
 TABLE_DTYPES[5] = TABLE_DTYPES[3]
@@ -278,6 +301,13 @@ def heff_svd_truncate(s, m_max, cutoff, nq, max_sectors):
     return q[:n * nq].reshape(n, nq), d[:n], disc.value, nrm.value
 
 
+def heff_svd_info(s):
+    """(FP32 preconditioning sweeps, FP64 sweeps) of the last heff_svd_compute."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(_lib.heff_svd_info(s, C.byref(a), C.byref(b)), "heff_svd_info")
+    return a.value, b.value
+
+
 def heff_svd_singular_values(s, n):
     out = np.zeros(n, dtype=np.float64)
     _check(_lib.heff_svd_singular_values(s, out.ctypes.data_as(_P(C.c_double))), "heff_svd_singular_values")
@@ -291,6 +321,20 @@ def heff_svd_write(s, A_layout, B_layout, A, B, absorb_right, ws, stream=None):
 
 def heff_svd_destroy(s):
     _lib.heff_svd_destroy(s)
+
+
+def heff_two_site_create(A, B, x):
+    out = _vp()
+    _check(_lib.heff_two_site_create(A, B, x, C.byref(out)), "heff_two_site_create")
+    return out
+
+
+def heff_two_site_apply(plan, A, B, x, stream=None):
+    _check(_lib.heff_two_site_apply(plan, _ptr(A), _ptr(B), _ptr(x), _stream(stream)), "heff_two_site_apply")
+
+
+def heff_two_site_destroy(plan):
+    _lib.heff_two_site_destroy(plan)
 
 
 def heff_grad_plan_create(L, W1, W2, R, x, W1_host, W2_host, ws_limit=0):
@@ -380,11 +424,16 @@ def heff_apply_noalloc(plan, L, W1, W2, R, x, y, stream=None):
                                    _stream(stream)), "heff_apply_noalloc")
 
 
-def heff_plan_autotune(plan, L, W1, W2, R, x, y, ws, stream=None):
-    """Pick the faster N tile (256 or 128) per GEMM on these inputs; returns (tn1, tn2)."""
+def heff_plan_autotune(plan, L, W1, W2, R, x, y, ws, stream=None, times=None):
+    """Pick the faster N tile (256 or 128) per GEMM on these inputs; returns (tn1, tn2).
+    If `times` is a list, the median times {GEMM 1 at 256, 128, GEMM 2 at 256, 128} (ms)
+    are appended to it."""
     tn = (_i32 * 2)()
+    ms = (C.c_float * 4)()
     _check(_lib.heff_plan_autotune(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y), _ptr(ws),
-                                   _nbytes(ws), _stream(stream), tn), "heff_plan_autotune")
+                                   _nbytes(ws), _stream(stream), tn, ms), "heff_plan_autotune")
+    if times is not None:
+        times.extend(float(v) for v in ms)
     return int(tn[0]), int(tn[1])
 
 
@@ -477,11 +526,11 @@ class Plan:
     """Owner of a heff_plan built from the five layouts and host MPO values."""
 
     def __init__(self, L, W1, W2, R, x, W1_host, W2_host, precision="bf16x3", io_dtype="f32",
-                 max_batch=1):
+                 max_batch=1, shard=None):
         self.layouts = (L, W1, W2, R, x)
         self.precision, self.io_dtype, self.max_batch = precision, io_dtype, max_batch
         self.handle = heff_plan_create(L.handle, W1.handle, W2.handle, R.handle, x.handle,
-                                       W1_host, W2_host, precision, io_dtype, max_batch)
+                                       W1_host, W2_host, precision, io_dtype, max_batch, shard)
         self.workspace_bytes = heff_plan_workspace_size(self.handle)
         self.flops_canonical, self.flops_executed = heff_plan_flops(self.handle)
         self.stats = heff_plan_stats(self.handle)

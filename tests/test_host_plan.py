@@ -136,3 +136,86 @@ def test_gradient_workspace_limit_splits_left_sectors():
         make(int(whole * 0.05))
     assert e.value.code == -7
     assert "minimum" in heff.heff_last_error()
+
+
+def _row_block_mask(xl, sectors):
+    """Flat mask of the y blocks whose left sector is in `sectors`."""
+    mask = np.zeros(xl.nelem, dtype=bool)
+    for key, off, size in xl.blocks():
+        if key[0] in set(int(s) for s in sectors):
+            mask[off:off + size] = True
+    return mask
+
+
+@pytest.mark.parametrize("name,prec,S", [("spin_m64", "fp64", 3), ("electron_m40", "bf16x3", 2),
+                                         ("electron_m96", "fp64", 5)])
+def test_row_shards_partition_and_sum_to_oracle(name, prec, S):
+    """Row shards own disjoint left sectors covering y; each writes exactly its blocks,
+    and the sum of the shards' outputs is the oracle's y."""
+    w = wl.workload_by_name(name)
+    lays, bufs = library_problem(w)
+    Ll, W1l, W2l, Rl, xl = lays
+    io = "f64" if prec == "fp64" else "f32"
+    whole = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, io)
+    L, W1, W2, R, x = oh.problem_from_workload(w)
+    y_ref = oracle_flat(xl, oh.heff_apply(L, W1, W2, R, x))
+    total = np.zeros(xl.nelem)
+    seen, canon = [], 0.0
+    for r in range(S):
+        P = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, io, shard=(r, S))
+        secs = heff.heff_plan_shard_sectors(P.handle)
+        seen.extend(int(s) for s in secs)
+        canon += P.flops_canonical
+        y = interpret_plan(P, bufs, bufs["x"][0])
+        mine = _row_block_mask(xl, secs)
+        assert not np.isnan(y[mine]).any()
+        assert np.isnan(y[~mine]).all()            # other shards' blocks are not written
+        total[mine] += y[mine]
+    assert sorted(seen) == list(range(len(w.alpha_d)))
+    assert canon == pytest.approx(whole.flops_canonical, rel=1e-12)
+    assert np.abs(total - y_ref).max() < 1e-12 * np.abs(y_ref).max()
+
+
+def test_row_shard_arguments_checked():
+    w = wl.workload_by_name("spin_m24")
+    lays, bufs = library_problem(w)
+    for shard in ((2, 2), (-1, 2), (1, 0)):
+        with pytest.raises(heff.HeffError) as e:
+            heff.Plan(*lays, bufs["W1"], bufs["W2"], "fp64", "f64", shard=shard)
+        assert e.value.code == -1
+    P = heff.Plan(*lays, bufs["W1"], bufs["W2"], "fp64", "f64", shard=(0, 1))
+    assert list(heff.heff_plan_shard_sectors(P.handle)) == list(range(len(w.alpha_d)))
+
+
+def test_select_tiles_swaps_task_lists():
+    """Both tile widths are planned; selecting one swaps its task list in (the schedule
+    still reproduces the oracle), unknown widths and FP64 plans are refused."""
+    w = wl.workload_by_name("spin_m64")
+    lays, bufs = library_problem(w)
+    P = _plan(w, lays, bufs, "bf16x3", "f32")
+    assert (P.stats[15], P.stats[22]) == (256, 256)
+    heff.heff_plan_select_tiles(P.handle, 128, 128)
+    st = heff.heff_plan_stats(P.handle)
+    assert (st[15], st[22]) == (128, 128)
+    P.stats = st
+    L, W1, W2, R, x = oh.problem_from_workload(w)
+    y_ref = oracle_flat(lays[4], oh.heff_apply(L, W1, W2, R, x))
+    y = interpret_plan(P, bufs, bufs["x"][0])
+    assert np.abs(y - y_ref).max() < 1e-12 * np.abs(y_ref).max()
+    with pytest.raises(heff.HeffError):
+        heff.heff_plan_select_tiles(P.handle, 64, 0)
+    P64 = _plan(w, lays, bufs, "fp64", "f64")
+    with pytest.raises(heff.HeffError):
+        heff.heff_plan_select_tiles(P64.handle, 128, 0)
+
+
+def test_product_state_reaches_total_charge():
+    from paper_2007_05540_gb300 import dmrg
+    sp = wl.spin_phys()
+    st = dmrg.product_state(sp, 16, (0,))
+    assert sum(int(sp[s][0]) for s in st) == 0 and len(st) == 16
+    el = wl.electron_phys()
+    st = dmrg.product_state(el, 6, (6, 0))
+    assert tuple(map(int, el[st].sum(axis=0))) == (6, 0)
+    with pytest.raises(ValueError):
+        dmrg.product_state(sp, 3, (0,))          # odd chain cannot reach 2Sz = 0
