@@ -216,7 +216,12 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
         if (count_below(mid) >= 1) hi = mid; else lo = mid;
     }
     const double theta = 0.5 * (lo + hi);
-    // inverse iteration: (T - theta I) z_new = z, banded LU with partial pivoting
+    // inverse iteration: (T - theta I) z_new = z, banded LU with partial pivoting.  A pivot
+    // below tiny (theta is an eigenvalue to rounding, so one pivot is ~0: exactly 0 when
+    // n = 1) is replaced by +-tiny, and z is rescaled by its largest entry before it is
+    // normalised, so the large solution neither overflows nor turns into NaN.
+    const double tiny = 1e-15 * scale;
+    auto guard = [&](double v) { return fabs(v) < tiny ? (v < 0.0 ? -tiny : tiny) : v; };
     double* dl = T;              // sub-diagonal / multipliers
     double* dd = T + nmax;       // diagonal
     double* du = T + 2 * nmax;   // first super-diagonal
@@ -231,7 +236,7 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
         }
         for (int i = 0; i + 1 < n; ++i) {
             if (fabs(dd[i]) >= fabs(dl[i])) {              // no row swap
-                if (dd[i] == 0.0) dd[i] = 1e-300 * scale;
+                dd[i] = guard(dd[i]);
                 const double f = dl[i] / dd[i];
                 dl[i] = f;
                 dd[i + 1] -= f * du[i];
@@ -252,7 +257,7 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
                 s[i + 1] = sv - f * s[i + 1];
             }
         }
-        if (dd[n - 1] == 0.0) dd[n - 1] = 1e-300 * scale;
+        dd[n - 1] = guard(dd[n - 1]);
         // back substitution
         for (int i = n - 1; i >= 0; --i) {
             double v = s[i];
@@ -260,8 +265,14 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
             if (i + 2 < n) v -= du2[i] * s[i + 2];
             s[i] = v / dd[i];
         }
+        double mx = 0.0;
+        for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(s[i]));
+        if (!(mx > 0.0) || !isfinite(mx)) {           // cannot happen with the guards; keep e_0
+            for (int i = 0; i < n; ++i) s[i] = i == 0 ? 1.0 : 0.0;
+            break;
+        }
         double nr = 0.0;
-        for (int i = 0; i < n; ++i) nr += s[i] * s[i];
+        for (int i = 0; i < n; ++i) { s[i] /= mx; nr += s[i] * s[i]; }
         nr = sqrt(nr);
         for (int i = 0; i < n; ++i) s[i] /= nr;
     }

@@ -120,3 +120,18 @@ def test_lanczos_rejects_f32_plans():
     with pytest.raises(heff.HeffError) as e:
         heff.heff_lanczos(P.handle, t, t, t, t, t, 5, t, t, ws, ws)
     assert e.value.code == -3
+
+
+def test_restart_from_converged_vector_breaks_down_cleanly():
+    """Started from a converged Ritz vector the Krylov space is invariant after one step
+    (the situation at the turn of a DMRG sweep): the result must be that vector and its
+    Rayleigh quotient, finite, with a Krylov dimension of 1."""
+    p = LzProblem("spin_m24")
+    res, x = p.lanczos("fp64", min(120, p.lays[4].nelem))
+    p.x0 = x.clone()
+    res2, x2 = p.lanczos("fp64", 10)
+    assert np.isfinite(res2[:3]).all() and torch.isfinite(x2).all()
+    assert res2[2] <= 2
+    assert abs(res2[0] - res[0]) < 1e-10 * abs(res[0])
+    ov = abs(float(torch.dot(x2, x)))
+    assert ov > 1 - 1e-10, ov
