@@ -27,6 +27,7 @@
 #include <new>
 #include <numeric>
 #include <tuple>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -75,6 +76,7 @@ struct heff_svd {
     heff::BList gram, vg, jv;                  // G = V^T V, W = V G, W = J V (all sectors)
     bool lists_uploaded = false;
     int fp32_sweeps = 0, fp64_sweeps = 0;
+    std::vector<int> pair_off;                 // prefix sums of the sectors' pair counts
     int max_k = 0;
     bool computed = false;
     int alpha_nsec = 0, beta_nsec = 0;
@@ -108,76 +110,6 @@ __global__ void svd_load_kernel(const SvdSector* __restrict__ secs, const int64_
     }
 }
 
-
-// one round of the round-robin ordering: block x of the launch rotates pair x of sector y.
-// A whole block per pair (columns of up to a few thousand doubles): the three dot products
-// are block reductions in a fixed order, then every thread rotates its elements of the two
-// columns of J and of V.
-constexpr int SVD_NT = 256;
-
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& g, double (*sh)[3]) {
-    a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sh[w][0] = a; sh[w][1] = b; sh[w][2] = g; }
-    __syncthreads();
-    a = b = g = 0.0;
-    for (int i = 0; i < SVD_NT / 32; ++i) { a += sh[i][0]; b += sh[i][1]; g += sh[i][2]; }
-}
-
-// off: one slot per (sector, pair position) holding the largest off-diagonal measure seen in
-// this sweep; each slot has one writer per round (its block), so no atomics.  T = double
-// works on (J, V) in the FP64 region, T = float on (J32, V32) in the FP32 region.
-template <typename T>
-__global__ void __launch_bounds__(SVD_NT) svd_round_kernel(const SvdSector* __restrict__ secs, T* __restrict__ base,
-                                                           int round, float* __restrict__ off, int off_ld) {
-    __shared__ double sh[SVD_NT / 32][3];
-    constexpr bool F32 = sizeof(T) == 4;
-    const SvdSector s = secs[blockIdx.y];
-    const int kk = s.k + (s.k & 1);                   // padded to even (dummy column = k)
-    if (kk < 2 || round >= kk - 1) return;
-    const int pair = blockIdx.x;
-    if (pair >= kk / 2) return;
-    auto pos = [&](int j) { return j == 0 ? 0 : 1 + (j - 1 + round) % (kk - 1); };
-    int p = pos(pair), q = pos(kk - 1 - pair);
-    if (p >= s.k || q >= s.k) return;                 // pair with the dummy column
-    if (p > q) { const int t = p; p = q; q = t; }
-    T* J = base + (F32 ? s.j32_off : s.j_off);
-    T* cp = J + (int64_t)p * s.r;
-    T* cq = J + (int64_t)q * s.r;
-    T a = 0, b = 0, g = 0;
-    for (int i = threadIdx.x; i < s.r; i += SVD_NT) {
-        const T u = cp[i], v = cq[i];
-        a = fma(u, u, a);
-        b = fma(v, v, b);
-        g = fma(u, v, g);
-    }
-    double da = a, db = b, dg = g;
-    block_sum3(da, db, dg, sh);
-    if (dg == 0.0 || da == 0.0 || db == 0.0) return;  // block-uniform
-    const double meas = fabs(dg) / sqrt(da * db);
-    if (threadIdx.x == 0) {
-        float* o = off + (int64_t)blockIdx.y * off_ld + pair;
-        *o = fmaxf(*o, (float)meas);
-    }
-    if (meas < (F32 ? 1e-7 : 1e-15)) return;
-    const double zeta = (db - da) / (2.0 * dg);
-    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double cd = 1.0 / sqrt(1.0 + t * t);
-    const T c = (T)cd, sn = (T)(cd * t);
-    for (int i = threadIdx.x; i < s.r; i += SVD_NT) {
-        const T u = cp[i], v = cq[i];
-        cp[i] = c * u - sn * v;
-        cq[i] = sn * u + c * v;
-    }
-    T* V = base + (F32 ? s.v32_off : s.v_off);
-    T* vp = V + (int64_t)p * s.k;
-    T* vq = V + (int64_t)q * s.k;
-    for (int i = threadIdx.x; i < s.k; i += SVD_NT) {
-        const T u = vp[i], v = vq[i];
-        vp[i] = c * u - sn * v;
-        vq[i] = sn * u + c * v;
-    }
-}
 
 // J32 = float(J), V32 = I
 __global__ void svd_to_f32_kernel(const SvdSector* __restrict__ secs, const double* __restrict__ ws,
@@ -216,6 +148,123 @@ __global__ void svd_copy_w_kernel(const SvdSector* __restrict__ secs, double* __
     const int64_t nj = (int64_t)s.r * s.k;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nj; e += (int64_t)gridDim.x * blockDim.x)
         ws[s.j_off + e] = ws[s.w_off + e];
+}
+
+// One sweep (all rounds) as one cooperative launch: the warps of the grid take the
+// (sector, pair) items of a round from a flattened list (pair_off: prefix sums of each
+// sector's pair count), rotate, and meet at a grid barrier before the next round.  The
+// barrier is a counter and a generation word in global memory; its wait is bounded (about a
+// second), after which the kernel sets err and returns.  Each block writes the largest
+// off-diagonal measure it saw to block_max[blockIdx.x].
+constexpr int SVD_SWEEP_NT = 256;
+constexpr long long SVD_BARRIER_CYCLES = 2ll << 30;
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks,
+                                             int* err) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int* vgen = gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (*(volatile int*)err || clock64() - t0 > SVD_BARRIER_CYCLES) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector* __restrict__ secs, int nsec,
+                                                                 const int* __restrict__ pair_off, int kk_all,
+                                                                 T* __restrict__ base, float* __restrict__ block_max,
+                                                                 unsigned int* __restrict__ bar, int* __restrict__ err) {
+    constexpr bool F32 = sizeof(T) == 4;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int warps = SVD_SWEEP_NT / 32;
+    const int gw = blockIdx.x * warps + w, nw = gridDim.x * warps;
+    const int npairs = pair_off[nsec];
+    float mymax = 0.f;
+    for (int round = 0; round < kk_all - 1; ++round) {
+        for (int item = gw; item < npairs; item += nw) {
+            int lo = 0, hi = nsec;                       // sector: pair_off[lo] <= item < pair_off[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pair_off[mid] <= item) lo = mid; else hi = mid;
+            }
+            const SvdSector s = secs[lo];
+            const int kk = s.k + (s.k & 1);
+            if (round >= kk - 1) continue;
+            const int pair = item - pair_off[lo];
+            auto pos = [&](int j) { return j == 0 ? 0 : 1 + (j - 1 + round) % (kk - 1); };
+            int p = pos(pair), q = pos(kk - 1 - pair);
+            if (p >= s.k || q >= s.k) continue;          // pair with the dummy column
+            if (p > q) { const int t = p; p = q; q = t; }
+            T* J = base + (F32 ? s.j32_off : s.j_off);
+            T* cp = J + (int64_t)p * s.r;
+            T* cq = J + (int64_t)q * s.r;
+            T a = 0, b = 0, g = 0;
+            for (int i = lane; i < s.r; i += 32) {
+                const T u = cp[i], v = cq[i];
+                a = fma(u, u, a);
+                b = fma(v, v, b);
+                g = fma(u, v, g);
+            }
+            a = warp_sum_t(a); b = warp_sum_t(b); g = warp_sum_t(g);
+            if (g == (T)0 || a == (T)0 || b == (T)0) continue;
+            const double da = a, db = b, dg = g;
+            const double meas = fabs(dg) / sqrt(da * db);
+            mymax = fmaxf(mymax, (float)meas);
+            if (meas < (F32 ? 1e-7 : 1e-15)) continue;
+            const double zeta = (db - da) / (2.0 * dg);
+            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double cd = 1.0 / sqrt(1.0 + t * t);
+            const T c = (T)cd, sn = (T)(cd * t);
+            for (int i = lane; i < s.r; i += 32) {
+                const T u = cp[i], v = cq[i];
+                cp[i] = c * u - sn * v;
+                cq[i] = sn * u + c * v;
+            }
+            T* V = base + (F32 ? s.v32_off : s.v_off);
+            T* vp = V + (int64_t)p * s.k;
+            T* vq = V + (int64_t)q * s.k;
+            for (int i = lane; i < s.k; i += 32) {
+                const T u = vp[i], v = vq[i];
+                vp[i] = c * u - sn * v;
+                vq[i] = sn * u + c * v;
+            }
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err)) break;
+    }
+    __shared__ float wm[SVD_SWEEP_NT / 32];
+    for (int o = 16; o > 0; o >>= 1) mymax = fmaxf(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+    if (lane == 0) wm[w] = mymax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int i = 0; i < warps; ++i) m = fmaxf(m, wm[i]);
+        block_max[blockIdx.x] = m;
+    }
 }
 
 // largest slot value -> out[0] (one block; fixed order)
@@ -385,7 +434,7 @@ extern "C" int heff_svd_create(const heff_layout* x, heff_svd** out) {
         S->slot_ld = std::max(1, kk / 2);
         S->nslots = (int64_t)nsec * S->slot_ld;
         S->off_slots = ((size_t)S->ws_doubles * sizeof(double) + tab.size() * sizeof(int64_t) + 255) / 256 * 256;
-        S->off_f32 = (S->off_slots + (size_t)(S->nslots + 64) * sizeof(float) + 255) / 256 * 256;
+        S->off_f32 = (S->off_slots + (size_t)(S->nslots + 64 + nsec + 8) * sizeof(float) + 255) / 256 * 256;
         S->ws_bytes = S->off_f32 + (size_t)o32 * sizeof(float) + 1024;
     } catch (const std::bad_alloc&) {
         delete S;
@@ -437,21 +486,46 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
         if (rc) return rc;
         S->lists_uploaded = true;
     }
-    // Jacobi sweeps until the largest off-diagonal measure is below tol: every round is one
-    // launch over all sectors (a sector whose own rounds are done returns at once)
+    // Jacobi sweeps until the largest off-diagonal measure is below tol: one cooperative
+    // launch per sweep (all rounds, grid barrier between rounds)
     const int kk_all = S->max_k + (S->max_k & 1);
+    if (S->pair_off.empty()) {
+        S->pair_off.push_back(0);
+        for (const SvdSector& sc : S->sec) S->pair_off.push_back(S->pair_off.back() + (sc.k + (sc.k & 1)) / 2);
+    }
+    int* d_pair_off = reinterpret_cast<int*>(slots + S->nslots + 16);
+    unsigned int* d_bar = reinterpret_cast<unsigned int*>(d_pair_off + S->pair_off.size());
+    int* d_err = reinterpret_cast<int*>(d_bar + 2);
+    SVD_CK(cudaMemcpyAsync(d_pair_off, S->pair_off.data(), S->pair_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           st));
+    SVD_CK(cudaMemsetAsync(d_bar, 0, 3 * sizeof(unsigned int), st));
     auto sweeps = [&](auto* base, float tol, int max_sweeps, int& out) -> int {
+        using T = typename std::remove_pointer<decltype(base)>::type;
         out = 0;
-        const int gx = std::max(1, kk_all / 2);
-        while (out < max_sweeps && kk_all >= 2) {
-            SVD_CK(cudaMemsetAsync(slots, 0, (size_t)S->nslots * sizeof(float), st));
-            for (int r = 0; r < kk_all - 1; ++r)
-                svd_round_kernel<<<dim3(gx, nsec), SVD_NT, 0, st>>>(S->d_sec, base, r, slots, (int)S->slot_ld);
-            svd_offmax_kernel<<<1, 256, 0, st>>>(slots, (int)S->nslots, offmax);
-            heff::count_launches(kk_all);
+        if (kk_all < 2) return HEFF_OK;
+        int dev = 0, nsm = 0, per_sm = 0;
+        SVD_CK(cudaGetDevice(&dev));
+        SVD_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        SVD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_sweep_kernel<T>, SVD_SWEEP_NT, 0));
+        const int npairs = S->pair_off.back();
+        int grid = std::max(1, std::min(nsm * std::max(per_sm, 1), (npairs + 7) / 8));
+        grid = std::min<int>(grid, (int)S->nslots);
+        const SvdSector* secs = S->d_sec;
+        int nsec_i = nsec, kk_i = kk_all;
+        T* base_t = base;
+        while (out < max_sweeps) {
+            void* args[] = {(void*)&secs, (void*)&nsec_i, (void*)&d_pair_off, (void*)&kk_i, (void*)&base_t,
+                            (void*)&slots, (void*)&d_bar, (void*)&d_err};
+            SVD_CK(cudaLaunchCooperativeKernel((const void*)svd_sweep_kernel<T>, dim3(grid), dim3(SVD_SWEEP_NT),
+                                               args, 0, st));
+            svd_offmax_kernel<<<1, 256, 0, st>>>(slots, grid, offmax);
+            heff::count_launches(2);
             float m = 0.f;
+            int e = 0;
             SVD_CK(cudaMemcpyAsync(&m, offmax, sizeof(float), cudaMemcpyDeviceToHost, st));
+            SVD_CK(cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             SVD_CK(cudaStreamSynchronize(st));
+            if (e) return fail(HEFF_ERR_TIMEOUT, "SVD sweep: grid barrier timed out");
             ++out;
             if (m < tol) break;
         }

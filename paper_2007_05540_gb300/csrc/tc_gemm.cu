@@ -286,17 +286,18 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             const uint32_t nmma = t.n <= 16 ? 16u : (uint32_t)((t.n + 15) & ~15);
             const uint32_t id = idesc(FMT, TM, nmma);
             uint32_t first = 1, acc = 0, d = 0;
-            int kb = 0;
+            int kb = 0, left = 0;              // K blocks issued, left in the current chunk
             for (int s = 0; s < t.seg_count && ok; ++s) {
                 const KSeg sg = g.segs[t.seg_begin + s];
                 for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
-                    if (kb % CH == 0) {        // a new accumulation chunk
+                    if (left == 0) {           // a new accumulation chunk
                         acc = ccount & 1;
                         const uint32_t use = ccount >> 1;
                         if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
                         tc_fence_after();
                         d = tmem + acc * TN;
                         first = 1;
+                        left = nkb - kb < CH ? nkb - kb : CH;
                     }
                     const int st = it % STAGES;
                     if (!(ok = mbar_wait(&full[st], (it / STAGES) & 1, abort_flag, g.err))) break;
@@ -314,7 +315,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                         first = 0;
                     }
                     umma_commit(&empty[st]);
-                    if (++kb % CH == 0 || kb == nkb) {
+                    ++kb;
+                    if (--left == 0) {
                         umma_commit(&tfull[acc]);
                         ++ccount;
                     }
@@ -444,27 +446,33 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     }
                 } else if (c < t.n) {
                     // chunk 0 stores, later chunks add (same thread, same order: deterministic);
-                    // the previous values of all 32 rows are loaded before any store so the
-                    // loads overlap
+                    // the previous values of 8 rows are loaded before their stores so the
+                    // loads overlap (8 at a time keeps the register count of the kernel low)
                     const int64_t o0 = t.c_off + c;
                     if (g.y_f64) {
                         double* y = static_cast<double*>(const_cast<void*>(g.y.p[brel])) + o0;
-                        double old[32];
+                        for (int r0 = 0; r0 < rows; r0 += 8) {
+                            double old[8];
 #pragma unroll
-                        for (int rr = 0; rr < 32; ++rr)
-                            old[rr] = (ch && rr < rows) ? y[(int64_t)(q * 32 + rr) * t.ldc] : 0.0;
+                            for (int u = 0; u < 8; ++u)
+                                old[u] = (ch && r0 + u < rows) ? y[(int64_t)(q * 32 + r0 + u) * t.ldc] : 0.0;
 #pragma unroll
-                        for (int rr = 0; rr < 32; ++rr)
-                            if (rr < rows) y[(int64_t)(q * 32 + rr) * t.ldc] = old[rr] + (double)stage[rr][lane];
+                            for (int u = 0; u < 8; ++u)
+                                if (r0 + u < rows)
+                                    y[(int64_t)(q * 32 + r0 + u) * t.ldc] = old[u] + (double)stage[r0 + u][lane];
+                        }
                     } else {
                         float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o0;
-                        float old[32];
+                        for (int r0 = 0; r0 < rows; r0 += 8) {
+                            float old[8];
 #pragma unroll
-                        for (int rr = 0; rr < 32; ++rr)
-                            old[rr] = (ch && rr < rows) ? y[(int64_t)(q * 32 + rr) * t.ldc] : 0.f;
+                            for (int u = 0; u < 8; ++u)
+                                old[u] = (ch && r0 + u < rows) ? y[(int64_t)(q * 32 + r0 + u) * t.ldc] : 0.f;
 #pragma unroll
-                        for (int rr = 0; rr < 32; ++rr)
-                            if (rr < rows) y[(int64_t)(q * 32 + rr) * t.ldc] = old[rr] + stage[rr][lane];
+                            for (int u = 0; u < 8; ++u)
+                                if (r0 + u < rows)
+                                    y[(int64_t)(q * 32 + r0 + u) * t.ldc] = old[u] + stage[r0 + u][lane];
+                        }
                     }
                 }
                 __syncwarp();
