@@ -242,10 +242,14 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
-        uint32_t it = 0;
+        uint32_t st = 0, ph = 0;               // ring stage and its phase parity
         bool ok = true;
+        // the next task and the next segment are loaded one step ahead, so their latency
+        // overlaps with the current loads instead of draining the ring
+        GemmTask tn = blockIdx.x < total ? g.tasks[blockIdx.x % g.ntasks] : GemmTask{};
         for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x) {
-            const GemmTask t = g.tasks[gi % g.ntasks];
+            const GemmTask t = tn;
+            if (gi + gridDim.x < total) tn = g.tasks[(gi + gridDim.x) % g.ntasks];
             const int b = g.b0 + (int)(gi / g.ntasks);
             const int ah = (int)(t.a_row + b * g.a_batch_rows), al = (int)(ah + g.a_plane_rows);
             const int bh = (int)(t.b_row + b * g.b_batch_rows), bl = (int)(bh + g.b_plane_rows);
@@ -253,28 +257,38 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             const CUtensorMap* ma = &maps.a[ia];
             const CUtensorMap* mb = &maps.b[ib];
             const uint32_t bytes = 2u * (uint32_t)((64 << ia) + (64 << ib)) * SWZ;
+            KSeg sn = t.seg_count > 0 ? g.segs[t.seg_begin] : KSeg{};
             for (int s = 0; s < t.seg_count && ok; ++s) {
-                const KSeg sg = g.segs[t.seg_begin + s];
-                for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
-                    const int st = it % STAGES;
-                    if (!(ok = mbar_wait(&empty[st], ((it / STAGES) & 1) ^ 1, abort_flag, g.err))) break;
+                const KSeg sg = sn;
+                if (s + 1 < t.seg_count) sn = g.segs[t.seg_begin + s + 1];
+                for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB) {
+                    if (!(ok = mbar_wait(&empty[st], ph ^ 1, abort_flag, g.err))) break;
                     uint8_t* base = smem + st * S::STAGE_BYTES;
                     mbar_expect_tx(&full[st], bytes);
                     tma_load(base, ma, &full[st], k, ah);
                     tma_load(base + S::A_BYTES, ma, &full[st], k, al);
                     tma_load(base + 2 * S::A_BYTES, mb, &full[st], k, bh);
                     tma_load(base + 2 * S::A_BYTES + S::B_BYTES, mb, &full[st], k, bl);
+                    if (++st == STAGES) { st = 0; ph ^= 1; }
                 }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
         constexpr uint32_t FMT = PREC == HEFF_PREC_BF16X3 ? 1u : 2u;
+        // This thread feeds the tensor pipe: per K block it only waits, adds constant offsets
+        // to precomputed descriptors and issues (no divisions, no descriptor packing).
         const int CH = g.kchunk > 0 ? g.kchunk : 0x7fffffff;
-        uint32_t it = 0, ccount = 0;           // ring position, accumulator chunk counter
+        uint32_t ccount = 0;                   // accumulator chunk counter
+        uint32_t st = 0, ph = 0;               // ring stage and its phase parity
+        const uint64_t dsc0 = sdesc<SWZ>(su32(smem));
+        constexpr uint64_t O_ALO = S::A_BYTES >> 4, O_BHI = (2 * S::A_BYTES) >> 4;
+        constexpr uint64_t O_BLO = (2 * S::A_BYTES + S::B_BYTES) >> 4, O_STAGE = S::STAGE_BYTES >> 4;
         bool ok = true;
+        GemmTask tn = blockIdx.x < total ? g.tasks[blockIdx.x % g.ntasks] : GemmTask{};
         for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x) {
-            const GemmTask t = g.tasks[gi % g.ntasks];
+            const GemmTask t = tn;
+            if (gi + gridDim.x < total) tn = g.tasks[(gi + gridDim.x) % g.ntasks];
             if (t.seg_count == 0) {            // nothing to contract: the epilogue writes zeros
                 const uint32_t acc = ccount & 1, use = ccount >> 1;
                 if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
@@ -286,40 +300,35 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             const uint32_t nmma = t.n <= 16 ? 16u : (uint32_t)((t.n + 15) & ~15);
             const uint32_t id = idesc(FMT, TM, nmma);
             uint32_t first = 1, acc = 0, d = 0;
-            int kb = 0, left = 0;              // K blocks issued, left in the current chunk
-            for (int s = 0; s < t.seg_count && ok; ++s) {
-                const KSeg sg = g.segs[t.seg_begin + s];
-                for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB, ++it) {
-                    if (left == 0) {           // a new accumulation chunk
-                        acc = ccount & 1;
-                        const uint32_t use = ccount >> 1;
-                        if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
-                        tc_fence_after();
-                        d = tmem + acc * TN;
-                        first = 1;
-                        left = nkb - kb < CH ? nkb - kb : CH;
-                    }
-                    const int st = it % STAGES;
-                    if (!(ok = mbar_wait(&full[st], (it / STAGES) & 1, abort_flag, g.err))) break;
+            int left = 0;                      // K blocks left in the current chunk
+            // the ring holds the tile's K blocks in order: only their number matters here
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                if (left == 0) {               // a new accumulation chunk
+                    acc = ccount & 1;
+                    const uint32_t use = ccount >> 1;
+                    if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
                     tc_fence_after();
-                    const uint32_t base = su32(smem + st * S::STAGE_BYTES);
-                    const uint64_t ahi = sdesc<SWZ>(base), alo = sdesc<SWZ>(base + S::A_BYTES);
-                    const uint64_t bhi = sdesc<SWZ>(base + 2 * S::A_BYTES);
-                    const uint64_t blo = sdesc<SWZ>(base + 2 * S::A_BYTES + S::B_BYTES);
+                    d = tmem + acc * TN;
+                    first = 1;
+                    left = nkb - kb < CH ? nkb - kb : CH;
+                }
+                if (!(ok = mbar_wait(&full[st], ph, abort_flag, g.err))) break;
+                tc_fence_after();
+                const uint64_t ahi = dsc0 + st * O_STAGE, alo = ahi + O_ALO;
+                const uint64_t bhi = ahi + O_BHI, blo = ahi + O_BLO;
 #pragma unroll
-                    for (int kk = 0; kk < KSUB; ++kk) {
-                        const uint64_t o = (uint64_t)(kk * 32) >> 4;     // 32-byte step inside the row
-                        umma<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
-                        umma<PREC>(d, ahi + o, blo + o, id, 1u);
-                        umma<PREC>(d, alo + o, bhi + o, id, 1u);
-                        first = 0;
-                    }
-                    umma_commit(&empty[st]);
-                    ++kb;
-                    if (--left == 0) {
-                        umma_commit(&tfull[acc]);
-                        ++ccount;
-                    }
+                for (int kk = 0; kk < KSUB; ++kk) {
+                    const uint64_t o = (uint64_t)(kk * 32) >> 4;     // 32-byte step inside the row
+                    umma<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
+                    umma<PREC>(d, ahi + o, blo + o, id, 1u);
+                    umma<PREC>(d, alo + o, bhi + o, id, 1u);
+                    first = 0;
+                }
+                umma_commit(&empty[st]);
+                if (++st == STAGES) { st = 0; ph ^= 1; }
+                if (--left == 0) {
+                    umma_commit(&tfull[acc]);
+                    ++ccount;
                 }
             }
         }
