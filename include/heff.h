@@ -195,6 +195,19 @@ int heff_apply_prepared(heff_plan* plan, const void* x, void* y, void* workspace
                         size_t workspace_bytes, void* stream);
 
 /*
+ * heff_apply_host -- heff_apply on tensors in host memory: the five inputs are copied into
+ * `staging` (device, >= heff_apply_host_staging_size bytes, 256-byte aligned; laid out as
+ * L, W1, W2, R, x, y), the apply runs there, and y is copied back, all asynchronously on
+ * `stream` (pinned host memory lets the copies overlap work on other streams; pageable
+ * memory makes them synchronous).  Host buffers must stay valid until the stream reaches
+ * the end of the call.  Errors: as heff_apply, WORKSPACE for a small staging buffer.
+ */
+int heff_apply_host_staging_size(const heff_plan* plan, size_t* bytes);
+int heff_apply_host(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                    const void* x, void* y, void* staging, size_t staging_bytes, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/*
  * heff_apply_batched -- y_b = K x_b for b < nbatch (<= max_batch) vectors sharing L, W1,
  * W2, R: one preparation and one launch of each GEMM over all vectors.  x, y: HOST arrays
  * of nbatch device pointers.  Errors as heff_apply.
@@ -224,6 +237,29 @@ int heff_lanczos_workspace_size(const heff_plan* plan, int32_t n_iter, size_t* b
 int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                  const double* x0, int32_t n_iter, double* x_out, double* result, void* apply_ws,
                  size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes, void* stream);
+
+/*
+ * heff_davidson -- lowest eigenpair of H_eff by the Davidson routine of Algorithm 1
+ * (no preconditioner; randomisation when re-orthogonalisation fails), all in FP64 on the
+ * device except the matvecs (the plan's precision; HEFF_DTYPE_F64 tensors).  Per step i:
+ * m_ij = (A v_j)^T v_i for j <= i; the lowest eigenpair (lambda, s) of the leading
+ * (i+1) x (i+1) block of M (one-thread Jacobi); x = sum s_j v_j, q = sum s_j A v_j -
+ * lambda x; stop when ||q|| < tol max(1, |lambda|) or max_vecs vectors are in use; else q
+ * is orthogonalised against v_0..v_i (two classical Gram-Schmidt passes), replaced by
+ * `rnd` if less than 1e-12 of it survives (then orthogonalised again), normalised into
+ * v_{i+1}.  The paper runs it with a subspace of 2 inside the sweeps (max_vecs = 2).
+ *   x0      device, nelem(x) doubles, nonzero start vector
+ *   rnd     device, nelem(x) doubles, the random vector of the randomisation step
+ *   x_out   device, nelem(x) doubles: normalised x
+ *   result  device, 3 doubles: lambda, ||q||, vectors used
+ *   dav_ws  >= heff_davidson_workspace_size bytes, 256-byte aligned
+ * max_vecs 1..64, tol >= 0.  Asynchronous; never synchronises.
+ */
+int heff_davidson_workspace_size(const heff_plan* plan, int32_t max_vecs, size_t* bytes);
+int heff_davidson(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                  const double* x0, const double* rnd, int32_t max_vecs, double tol, double* x_out,
+                  double* result, void* apply_ws, size_t apply_ws_bytes, void* dav_ws, size_t dav_ws_bytes,
+                  void* stream);
 
 /*
  * Environment extension (Section II-C: the left environment A and right environment B

@@ -457,6 +457,56 @@ extern "C" int heff_apply(heff_plan* plan, const void* L, const void* W1, const 
     return do_matvec(plan, xs, ys, 1, workspace, stream);
 }
 
+namespace {
+struct Staging {
+    size_t off[6];      // L, W1, W2, R, x, y
+    size_t bytes[6];
+    size_t total;
+};
+Staging staging_layout(const heff_plan* p) {
+    const size_t es = p->opts.io_dtype == HEFF_DTYPE_F64 ? 8 : 4;
+    const int64_t n[6] = {p->nelem_L, p->nelem_W1, p->nelem_W2, p->nelem_R, p->nelem_x, p->nelem_x};
+    Staging s{};
+    size_t o = 0;
+    for (int k = 0; k < 6; ++k) {
+        s.off[k] = o;
+        s.bytes[k] = (size_t)n[k] * es;
+        o = (o + s.bytes[k] + 255) / 256 * 256;
+    }
+    s.total = o;
+    return s;
+}
+}  // namespace
+
+extern "C" int heff_apply_host_staging_size(const heff_plan* plan, size_t* bytes) {
+    heff::clear_error();
+    if (!plan || !bytes) return fail(HEFF_ERR_INVALID_ARG, "heff_apply_host_staging_size: null argument");
+    *bytes = staging_layout(plan).total;
+    return HEFF_OK;
+}
+
+extern "C" int heff_apply_host(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                               const void* x, void* y, void* staging, size_t staging_bytes, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x || !y || !staging)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_apply_host: null argument");
+    const Staging sl = staging_layout(plan);
+    if (staging_bytes < sl.total || reinterpret_cast<uintptr_t>(staging) % 256)
+        return fail(HEFF_ERR_WORKSPACE, "staging buffer of %zu bytes, needs %zu (256-byte aligned)", staging_bytes,
+                    sl.total);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* d = static_cast<char*>(staging);
+    const void* src[5] = {L, W1, W2, R, x};
+    for (int k = 0; k < 5; ++k)
+        CK(cudaMemcpyAsync(d + sl.off[k], src[k], sl.bytes[k], cudaMemcpyHostToDevice, st));
+    int rc = heff_apply(plan, d + sl.off[0], d + sl.off[1], d + sl.off[2], d + sl.off[3], d + sl.off[4],
+                        d + sl.off[5], workspace, workspace_bytes, stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(y, d + sl.off[5], sl.bytes[5], cudaMemcpyDeviceToHost, st));
+    return HEFF_OK;
+}
+
 extern "C" int heff_apply_batched(heff_plan* plan, const void* L, const void* W1, const void* W2,
                                   const void* R, const void* const* x, void* const* y, int32_t nbatch,
                                   void* workspace, size_t workspace_bytes, void* stream) {

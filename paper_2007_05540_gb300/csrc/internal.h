@@ -169,9 +169,11 @@ struct heff_plan {
     heff::GemmList g1, g2;            // active task lists
     heff::GemmList g1_alt, g2_alt;    // the other tile width (tensor-core paths), see heff_plan_autotune
     int64_t stats[24] = {0};
-    // tensor-map cache for the tensor-core path (keyed by workspace pointer)
-    void* tmap_ws = nullptr;
-    alignas(64) unsigned char tmaps[12][128];
+    // tensor-map cache for the tensor-core path: two entries keyed by workspace pointer
+    // (two streams alternating workspaces reuse their maps), replaced round-robin
+    void* tmap_ws[2] = {nullptr, nullptr};
+    int tmap_next = 0;
+    alignas(64) unsigned char tmaps[2][12][128];
     int device = 0;
     int num_sms = 0;
     bool uploaded = false;    // false: created without a CUDA device (inspection only)

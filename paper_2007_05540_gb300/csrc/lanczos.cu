@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict_
                                                        int64_t n, double* state, int mode, int k, int nmax) {
     __shared__ double sh[RT / 32];
     __shared__ double nrm;
-    if (mode == 1 && state[1] == 0.0) return;
+    if ((mode == 1 || mode == 3) && state[1] == 0.0) return;     // 3: plain, only while active
     double v = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT];
     v = block_sum(v, sh);
@@ -284,6 +284,115 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
     state[3] = fabs(be[n - 1] * s[n - 1]);
 }
 
+// ---------------------------------------------------------------- Davidson (Algorithm 1)
+// State (doubles): [0] vectors in use, [1] active, [2] lambda, [3] ||q||, [4] ||q|| before
+// the Gram-Schmidt passes, [5] tol.
+
+// M[i][j] = M[j][i] = h[j], j <= i
+__global__ void dav_set_m_kernel(double* M, const double* h, int i, int maxv, const double* state) {
+    if (state[1] == 0.0) return;
+    for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+        M[i * maxv + j] = h[j];
+        M[j * maxv + i] = h[j];
+    }
+}
+
+// Lowest eigenpair of the leading m x m block of the symmetric M (one thread, cyclic
+// Jacobi rotations in FP64 until the off-diagonal mass is below 1e-30 of the total):
+// lambda -> state[2], eigenvector (largest component positive) -> s.
+__global__ void dav_eig_kernel(const double* M, double* E, double* s, double* state, int m, int maxv) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || state[1] == 0.0) return;
+    double* A = E;                    // m x m working copy
+    double* Q = E + maxv * maxv;      // accumulated rotations
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) {
+            A[r * m + c] = M[r * maxv + c];
+            Q[r * m + c] = r == c ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) {
+                const double v = A[r * m + c] * A[r * m + c];
+                tot += v;
+                if (r != c) off += v;
+            }
+        if (!(off > 1e-30 * tot)) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                const double zeta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int k = 0; k < m; ++k) {           // columns p, q
+                    const double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = c * akp - sn * akq;
+                    A[k * m + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {           // rows p, q
+                    const double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = c * apk - sn * aqk;
+                    A[q * m + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double qkp = Q[k * m + p], qkq = Q[k * m + q];
+                    Q[k * m + p] = c * qkp - sn * qkq;
+                    Q[k * m + q] = sn * qkp + c * qkq;
+                }
+            }
+    }
+    int lo = 0;
+    for (int r = 1; r < m; ++r) if (A[r * m + r] < A[lo * m + lo]) lo = r;
+    int im = 0;
+    for (int r = 1; r < m; ++r) if (fabs(Q[r * m + lo]) > fabs(Q[im * m + lo])) im = r;
+    const double sg = Q[im * m + lo] < 0.0 ? -1.0 : 1.0;
+    for (int r = 0; r < maxv; ++r) s[r] = r < m ? sg * Q[r * m + lo] : 0.0;
+    state[2] = A[lo * m + lo];
+    state[0] = (double)m;
+}
+
+// q -= lambda x
+__global__ void __launch_bounds__(RT) dav_shift_kernel(double* __restrict__ q, const double* __restrict__ x,
+                                                       int64_t n, const double* __restrict__ state) {
+    if (state[1] == 0.0) return;
+    const double lam = state[2];
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) q[i] -= lam * x[i];
+}
+
+// ||q|| -> state[3]; stop (active = 0) when ||q|| < tol max(1, |lambda|) or the subspace is
+// full, else remember ||q|| in state[4]
+__global__ void dav_check_kernel(const double* __restrict__ part, int nb, double* state, int last) {
+    __shared__ double sh[RT / 32];
+    if (state[1] == 0.0) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        const double r = sqrt(v);
+        state[3] = r;
+        state[4] = r;
+        if (last || !(r >= state[5] * fmax(1.0, fabs(state[2])))) state[1] = 0.0;
+    }
+}
+
+// Randomisation (Algorithm 1's remedy for a failed reorthogonalisation): if Gram-Schmidt
+// left less than 1e-12 of ||q||, replace q by the caller's random vector
+__global__ void __launch_bounds__(RT) dav_random_kernel(const double* __restrict__ part, int nb,
+                                                        double* __restrict__ q, const double* __restrict__ rnd,
+                                                        int64_t n, const double* __restrict__ state) {
+    __shared__ double sh[RT / 32];
+    __shared__ int swap;
+    if (state[1] == 0.0) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) swap = !(sqrt(v) >= 1e-12 * state[4]);
+    __syncthreads();
+    if (!swap) return;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) q[i] = rnd[i];
+}
+
 int grid_for(int64_t n) {
     int64_t g = (n + RT - 1) / RT;
     return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
@@ -364,5 +473,139 @@ extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, cons
     cudaMemcpyAsync(result + 3, z.state + 8, sizeof(double) * 2 * z.nmax, cudaMemcpyDeviceToDevice, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_lanczos: %s", cudaGetErrorString(e));
+    return HEFF_OK;
+}
+
+// ---------------------------------------------------------------- Davidson host side
+namespace heff {
+namespace {
+
+struct DavLayout {
+    int maxv;
+    size_t off_state, off_M, off_E, off_s, off_h, off_part, off_V, off_VA, off_q, bytes;
+};
+
+DavLayout dav_layout(int64_t n, int maxv) {
+    DavLayout l{};
+    l.maxv = maxv;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    size_t o = 0;
+    l.off_state = o; o = al(o + sizeof(double) * 16);
+    l.off_M = o;     o = al(o + sizeof(double) * (size_t)maxv * maxv);
+    l.off_E = o;     o = al(o + sizeof(double) * 2 * (size_t)maxv * maxv);
+    l.off_s = o;     o = al(o + sizeof(double) * (size_t)maxv);
+    l.off_h = o;     o = al(o + sizeof(double) * (size_t)maxv);
+    l.off_part = o;  o = al(o + sizeof(double) * (size_t)RB * VT);
+    l.off_V = o;     o = al(o + sizeof(double) * (size_t)maxv * (size_t)n);
+    l.off_VA = o;    o = al(o + sizeof(double) * (size_t)maxv * (size_t)n);
+    l.off_q = o;     o = al(o + sizeof(double) * (size_t)n);
+    l.bytes = o;
+    return l;
+}
+
+__global__ void dav_init_state_kernel(double* state, double tol) {
+    if (threadIdx.x == 0) state[5] = tol;
+}
+
+}  // namespace
+}  // namespace heff
+
+extern "C" int heff_davidson_workspace_size(const heff_plan* plan, int32_t max_vecs, size_t* bytes) {
+    clear_error();
+    if (!plan || !bytes || max_vecs < 1 || max_vecs > 64)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_davidson_workspace_size: bad arguments (max_vecs 1..64)");
+    *bytes = dav_layout(plan->nelem_x, max_vecs).bytes;
+    return HEFF_OK;
+}
+
+extern "C" int heff_davidson(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                             const double* x0, const double* rnd, int32_t max_vecs, double tol, double* x_out,
+                             double* result, void* apply_ws, size_t apply_ws_bytes, void* dav_ws,
+                             size_t dav_ws_bytes, void* stream) {
+    clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x0 || !rnd || !x_out || !result || !dav_ws)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_davidson: null argument");
+    if (plan->opts.io_dtype != HEFF_DTYPE_F64)
+        return fail(HEFF_ERR_UNSUPPORTED, "heff_davidson needs a plan with HEFF_DTYPE_F64 tensors");
+    if (max_vecs < 1 || max_vecs > 64) return fail(HEFF_ERR_INVALID_ARG, "max_vecs must be 1..64");
+    if (!(tol >= 0.0)) return fail(HEFF_ERR_INVALID_ARG, "tol must be >= 0");
+    const DavLayout lay = dav_layout(plan->nelem_x, max_vecs);
+    if (dav_ws_bytes < lay.bytes || reinterpret_cast<uintptr_t>(dav_ws) % 256)
+        return fail(HEFF_ERR_WORKSPACE, "Davidson workspace of %zu bytes, needs %zu (256-byte aligned)",
+                    dav_ws_bytes, lay.bytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(dav_ws);
+    double* state = reinterpret_cast<double*>(base + lay.off_state);
+    double* M = reinterpret_cast<double*>(base + lay.off_M);
+    double* E = reinterpret_cast<double*>(base + lay.off_E);
+    double* s = reinterpret_cast<double*>(base + lay.off_s);
+    double* h = reinterpret_cast<double*>(base + lay.off_h);
+    double* part = reinterpret_cast<double*>(base + lay.off_part);
+    double* V = reinterpret_cast<double*>(base + lay.off_V);
+    double* VA = reinterpret_cast<double*>(base + lay.off_VA);
+    double* q = reinterpret_cast<double*>(base + lay.off_q);
+    const int64_t n = plan->nelem_x;
+    const int G = grid_for(n);
+    int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
+    if (rc) return rc;
+    dav_init_state_kernel<<<1, 32, 0, st>>>(state, tol);
+    // v_0 = x0 / ||x0|| (sets active when x0 != 0), v^A_0 = A v_0
+    sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, part);
+    normalize_kernel<<<G, RT, 0, st>>>(part, RB, x0, V, n, state, 0, 0, max_vecs);
+    count_launches(3);
+    if ((rc = heff_apply_prepared(plan, V, VA, apply_ws, apply_ws_bytes, stream))) return rc;
+    auto gram_schmidt = [&](int nv) {          // q -= V (V^T q) over v_0 .. v_{nv-1}
+        for (int j0 = 0; j0 < nv; j0 += VT) {
+            const int k = nv - j0 < VT ? nv - j0 : VT;
+            multidot_kernel<<<RB, RT, 0, st>>>(V, q, n, j0, k, part, state);
+            finish_dots_kernel<<<1, RT, 0, st>>>(part, RB, j0, k, h, 0, state);
+            count_launches(2);
+        }
+        combine_kernel<<<G, RT, 0, st>>>(V, n, nv, h, -1.0, 1.0, q, state, 0);
+        count_launches(1);
+    };
+    for (int i = 0; i < max_vecs; ++i) {
+        double* vi = V + (int64_t)i * n;
+        // m_ij = (v^A_j)^T v_i, j <= i
+        for (int j0 = 0; j0 <= i; j0 += VT) {
+            const int k = i + 1 - j0 < VT ? i + 1 - j0 : VT;
+            multidot_kernel<<<RB, RT, 0, st>>>(VA, vi, n, j0, k, part, state);
+            finish_dots_kernel<<<1, RT, 0, st>>>(part, RB, j0, k, h, 0, state);
+            count_launches(2);
+        }
+        dav_set_m_kernel<<<1, 64, 0, st>>>(M, h, i, max_vecs, state);
+        dav_eig_kernel<<<1, 32, 0, st>>>(M, E, s, state, i + 1, max_vecs);
+        // x = V s, q = V^A s - lambda x, ||q||
+        combine_kernel<<<G, RT, 0, st>>>(V, n, i + 1, s, 1.0, 0.0, x_out, state, 0);
+        combine_kernel<<<G, RT, 0, st>>>(VA, n, i + 1, s, 1.0, 0.0, q, state, 0);
+        dav_shift_kernel<<<G, RT, 0, st>>>(q, x_out, n, state);
+        sumsq_kernel<<<RB, RT, 0, st>>>(q, n, part);
+        dav_check_kernel<<<1, RT, 0, st>>>(part, RB, state, i + 1 == max_vecs);
+        count_launches(7);
+        if (i + 1 == max_vecs) break;
+        // orthogonalise q against v_0..v_i (two classical Gram-Schmidt passes), randomise if
+        // nothing is left, orthogonalise again, normalise into v_{i+1}, v^A_{i+1} = A v_{i+1}
+        gram_schmidt(i + 1);
+        gram_schmidt(i + 1);
+        sumsq_kernel<<<RB, RT, 0, st>>>(q, n, part);
+        dav_random_kernel<<<G, RT, 0, st>>>(part, RB, q, rnd, n, state);
+        count_launches(2);
+        gram_schmidt(i + 1);
+        gram_schmidt(i + 1);
+        double* vn = V + (int64_t)(i + 1) * n;
+        sumsq_kernel<<<RB, RT, 0, st>>>(q, n, part);
+        normalize_kernel<<<G, RT, 0, st>>>(part, RB, q, vn, n, state, 3, 0, max_vecs);
+        count_launches(2);
+        if ((rc = heff_apply_prepared(plan, vn, VA + (int64_t)(i + 1) * n, apply_ws, apply_ws_bytes, stream)))
+            return rc;
+    }
+    sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, part);
+    normalize_kernel<<<G, RT, 0, st>>>(part, RB, x_out, x_out, n, state, 2, 0, max_vecs);
+    count_launches(2);
+    // result: [lambda, ||q||, vectors used]
+    cudaMemcpyAsync(result, state + 2, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(result + 2, state, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_davidson: %s", cudaGetErrorString(e));
     return HEFF_OK;
 }

@@ -562,8 +562,15 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
     }
     char* w = static_cast<char*>(ws);
     const int64_t B = p->opts.max_batch;
-    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps);
-    if (p->tmap_ws != ws) {
+    int slot = p->tmap_ws[0] == ws ? 0 : (p->tmap_ws[1] == ws ? 1 : -1);
+    const bool fresh = slot < 0;
+    if (fresh) {
+        slot = p->tmap_next;
+        p->tmap_next ^= 1;
+        p->tmap_ws[slot] = nullptr;        // set once every map of the entry is encoded
+    }
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps[slot]);
+    if (fresh) {
         // [0,1] LW (64, 128 rows)  [2,3,4] XT (64, 128, 256)  [5,6] T (64, 128)  [7,8,9] RW (64, 128, 256)
         // [10] T store boxes: 32 rows x 32 elements (64-byte swizzle for bf16, 128-byte for fp32)
         struct { char* base; int64_t rows, ld; int slot, nbox; } ops[4] = {
@@ -579,7 +586,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
         int rc = make_map(&m[10], w + p->off_t, PREC, (uint64_t)(2 * B * p->rows_t), (uint64_t)p->ld_t, 32u,
                           PREC == HEFF_PREC_BF16X3 ? 64 : 128);
         if (rc) return rc;
-        p->tmap_ws = ws;
+        p->tmap_ws[slot] = ws;
     }
     const GemmList& gl = which == 1 ? p->g1 : p->g2;
     if (gl.tasks.empty()) return HEFF_OK;

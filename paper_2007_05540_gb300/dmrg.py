@@ -4,7 +4,7 @@ Every numerical step runs in the library's kernels, with the tensors resident in
 memory: per bond (i, i+1) of a sweep
 
     x0 = A_i . B_{i+1}                        heff_two_site_apply  (Fig. 1d)
-    lowest eigenpair of K on the bond          heff_lanczos         (matvecs: heff_apply)
+    lowest eigenpair of K on the bond          heff_lanczos, or heff_davidson (Algorithm 1)
     x = U S V^T, truncated to m                heff_svd_*           (Fig. 1e, Section II-C)
     A_i <- U, B_{i+1} <- S V^T  (left -> right; mirrored right -> left)
     L_{i+1} from L_i, A_i  or  R_{i+1} from R_{i+2}, B_{i+1}        heff_env_update
@@ -48,7 +48,8 @@ class GpuDMRG:
     channel charges of bond b, ``phys`` the site charges, ``start_index(0)`` and
     ``done_index(N)`` the boundary channels) in the sector of total charge ``total``."""
 
-    def __init__(self, mpo, total, precision="fp64", n_iter=20, cutoff=1e-12, states=None, device="cuda"):
+    def __init__(self, mpo, total, precision="fp64", n_iter=20, cutoff=1e-12, states=None, device="cuda",
+                 solver="lanczos", davidson_vecs=2, seed=0):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -60,6 +61,11 @@ class GpuDMRG:
         self.precision = precision
         self.n_iter = int(n_iter)
         self.cutoff = float(cutoff)
+        if solver not in ("lanczos", "davidson"):
+            raise ValueError(f"unknown solver {solver!r}")
+        self.solver = solver
+        self.davidson_vecs = int(davidson_vecs)
+        self.rng = np.random.default_rng(seed)     # the randomisation vectors of Algorithm 1
         self.ch = [np.asarray(q, dtype=np.int32).reshape(-1, self.nq) for q in mpo.charges]
         d = len(self.phys)
         # MPO tensors in their layouts (host copy for the schedules, device copy for compute)
@@ -133,13 +139,22 @@ class GpuDMRG:
         finally:
             heff.heff_two_site_destroy(ts)
         plan = heff.Plan(Ll, W1l, W2l, Rl, xl, self.W[i][1], self.W[i + 1][1], self.precision, "f64")
-        n_it = max(1, min(self.n_iter, xl.nelem, 126))
         ws = plan.workspace(self.dev)
-        lz = torch.empty(heff.heff_lanczos_workspace_size(plan.handle, n_it), dtype=torch.uint8, device=self.dev)
         x = torch.empty_like(x0)
-        res = torch.zeros(3 + 2 * (n_it + 1), dtype=torch.float64, device=self.dev)
         Lenv, Renv = self.L[i][1], self.R[i + 2][1]
-        heff.heff_lanczos(plan.handle, Lenv, self.W[i][2], self.W[i + 1][2], Renv, x0, n_it, x, res, ws, lz)
+        if self.solver == "lanczos":
+            n_it = max(1, min(self.n_iter, xl.nelem, 126))
+            lz = torch.empty(heff.heff_lanczos_workspace_size(plan.handle, n_it), dtype=torch.uint8,
+                             device=self.dev)
+            res = torch.zeros(3 + 2 * (n_it + 1), dtype=torch.float64, device=self.dev)
+            heff.heff_lanczos(plan.handle, Lenv, self.W[i][2], self.W[i + 1][2], Renv, x0, n_it, x, res, ws, lz)
+        else:
+            nv = max(1, min(self.davidson_vecs, xl.nelem, 64))
+            dw = torch.empty(heff.heff_davidson_workspace_size(plan.handle, nv), dtype=torch.uint8, device=self.dev)
+            rnd = torch.from_numpy(self.rng.standard_normal(xl.nelem)).to(self.dev)
+            res = torch.zeros(3, dtype=torch.float64, device=self.dev)
+            heff.heff_davidson(plan.handle, Lenv, self.W[i][2], self.W[i + 1][2], Renv, x0, rnd, nv, 1e-10, x, res,
+                               ws, dw)
         energy = float(res[0].item())
         # split and truncate
         s = heff.heff_svd_create(xl.handle)
@@ -194,10 +209,12 @@ class GpuDMRG:
         return [int(np.sum(b[1])) for b in self.bonds]
 
 
-def dmrg(mpo, total, m_schedule, precision="fp64", n_iter=20, cutoff=1e-12, device="cuda"):
-    """Run one full sweep per entry of ``m_schedule`` (the bond cap of that sweep).
+def dmrg(mpo, total, m_schedule, precision="fp64", n_iter=20, cutoff=1e-12, device="cuda", solver="lanczos",
+         davidson_vecs=2):
+    """Run one full sweep per entry of ``m_schedule`` (the bond cap of that sweep); the
+    eigensolver is Lanczos (n_iter steps) or Algorithm 1's Davidson (davidson_vecs vectors).
     Returns dict(sweep_energies, energy, refined_energy, bond_dims, max_discarded)."""
-    run = GpuDMRG(mpo, total, precision, n_iter, cutoff, device=device)
+    run = GpuDMRG(mpo, total, precision, n_iter, cutoff, device=device, solver=solver, davidson_vecs=davidson_vecs)
     for m in m_schedule:
         run.sweep(int(m))
     out = {"sweep_energies": list(run.energies), "energy": run.energies[-1], "bond_dims": run.bond_dims(),

@@ -59,6 +59,10 @@ _sig = {
     "heff_plan_select_tiles": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "heff_two_site_create": (C.c_int, [_vp, _vp, _vp, _P(_vp)]),
     "heff_svd_info": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_int32)]),
+    "heff_davidson_workspace_size": (C.c_int, [_vp, C.c_int32, _P(_sz)]),
+    "heff_apply_host_staging_size": (C.c_int, [_vp, _P(_sz)]),
+    "heff_apply_host": (C.c_int, [_vp] * 8 + [_sz, _vp, _sz, _vp]),
+    "heff_davidson": (C.c_int, [_vp] * 7 + [C.c_int32, C.c_double, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
     "heff_two_site_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "heff_two_site_destroy": (None, [_vp]),
     "heff_plan_flops": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double)]),
@@ -262,6 +266,18 @@ def heff_apply(plan, L, W1, W2, R, x, y, ws, stream=None):
                            _nbytes(ws), _stream(stream)), "heff_apply")
 
 
+def heff_apply_host_staging_size(plan):
+    b = _sz()
+    _check(_lib.heff_apply_host_staging_size(plan, C.byref(b)), "heff_apply_host_staging_size")
+    return b.value
+
+
+def heff_apply_host(plan, L, W1, W2, R, x, y, staging, ws, stream=None):
+    """heff_apply on host (CPU, ideally pinned) tensors through a device staging buffer."""
+    _check(_lib.heff_apply_host(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y), _ptr(staging),
+                                _nbytes(staging), _ptr(ws), _nbytes(ws), _stream(stream)), "heff_apply_host")
+
+
 def heff_apply_batched(plan, L, W1, W2, R, xs, ys, ws, stream=None):
     n = len(xs)
     xa = (_vp * n)(*[t.data_ptr() for t in xs])
@@ -398,6 +414,19 @@ def heff_env_update(plan, env_old, site, W, env_new, ws, stream=None):
 
 def heff_env_plan_destroy(plan):
     _lib.heff_env_plan_destroy(plan)
+
+
+def heff_davidson_workspace_size(plan, max_vecs):
+    b = _sz()
+    _check(_lib.heff_davidson_workspace_size(plan, int(max_vecs), C.byref(b)), "heff_davidson_workspace_size")
+    return b.value
+
+
+def heff_davidson(plan, L, W1, W2, R, x0, rnd, max_vecs, tol, x_out, result, apply_ws, dav_ws, stream=None):
+    """Algorithm 1 (Davidson); result (device, 3 doubles): [lambda, ||q||, vectors used]."""
+    _check(_lib.heff_davidson(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x0), _ptr(rnd), int(max_vecs),
+                              float(tol), _ptr(x_out), _ptr(result), _ptr(apply_ws), _nbytes(apply_ws),
+                              _ptr(dav_ws), _nbytes(dav_ws), _stream(stream)), "heff_davidson")
 
 
 def heff_lanczos_workspace_size(plan, n_iter):

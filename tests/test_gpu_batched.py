@@ -101,3 +101,32 @@ def test_electron_full_size_batch_of_32_sampled():
         err = np.linalg.norm(yb[mask] - ref[mask]) / np.linalg.norm(ref[mask])
         print(f"electron m=2048 batch entry {b}: rel err {err:.2e}")
         assert err < 1e-3
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_apply_host_equals_device_apply(pinned):
+    """heff_apply_host (host inputs -> staging -> apply -> host y) gives bitwise the result
+    of heff_apply on device copies of the same inputs, on two alternating streams."""
+    w, lays, plan, d, xs = _setup("spin_m1024", 1)
+    ws = [plan.workspace(), plan.workspace()]
+    y_dev = torch.empty_like(xs[0])
+    heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs[0], y_dev, ws[0])
+    torch.cuda.synchronize()
+    host = {k: v.cpu() for k, v in d.items()}
+    host["x"] = xs[0].cpu()
+    if pinned:
+        host = {k: v.pin_memory() for k, v in host.items()}
+    ys = [torch.full((xs[0].numel(),), float("nan"), dtype=torch.float32) for _ in range(2)]
+    if pinned:
+        ys = [t.pin_memory() for t in ys]
+    staging = [torch.empty(heff.heff_apply_host_staging_size(plan.handle), dtype=torch.uint8, device="cuda")
+               for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k in range(4):
+        j = k % 2
+        heff.heff_apply_host(plan.handle, host["L"], host["W1"], host["W2"], host["R"], host["x"], ys[j],
+                             staging[j], ws[j], streams[j])
+    torch.cuda.synchronize()
+    ref = y_dev.cpu()
+    for t in ys:
+        assert torch.equal(t, ref)

@@ -65,3 +65,16 @@ def test_hubbard_chain_6_reaches_ed():
     r = dmrg.dmrg(mpo, (6, 0), [16, 64, 64, 64], n_iter=25)
     print(f"Hubbard L=6: {r['energy']:.12f} ED {E_ed:.12f}")
     assert abs(r["energy"] - E_ed) < 1e-9 * abs(E_ed)
+
+
+def test_heisenberg_chain_10_davidson_subspace_2_reaches_ed():
+    """The paper's sweep setting: Algorithm 1 with a subspace of 2 at every bond."""
+    from oracle import kron
+    n = 10
+    mpo = wl.heisenberg_mpo(n, wl.chain_pairs(n, [1.0]))
+    E_ed = kron.ground_energy(kron.heisenberg_hamiltonian(n, wl.chain_pairs(n, [1.0])),
+                              kron.basis_charges(n, wl.spin_phys()), (0,))
+    r = dmrg.dmrg(mpo, (0,), [32] * 10, solver="davidson", davidson_vecs=2)
+    print(f"L=10 chain, Davidson(2): sweeps {['%.12f' % e for e in r['sweep_energies']]} ED {E_ed:.12f}")
+    assert r["energy"] >= E_ed - 1e-12 * abs(E_ed)
+    assert abs(r["energy"] - E_ed) < 1e-8 * abs(E_ed)

@@ -135,3 +135,67 @@ def test_restart_from_converged_vector_breaks_down_cleanly():
     assert abs(res2[0] - res[0]) < 1e-10 * abs(res[0])
     ov = abs(float(torch.dot(x2, x)))
     assert ov > 1 - 1e-10, ov
+
+
+# ---------------------------------------------------------------- Davidson (Algorithm 1)
+def _davidson(p, prec, max_vecs, tol, x0=None, seed=7):
+    P = p.plan(prec)
+    ws = P.workspace()
+    dw = torch.empty(heff.heff_davidson_workspace_size(P.handle, max_vecs), dtype=torch.uint8, device="cuda")
+    x0 = p.x0 if x0 is None else x0
+    rnd = torch.from_numpy(np.random.default_rng(seed).standard_normal(x0.numel())).cuda()
+    x = torch.empty_like(x0)
+    res = torch.zeros(3, dtype=torch.float64, device="cuda")
+    d = p.d
+    heff.heff_davidson(P.handle, d["L"], d["W1"], d["W2"], d["R"], x0, rnd, max_vecs, tol, x, res, ws, dw)
+    torch.cuda.synchronize()
+    return res.cpu().numpy(), x
+
+
+@pytest.mark.parametrize("name,max_vecs", [("spin_m24", 12), ("electron_m40", 16), ("spin_m64", 2),
+                                           ("spin_m1024", 2), ("spin_m200", 6)])
+def test_fp64_davidson_matches_oracle_algorithm_1(name, max_vecs):
+    """Same start vector, same stopping rule: the GPU Davidson (two classical Gram-Schmidt
+    passes) and the oracle's (modified Gram-Schmidt) agree to rounding."""
+    p = LzProblem(name)
+    res, x = _davidson(p, "fp64", max_vecs, 1e-10)
+    L, W1, W2, R, xo = oh.problem_from_workload(p.w)
+
+    def mv(v):
+        return oh.heff_apply(L, W1, W2, R, xo.copy().set_flat(v)).flat()
+    lam_o, x_o = eig.davidson(mv, xo.flat(), max_vecs, tol=1e-10)
+    assert abs(res[0] - lam_o) < 1e-10 * abs(lam_o), (res[0], lam_o)
+    ov = abs(float(np.dot(x.cpu().numpy(), x_o)))
+    assert ov > 1 - 1e-8, ov
+    assert 1 <= res[2] <= max_vecs
+    print(f"{name} davidson({max_vecs}): lambda {res[0]:.15f} oracle {lam_o:.15f} |q| {res[1]:.2e} vecs {int(res[2])}")
+
+
+def test_davidson_converges_to_exact_lowest_eigenvalue():
+    p = LzProblem("spin_m24")
+    E0 = p.exact_lowest()
+    res, x = _davidson(p, "fp64", 60, 1e-10)
+    assert abs(res[0] - E0) < 1e-10 * abs(E0)
+    assert res[1] < 1e-9 * abs(E0)
+
+
+def test_davidson_from_an_eigenvector_stays_finite():
+    """Started from a converged eigenvector with tol = 0 the correction q is rounding noise
+    (the case Algorithm 1's randomisation guards); the result must stay that eigenpair."""
+    p = LzProblem("spin_m24")
+    res, x = p.lanczos("fp64", min(120, p.lays[4].nelem))
+    r2, x2 = _davidson(p, "fp64", 4, 0.0, x0=x.clone())
+    assert np.isfinite(r2).all() and torch.isfinite(x2).all()
+    assert abs(r2[0] - res[0]) < 1e-10 * abs(res[0])
+    assert abs(float(torch.dot(x2, x))) > 1 - 1e-10
+
+
+def test_davidson_with_bf16x3_matvecs():
+    """BF16x3 matvecs inside the FP64 Davidson (the subspace that converges in FP64 above):
+    the Ritz value carries the split precision, the FP64 Rayleigh quotient of the vector
+    does not."""
+    p = LzProblem("spin_m24")
+    E0 = p.exact_lowest()
+    res, x = _davidson(p, "bf16x3", 60, 1e-7)
+    assert abs(res[0] - E0) < 1e-3 * abs(E0)
+    assert abs(p.rayleigh_fp64(x) - E0) < 1e-8 * abs(E0)
