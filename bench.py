@@ -30,16 +30,20 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1"): (470.196224e6 + 286.387968e6, "c78b1d324289cd9f"),
-    ("spin_m4096", "bf16x3", "gemm2"): (810.263040e6 + 44.315904e6, "c78b1d324289cd9f"),
+    ("spin_m4096", "bf16x3", "gemm1"): (470.196224e6 + 286.387968e6, "9cb355059336568e"),
+    ("spin_m4096", "bf16x3", "gemm2"): (810.263040e6 + 44.315904e6, "9cb355059336568e"),
 }
 
 
 def _src_sha():
+    """Hash of the device code of tc_gemm.cu (everything before its host-side section), the
+    code the ncu traffic figures were measured on."""
     import hashlib
     p = os.path.join(ROOT, "paper_2007_05540_gb300", "csrc", "tc_gemm.cu")
     with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        txt = f.read()
+    cut = txt.find(b"// ---------------------------------------------------------------- host side")
+    return hashlib.sha256(txt[:cut] if cut >= 0 else txt).hexdigest()[:16]
 
 
 def parse():
@@ -288,6 +292,25 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     out["env_update"] = env_update_timing(w, dev, stream)
     # Rayleigh-quotient gradients: whole intermediates at m = 1024, streamed at m = 4096
     out["backward"] = backward_timing(dev, stream)
+
+    # the paper's own spin lattice: the 6 x 6 J1-J2 cylinder MPO window (k = 26) at m = 4096
+    wj, lj, bj = make_problem("spin_j1j2_6x6_m4096", 0)
+    Pj = heff.Plan(*lj, bj["W1"], bj["W2"], "bf16x3", "f32")
+    dj = {k: torch.from_numpy(np.asarray(v)).to(dev, torch.float32) for k, v in bj.items()}
+    wsj = Pj.workspace(dev)
+    yj = torch.empty_like(dj["x"])
+    tnj = heff.heff_plan_autotune(Pj.handle, dj["L"], dj["W1"], dj["W2"], dj["R"], dj["x"], yj, wsj, stream)
+
+    def fj():
+        heff.heff_apply(Pj.handle, dj["L"], dj["W1"], dj["W2"], dj["R"], dj["x"], yj, wsj, stream)
+    for _ in range(3):
+        fj()
+    msj = _events_ms(fj, 10, stream, flush)
+    out["j1j2_6x6_lattice_m4096"] = {
+        "applies_per_s": 1000.0 / msj, "ms": msj, "tile_n": list(tnj), "mpo_k": int(wj.W1.shape[0]),
+        "flops_per_apply": Pj.flops_canonical, "tflops_canonical": Pj.flops_canonical / (msj * 1e-3) / 1e12,
+        "note": "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"}
+    del Pj, dj, wsj, yj
 
     # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles)
     nb = 32

@@ -60,7 +60,7 @@ def _plan(w, lays, bufs, precision="fp64", io="f64"):
     return heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], precision, io)
 
 
-@pytest.mark.parametrize("name", ["spin_m24", "spin_m64", "electron_m40", "electron_m96"])
+@pytest.mark.parametrize("name", ["spin_m24", "spin_m64", "electron_m40", "electron_m96", "spin_j1j2_6x6_m200"])
 def test_canonical_flops_match_oracle(name):
     w = wl.workload_by_name(name)
     lays, bufs = library_problem(w)

@@ -14,7 +14,7 @@ import numpy as np
 
 from .sectors import (binomial_sectors, paper_model_sectors, electron_sectors,
                       spin_phys, electron_phys)
-from .mpo import heisenberg_mpo, hubbard_mpo, chain_pairs, bulk_window
+from .mpo import heisenberg_mpo, hubbard_mpo, chain_pairs, cylinder_pairs, bulk_window
 
 TAG_L, TAG_R, TAG_X, TAG_SITE = 1, 2, 3, 4
 
@@ -141,6 +141,16 @@ def spin_window(couplings=SPIN_COUPLINGS):
     return bulk_window(mpo, R + 1)
 
 
+def lattice_window(Lx=6, Ly=6, J1=1.0, J2=0.5):
+    """Two-site window of the snake-ordered Lx x Ly J1-J2 Heisenberg cylinder MPO (the
+    paper's spin lattice, Section V), at the first bond triple with the largest total
+    channel count (the MPO's k there: 26 on all three bonds for 6 x 6)."""
+    n = Lx * Ly
+    mpo = heisenberg_mpo(n, cylinder_pairs(Lx, Ly, J1, J2))
+    best = max(range(n - 1), key=lambda s: (mpo.bond_dim(s) + mpo.bond_dim(s + 1) + mpo.bond_dim(s + 2), -s))
+    return bulk_window(mpo, best)
+
+
 def electron_window(t=1.0, U=8.0, R=5):
     """Bulk two-site window of the range-R Hubbard chain MPO (k = 2 + 4R).
 
@@ -158,7 +168,7 @@ def electron_window(t=1.0, U=8.0, R=5):
 
 
 def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLINGS,
-                       name=None):
+                       name=None, window=None):
     """Spin-1/2 two-site H_eff inputs.
 
     ``model="binomial"``: left/right bonds from ``binomial_sectors`` with
@@ -173,7 +183,7 @@ def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLIN
         bq, bd = paper_model_sectors(m)
     else:
         raise ValueError(model)
-    win = spin_window(couplings)
+    win = spin_window(couplings) if window is None else window
     return HeffWorkload(
         name=name or f"spin_{model}_m{m}", alpha_q=aq, alpha_d=ad, beta_q=bq, beta_d=bd,
         phys=spin_phys(), W1=win["W1"], W2=win["W2"], ql=win["ql"], qm=win["qm"],
@@ -203,6 +213,12 @@ def workload_by_name(name):
         "spin_m4096": lambda: spin_heff_workload(4096, 40, 0, name="spin_m4096"),
         "spin_paper_m4096": lambda: spin_heff_workload(4096, 0, 0, model="paper",
                                                        name="spin_paper_m4096"),
+        "spin_j1j2_6x6_m1024": lambda: spin_heff_workload(1024, 30, 0, name="spin_j1j2_6x6_m1024",
+                                                          window=lattice_window()),
+        "spin_j1j2_6x6_m4096": lambda: spin_heff_workload(4096, 40, 0, name="spin_j1j2_6x6_m4096",
+                                                          window=lattice_window()),
+        "spin_j1j2_6x6_m200": lambda: spin_heff_workload(200, 10, 7, name="spin_j1j2_6x6_m200",
+                                                         window=lattice_window()),
         "electron_m2048": lambda: electron_heff_workload(2048, 0, name="electron_m2048"),
         "spin_m24": lambda: spin_heff_workload(24, 6, 9, name="spin_m24"),
         "spin_m64": lambda: spin_heff_workload(64, 8, 5, name="spin_m64"),
