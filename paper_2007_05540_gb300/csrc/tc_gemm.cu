@@ -127,7 +127,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
     d |= (uint64_t)((8 * SWZ) >> 4) << 32;           // stride byte offset: one 8-row group
     d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)(SWZ == 128 ? 2 : 4) << 61;       // SWIZZLE_128B / SWIZZLE_64B
+    d |= (uint64_t)(SWZ == 128 ? 2 : (SWZ == 64 ? 4 : 6)) << 61;   // SWIZZLE_128B / 64B / 32B
     return d;
 }
 
@@ -527,7 +527,8 @@ int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, u
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    swz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    swz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                               : (swz == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(HEFF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return HEFF_OK;
@@ -535,8 +536,11 @@ int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, u
 
 // Kernel configurations: 64-byte K blocks; N tile 256 with a 4-stage ring (4 x 48 KB,
 // 512 TMEM columns) or N tile 128 with a 6-stage ring (6 x 32 KB, 256 TMEM columns).
-constexpr int SWZ_TC = 64;
-// K blocks per accumulation chunk in GEMM 2 (32 bf16 / 16 tf32 elements per block): long
+#ifndef HEFF_SWZ_TC
+#define HEFF_SWZ_TC 64
+#endif
+constexpr int SWZ_TC = HEFF_SWZ_TC;      // bytes of one K block row (32 or 64)
+// 64-byte K spans per accumulation chunk in GEMM 2 (32 bf16 / 16 tf32 elements each): long
 // enough that a chunk's MMAs (about 0.5 us per block at N = 256) hide the epilogue's
 // read-add-write of the previous chunk, short enough to bound the accumulation bias
 // (measured at m = 4096: norm-wise error of y 1.4e-5 -> 5e-6 (bf16x3), 2.6e-5 -> 3e-6 (tf32x3))
@@ -551,7 +555,7 @@ constexpr int KCHUNK_TF32 = HEFF_KCHUNK_TF32;
 
 template <int PREC, int TN_TC>
 int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
-    constexpr int STAGES_TC = TN_TC == 256 ? 4 : 6;
+    constexpr int STAGES_TC = (192 * 1024) / (2 * (128 + TN_TC) * SWZ_TC);   // a 192 KB ring
     using S = Smem<TN_TC, STAGES_TC, SWZ_TC>;
     auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES_TC, SWZ_TC>;
     static bool attr = false;
@@ -618,7 +622,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
             g.a_batch_rows = p->rows_t; g.b_batch_rows = 0;
             for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
             g.mode = 1;
-            g.kchunk = PREC == HEFF_PREC_TF32X3 ? KCHUNK_TF32 : KCHUNK_BF16;
+            g.kchunk = (PREC == HEFF_PREC_TF32X3 ? KCHUNK_TF32 : KCHUNK_BF16) * (64 / SWZ_TC);
             g.y_f64 = p->opts.io_dtype == HEFF_DTYPE_F64;
         }
         const long total = (long)g.ntasks * nb;
