@@ -15,7 +15,10 @@ namespace heff {
 // Padding unit of every contraction (K) segment in the workspace operand arrays: one K
 // block of the tensor-core kernel (64-byte swizzled rows: 32 bf16 or 16 fp32 elements;
 // the FP64 kernel steps K by 16).  K tiles never straddle segments.
-constexpr int KPAD = 32;
+#ifndef HEFF_KPAD
+#define HEFF_KPAD 32
+#endif
+constexpr int KPAD = HEFF_KPAD;
 
 inline int64_t pad_up(int64_t v, int64_t p) { return (v + p - 1) / p * p; }
 

@@ -539,7 +539,8 @@ int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, u
 #ifndef HEFF_SWZ_TC
 #define HEFF_SWZ_TC 64
 #endif
-constexpr int SWZ_TC = HEFF_SWZ_TC;      // bytes of one K block row (32 or 64)
+constexpr int SWZ_TC = HEFF_SWZ_TC;      // bytes of one K block row (32, 64 or 128)
+static_assert(SWZ_TC / (int)sizeof(__nv_bfloat16) <= KPAD, "a K block must not span two contraction segments");
 // 64-byte K spans per accumulation chunk in GEMM 2 (32 bf16 / 16 tf32 elements each): long
 // enough that a chunk's MMAs (about 0.5 us per block at N = 256) hide the epilogue's
 // read-add-write of the previous chunk, short enough to bound the accumulation bias
@@ -622,7 +623,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
             g.a_batch_rows = p->rows_t; g.b_batch_rows = 0;
             for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
             g.mode = 1;
-            g.kchunk = (PREC == HEFF_PREC_TF32X3 ? KCHUNK_TF32 : KCHUNK_BF16) * (64 / SWZ_TC);
+            g.kchunk = (PREC == HEFF_PREC_TF32X3 ? KCHUNK_TF32 : KCHUNK_BF16) * 64 / SWZ_TC;
             g.y_f64 = p->opts.io_dtype == HEFF_DTYPE_F64;
         }
         const long total = (long)g.ntasks * nb;
