@@ -307,7 +307,7 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
         fj()
     msj = _events_ms(fj, 10, stream, flush)
     out["j1j2_6x6_lattice_m4096"] = {
-        "applies_per_s": 1000.0 / msj, "ms": msj, "tile_n": list(tnj), "mpo_k": int(wj.W1.shape[0]),
+        "applies_per_s": 1000.0 / msj, "ms": msj, "tile_variant": list(tnj), "mpo_k": int(wj.W1.shape[0]),
         "flops_per_apply": Pj.flops_canonical, "tflops_canonical": Pj.flops_canonical / (msj * 1e-3) / 1e12,
         "note": "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"}
     del Pj, dj, wsj, yj
@@ -336,7 +336,7 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     ms = _events_ms(g.replay, 10, torch.cuda.current_stream(), flush)
     fl = Pe.flops_canonical
     out["electron_m2048_batch32_graph"] = {
-        "applies_per_s": nb * 1000.0 / ms, "ms_per_batch": ms, "tile_n": list(tn),
+        "applies_per_s": nb * 1000.0 / ms, "ms_per_batch": ms, "tile_variant": list(tn),
         "tflops_canonical": nb * fl / (ms * 1e-3) / 1e12, "flops_per_apply": fl,
         "sectors": int(len(we.alpha_d)), "max_block": int(we.alpha_d.max()), "mpo_k": int(we.W1.shape[0])}
     return out
@@ -543,7 +543,7 @@ def run_ours(args):
         "data": "synthetic (seeded; no dataset)",
         "config": {"workload": args.workload, "m": int(w.alpha_d.sum()), "sectors": int(len(w.alpha_d)),
                    "mpo_k": int(w.W1.shape[0]), "d": int(w.W1.shape[1]), "precision": prec, "io_dtype": io,
-                   "tile_n": list(tile_n),
+                   "tile_variant": list(tile_n),
                    "autotune_ms": [round(v, 4) for v in tune_ms] if not args.no_autotune else None,
                    "l2": "flushed (512 MB write) between timed steps; working set > L2",
                    "parallelism": f"independent problems per rank x{world}"},

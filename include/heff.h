@@ -152,10 +152,10 @@ int heff_plan_flops(const heff_plan* plan, double* canonical, double* executed);
  * Plan statistics for diagnostics, stats[24]: [0] charge sectors, [1] LW row groups,
  * [2] RW row groups, [3] GEMM-1 tasks, [4] GEMM-2 tasks, [5] pack tiles, [6] mix tiles,
  * [7] mix terms, [8] XT rows, [9] XT/LW pitch, [10] LW rows, [11] T rows, [12] T/RW
- * pitch, [13] RW rows, [14] tile M, [15] GEMM-1 tile N, [16] canonical flops of the first
+ * pitch, [13] RW rows, [14] tile M, [15] GEMM-1 tile variant (HEFF_TILE_*), [16] canonical flops of the first
  * contraction, [17] of the second, [18] GEMM-1 flops over valid rows, columns and
  * unpadded K, [19] the same for GEMM 2, [20] GEMM-1 issued flops (padded K), [21] GEMM 2,
- * [22] GEMM-2 tile N.
+ * [22] GEMM-2 tile variant.
  */
 int heff_plan_stats(const heff_plan* plan, int64_t* stats /* [24] */);
 
@@ -392,23 +392,37 @@ int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1, const voi
                        const void* x, void* y, void* stream);
 
 /*
- * heff_plan_autotune -- choose the output tile width (N = 256 or 128 columns) of each of
- * the two tensor-core GEMMs by timing both on the given inputs (which must be valid
- * tensors for the plan; y and the workspace are overwritten) and keep the faster one in
- * the plan (each candidate: one warm-up launch, then the median of five timed launches).
- * tn_out (host, may be NULL) receives the chosen widths {GEMM 1, GEMM 2}; ms_out (host,
- * may be NULL) the median times {GEMM 1 at 256, at 128, GEMM 2 at 256, at 128} in ms.
- * No-op for the FP64 precision.  Synchronises (event timing); call it before capturing
- * applies into a CUDA graph.
+ * Tensor-core tile variants of a GEMM (the plan builds all three task lists):
+ *   HEFF_TILE_256       one CTA per 128 x 256 output tile (the default)
+ *   HEFF_TILE_128       one CTA per 128 x 128 output tile
+ *   HEFF_TILE_PAIR_256  128 x 256 tiles in pairs that share their B rows and K segments, run
+ *                       by the two CTAs of a cluster: each CTA loads half of the B box,
+ *                       multicast to both, so B is read once per pair
+ * Results are bitwise identical across variants (a tile's K order does not depend on them).
+ */
+#define HEFF_TILE_256 256
+#define HEFF_TILE_128 128
+#define HEFF_TILE_PAIR_256 512
+#define HEFF_TILE_VARIANTS 3
+
+/*
+ * heff_plan_autotune -- choose the tile variant of each of the two tensor-core GEMMs by
+ * timing every variant on the given inputs (which must be valid tensors for the plan; y and
+ * the workspace are overwritten) and keep the fastest in the plan (each candidate: one
+ * warm-up launch, then the median of five timed launches).  tn_out (host, may be NULL)
+ * receives the chosen variants {GEMM 1, GEMM 2}; ms_out (host, may be NULL, 2 x
+ * HEFF_TILE_VARIANTS floats) the median times {GEMM 1: 256, 128, pairs; GEMM 2: 256, 128,
+ * pairs} in ms (0 where a variant has no task list).  No-op for the FP64 precision.
+ * Synchronises (event timing); call it before capturing applies into a CUDA graph.
  */
 int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                        const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream,
                        int32_t* tn_out, float* ms_out);
 
 /*
- * Select the tile width (N of a tensor-core tile: 256 or 128) of GEMM 1 and GEMM 2
- * without measuring (0 keeps the current choice); heff_plan_autotune picks by timing.
- * Results do not depend on the choice.  Errors: INVALID_ARG (width not built for this
+ * Select the tile variant (HEFF_TILE_256, HEFF_TILE_128 or HEFF_TILE_PAIR_256) of GEMM 1 and
+ * GEMM 2 without measuring (0 keeps the current choice); heff_plan_autotune picks by timing.
+ * Results do not depend on the choice.  Errors: INVALID_ARG (variant not built for this
  * plan, or an FP64 plan).
  */
 int heff_plan_select_tiles(heff_plan* plan, int32_t tn1, int32_t tn2);

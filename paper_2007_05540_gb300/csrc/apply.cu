@@ -63,15 +63,13 @@ template <> struct Plane<HEFF_PREC_TF32X3> {
 
 // ------------------------------------------------------------------ pack x -> XT
 template <typename In, int PREC>
-__global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, PtrBatch xs,
-                                                   char* __restrict__ xt, int64_t ld, int64_t plane_elems,
-                                                   int64_t batch_elems) {
+__device__ __forceinline__ void pack_tile(const PackTile& t, int bz, const PtrBatch& xs, char* __restrict__ xt,
+                                          int64_t ld, int64_t plane_elems, int64_t batch_elems) {
     using E = typename Plane<PREC>::T;
     using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
     __shared__ Acc s[32][33];
-    const PackTile t = tiles[blockIdx.x];
-    const In* x = static_cast<const In*>(xs.p[blockIdx.y]);
-    E* hi = reinterpret_cast<E*>(xt) + (int64_t)blockIdx.y * batch_elems;
+    const In* x = static_cast<const In*>(xs.p[bz]);
+    E* hi = reinterpret_cast<E*>(xt) + (int64_t)bz * batch_elems;
     E* lo = hi + plane_elems;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     // read rows a (stride m_b), columns b contiguous
@@ -95,24 +93,44 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ 
     }
 }
 
+template <typename In, int PREC>
+__global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, PtrBatch xs,
+                                                   char* __restrict__ xt, int64_t ld, int64_t plane_elems,
+                                                   int64_t batch_elems) {
+    pack_tile<In, PREC>(tiles[blockIdx.x], blockIdx.y, xs, xt, ld, plane_elems, batch_elems);
+}
+
 // ------------------------------------------------------------------ LW / RW preparation
 #ifndef HEFF_MIX_UNROLL
-#define HEFF_MIX_UNROLL 2      // column pairs per lane and pass
+#define HEFF_MIX_UNROLL 4      // column pairs per lane and pass
 #endif
+#ifndef HEFF_MIX_ROWS
+#define HEFF_MIX_ROWS 1        // rows per warp and pass
+#endif
+struct MixArgs {
+    const MixTile* tiles;
+    const MixTerm* terms;
+    const void *L, *W1, *W2, *R;
+    char* lw; int64_t ld_lw, lw_plane;
+    char* rw; int64_t ld_rw, rw_plane;
+};
+
 template <typename In, int PREC>
-__global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ tiles,
-                                                  const MixTerm* __restrict__ terms,
-                                                  const In* __restrict__ L, const In* __restrict__ W1,
-                                                  const In* __restrict__ W2, const In* __restrict__ R,
-                                                  char* __restrict__ lw, int64_t ld_lw, int64_t lw_plane,
-                                                  char* __restrict__ rw, int64_t ld_rw, int64_t rw_plane) {
+__device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
+    const MixTerm* __restrict__ terms = a.terms;
+    const In* __restrict__ L = static_cast<const In*>(a.L);
+    const In* __restrict__ W1 = static_cast<const In*>(a.W1);
+    const In* __restrict__ W2 = static_cast<const In*>(a.W2);
+    const In* __restrict__ R = static_cast<const In*>(a.R);
+    char* __restrict__ lw = a.lw;
+    char* __restrict__ rw = a.rw;
+    const int64_t ld_lw = a.ld_lw, lw_plane = a.lw_plane, ld_rw = a.ld_rw, rw_plane = a.rw_plane;
     // FP64 path accumulates in double; the split paths in float (1-4 terms, each product
     // exact to 24 bits, well inside the 16-bit (bf16 hi+lo) / 22-bit (tf32 hi+lo) split).
     using E = typename Plane<PREC>::T;
     using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
     __shared__ Acc coef[64];
     __shared__ int64_t srco[64];
-    const MixTile t = tiles[blockIdx.x];
     const In* src = t.which ? R : L;
     const In* W = t.which ? W2 : W1;
     const int nt = t.term_count < 64 ? t.term_count : 64;
@@ -126,56 +144,77 @@ __global__ void __launch_bounds__(256) mix_kernel(const MixTile* __restrict__ ti
     const int64_t ld = t.which ? ld_rw : ld_lw;
     E* lo = hi + (t.which ? rw_plane : lw_plane);
     // warps over rows, lanes over column pairs: each thread writes two adjacent columns
-    // (dst_col0 and cols_pad are multiples of 32, so the pair stores are aligned), four
-    // pairs 64 columns apart per pass, with all loads of a term issued before its FMAs
-    // (eight loads in flight per thread: the kernel is bound by HBM latency x bytes in flight)
+    // (dst_col0 and cols_pad are multiples of 32, so the pair stores are aligned) of RW rows,
+    // U pairs 64 columns apart per pass, with all loads of a term issued before its FMAs
+    // (2 RW U loads in flight per thread: the kernel is bound by HBM latency x bytes in flight)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int U = HEFF_MIX_UNROLL;
-    for (int rr = warp; rr < t.nrows; rr += blockDim.x >> 5) {
-        const int r = t.r0 + rr;
-        const int64_t rc0 = (int64_t)r * t.cols;
-        E* hrow = hi + (t.dst_row0 + r) * ld + t.dst_col0;
-        E* lrow = lo + (t.dst_row0 + r) * ld + t.dst_col0;
-        for (int cb = 2 * lane; cb < t.cols_pad; cb += 64 * U) {
-            Acc a0[U], a1[U];
+    constexpr int RW = HEFF_MIX_ROWS;
+    const int nw = blockDim.x >> 5;
+    for (int rr = warp * RW; rr < t.nrows; rr += nw * RW) {
+        int64_t rc[RW];
+        bool rv[RW];
 #pragma unroll
-            for (int u = 0; u < U; ++u) { a0[u] = 0; a1[u] = 0; }
+        for (int i = 0; i < RW; ++i) {
+            rv[i] = rr + i < t.nrows;
+            rc[i] = (int64_t)(t.r0 + rr + i) * t.cols;
+        }
+        for (int cb = 2 * lane; cb < t.cols_pad; cb += 64 * U) {
+            Acc a0[RW][U], a1[RW][U];
+#pragma unroll
+            for (int i = 0; i < RW; ++i)
+#pragma unroll
+                for (int u = 0; u < U; ++u) { a0[i][u] = 0; a1[i][u] = 0; }
             for (int k = 0; k < t.term_count; ++k) {
                 const In* s;
                 Acc cf;
                 if (k < nt) {
-                    s = src + srco[k] + rc0;
+                    s = src + srco[k];
                     cf = coef[k];
                 } else {                                      // rare: more than 64 terms
                     const MixTerm m = terms[t.term_begin + k];
-                    s = src + m.src_off + rc0;
+                    s = src + m.src_off;
                     cf = (Acc)W[m.w_idx];
                 }
-                In v0[U], v1[U];
+                In v0[RW][U], v1[RW][U];
+#pragma unroll
+                for (int i = 0; i < RW; ++i)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int c = cb + 64 * u;
+                        v0[i][u] = rv[i] && c < t.cols ? s[rc[i] + c] : (In)0;
+                        v1[i][u] = rv[i] && c + 1 < t.cols ? s[rc[i] + c + 1] : (In)0;
+                    }
+#pragma unroll
+                for (int i = 0; i < RW; ++i)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        a0[i][u] += cf * (Acc)v0[i][u];
+                        a1[i][u] += cf * (Acc)v1[i][u];
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < RW; ++i) {
+                if (!rv[i]) break;
+                const int64_t o = (t.dst_row0 + t.r0 + rr + i) * ld + t.dst_col0;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int c = cb + 64 * u;
-                    v0[u] = c < t.cols ? s[c] : (In)0;
-                    v1[u] = c + 1 < t.cols ? s[c + 1] : (In)0;
+                    if (c >= t.cols_pad) break;
+                    E h0, l0, h1, l1;
+                    Plane<PREC>::split(a0[i][u], h0, l0);
+                    Plane<PREC>::split(a1[i][u], h1, l1);
+                    Plane<PREC>::store2(hi + o + c, h0, h1);
+                    if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lo + o + c, l0, l1);
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    a0[u] += cf * (Acc)v0[u];
-                    a1[u] += cf * (Acc)v1[u];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int c = cb + 64 * u;
-                if (c >= t.cols_pad) break;
-                E h0, l0, h1, l1;
-                Plane<PREC>::split(a0[u], h0, l0);
-                Plane<PREC>::split(a1[u], h1, l1);
-                Plane<PREC>::store2(hrow + c, h0, h1);
-                if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lrow + c, l0, l1);
             }
         }
     }
+}
+
+template <typename In, int PREC>
+__global__ void __launch_bounds__(256) mix_kernel(MixArgs a) {
+    mix_tile<In, PREC>(a.tiles[blockIdx.x], a);
 }
 
 // ------------------------------------------------------------------ FP64 CUDA-core GEMM
@@ -266,7 +305,7 @@ int plan_upload(heff_plan* p) {
     if ((rc = upload(p->pack, &p->d_pack)) != HEFF_OK) return rc;
     if ((rc = upload(p->mix, &p->d_mix)) != HEFF_OK) return rc;
     if ((rc = upload(p->terms, &p->d_terms)) != HEFF_OK) return rc;
-    for (GemmList* g : {&p->g1, &p->g2, &p->g1_alt, &p->g2_alt}) {
+    for (GemmList* g : {&p->g1, &p->g2, &p->g1_alt, &p->g2_alt, &p->g1_pair, &p->g2_pair}) {
         if ((rc = upload(g->tasks, &g->d_tasks)) != HEFF_OK) return rc;
         if ((rc = upload(g->segs, &g->d_segs)) != HEFF_OK) return rc;
     }
@@ -283,8 +322,10 @@ void plan_free_device(heff_plan* p) {
         if (p->ev[k]) { cudaEventDestroy(static_cast<cudaEvent_t>(p->ev[k])); p->ev[k] = nullptr; }
     cudaFree(p->d_pack); cudaFree(p->d_mix); cudaFree(p->d_terms);
     cudaFree(p->g1.d_tasks); cudaFree(p->g1.d_segs); cudaFree(p->g2.d_tasks); cudaFree(p->g2.d_segs);
-    cudaFree(p->g1_alt.d_tasks); cudaFree(p->g1_alt.d_segs); cudaFree(p->g2_alt.d_tasks); cudaFree(p->g2_alt.d_segs);
-    p->g1_alt.d_tasks = p->g2_alt.d_tasks = nullptr; p->g1_alt.d_segs = p->g2_alt.d_segs = nullptr;
+    for (GemmList* g : {&p->g1_alt, &p->g2_alt, &p->g1_pair, &p->g2_pair}) {
+        cudaFree(g->d_tasks); cudaFree(g->d_segs);
+        g->d_tasks = nullptr; g->d_segs = nullptr;
+    }
     p->d_pack = nullptr; p->d_mix = nullptr; p->d_terms = nullptr;
     p->g1.d_tasks = p->g2.d_tasks = nullptr; p->g1.d_segs = p->g2.d_segs = nullptr;
 }
@@ -323,12 +364,15 @@ int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, 
     return HEFF_OK;
 }
 
+static MixArgs mix_args(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R, char* ws) {
+    return MixArgs{p->d_mix, p->d_terms, L, W1, W2, R, ws + p->off_lw, p->ld_x, p->rows_lw * p->ld_x,
+                   ws + p->off_rw, p->ld_t, p->rows_rw * p->ld_t};
+}
+
 template <typename In, int PREC>
 static void launch_mix_t(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R,
                          char* ws, cudaStream_t st) {
-    mix_kernel<In, PREC><<<(unsigned)p->mix.size(), 256, 0, st>>>(
-        p->d_mix, p->d_terms, (const In*)L, (const In*)W1, (const In*)W2, (const In*)R,
-        ws + p->off_lw, p->ld_x, p->rows_lw * p->ld_x, ws + p->off_rw, p->ld_t, p->rows_rw * p->ld_t);
+    mix_kernel<In, PREC><<<(unsigned)p->mix.size(), 256, 0, st>>>(mix_args(p, L, W1, W2, R, ws));
 }
 
 int launch_mix(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R, void* ws,
@@ -407,16 +451,28 @@ static int do_prepare(heff_plan* plan, const void* L, const void* W1, const void
     return rc;
 }
 
-static int do_matvec(heff_plan* plan, const void* const* x, void* const* y, int nbatch, void* workspace,
-                     void* stream) {
+static int do_gemms(heff_plan* plan, void* const* y, int nbatch, void* workspace, void* stream) {
     int rc;
-    if ((rc = heff::launch_pack_batch(plan, x, nbatch, workspace, stream))) return rc;
-    heff::record_phase(plan, 2, stream);
     if ((rc = heff::launch_gemm(plan, 1, workspace, y, nbatch, stream))) return rc;
     heff::record_phase(plan, 3, stream);
     if ((rc = heff::launch_gemm(plan, 2, workspace, y, nbatch, stream))) return rc;
     heff::record_phase(plan, 4, stream);
     return HEFF_OK;
+}
+
+static int do_matvec(heff_plan* plan, const void* const* x, void* const* y, int nbatch, void* workspace,
+                     void* stream) {
+    int rc;
+    if ((rc = heff::launch_pack_batch(plan, x, nbatch, workspace, stream))) return rc;
+    heff::record_phase(plan, 2, stream);
+    return do_gemms(plan, y, nbatch, workspace, stream);
+}
+
+static int do_apply(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                    const void* const* x, void* const* y, int nbatch, void* workspace, void* stream) {
+    plan->ev_prepare = true;
+    int rc = do_prepare(plan, L, W1, W2, R, workspace, stream);
+    return rc ? rc : do_matvec(plan, x, y, nbatch, workspace, stream);
 }
 
 extern "C" int heff_prepare(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
@@ -452,9 +508,7 @@ extern "C" int heff_apply(heff_plan* plan, const void* L, const void* W1, const 
     if (rc) return rc;
     const void* xs[1] = {x};
     void* ys[1] = {y};
-    plan->ev_prepare = true;
-    if ((rc = do_prepare(plan, L, W1, W2, R, workspace, stream))) return rc;
-    return do_matvec(plan, xs, ys, 1, workspace, stream);
+    return do_apply(plan, L, W1, W2, R, xs, ys, 1, workspace, stream);
 }
 
 namespace {
@@ -522,12 +576,30 @@ extern "C" int heff_apply_batched(heff_plan* plan, const void* L, const void* W1
     int rc = check_ws(plan, workspace, workspace_bytes);
     if (rc) return rc;
     plan->ev_prepare = true;
-    if ((rc = do_prepare(plan, L, W1, W2, R, workspace, stream))) return rc;
-    return do_matvec(plan, x, y, nbatch, workspace, stream);
+    return do_apply(plan, L, W1, W2, R, x, y, nbatch, workspace, stream);
 }
 
-// Tile-shape autotuner: time each GEMM with the N = 256 and N = 128 task lists on the
-// caller's inputs and keep the faster one per GEMM (tensor-core precisions only).
+// Tile-shape autotuner: time each GEMM with every task list the plan built (N = 256, N = 128,
+// N = 256 in CTA pairs) on the caller's inputs and keep the fastest one per GEMM (tensor-core
+// precisions only).
+namespace {
+// the plan's task lists of one GEMM, the active one first
+void gemm_variants(heff_plan* p, int which, heff::GemmList* v[HEFF_TILE_VARIANTS]) {
+    v[0] = which == 1 ? &p->g1 : &p->g2;
+    v[1] = which == 1 ? &p->g1_alt : &p->g2_alt;
+    v[2] = which == 1 ? &p->g1_pair : &p->g2_pair;
+}
+int tile_code(const heff::GemmList& g) { return g.tn * g.cl; }
+void record_tiles(heff_plan* p) {
+    p->stats[3] = (int64_t)p->g1.tasks.size();
+    p->stats[4] = (int64_t)p->g2.tasks.size();
+    p->stats[15] = tile_code(p->g1);
+    p->stats[22] = tile_code(p->g2);
+}
+// slot of a tile code in the autotuner's report: 256, 128, 512
+int code_slot(int code) { return code == 256 ? 0 : (code == 128 ? 1 : 2); }
+}  // namespace
+
 extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                                   const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream,
                                   int32_t* tn_out, float* ms_out) {
@@ -535,6 +607,8 @@ extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1
     if (!plan || !L || !W1 || !W2 || !R || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_autotune: null argument");
     int rc = check_ws(plan, workspace, workspace_bytes);
     if (rc) return rc;
+    if (ms_out)
+        for (int i = 0; i < 2 * HEFF_TILE_VARIANTS; ++i) ms_out[i] = 0.f;
     if (plan->opts.precision != HEFF_PREC_FP64 && !plan->g1_alt.tasks.empty()) {
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         const void* xs[1] = {x};
@@ -545,11 +619,14 @@ extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1
         cudaEvent_t e[6];
         for (auto& ev : e) CK(cudaEventCreate(&ev));
         for (int which = 1; which <= 2 && !rc; ++which) {
-            heff::GemmList& act = which == 1 ? plan->g1 : plan->g2;
-            heff::GemmList& alt = which == 1 ? plan->g1_alt : plan->g2_alt;
-            float ms[2] = {0.f, 0.f};
-            for (int v = 0; v < 2 && !rc; ++v) {
-                if (v == 1) std::swap(act, alt);
+            heff::GemmList* v[HEFF_TILE_VARIANTS];
+            gemm_variants(plan, which, v);
+            float ms[HEFF_TILE_VARIANTS];
+            int best = 0;
+            for (int c = 0; c < HEFF_TILE_VARIANTS && !rc; ++c) {
+                ms[c] = 0.f;
+                if (v[c]->tasks.empty() && !v[0]->tasks.empty()) continue;
+                std::swap(*v[0], *v[c]);
                 rc = heff::launch_gemm(plan, which, workspace, ys, 1, stream);
                 CK(cudaEventRecord(e[0], st));
                 for (int r = 0; r < 5 && !rc; ++r) {
@@ -561,24 +638,22 @@ extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1
                     float t[5];
                     for (int r = 0; r < 5; ++r) CK(cudaEventElapsedTime(&t[r], e[r], e[r + 1]));
                     std::sort(t, t + 5);
-                    ms[v] = t[2];
+                    ms[c] = t[2];
+                    if (ms[c] < ms[best]) best = c;
                 }
-                if (v == 1) std::swap(act, alt);
+                std::swap(*v[0], *v[c]);
+                if (ms_out && !rc) ms_out[HEFF_TILE_VARIANTS * (which - 1) + code_slot(tile_code(*v[c]))] = ms[c];
             }
             if (rc) break;
-            if (ms_out) { ms_out[2 * (which - 1)] = ms[0]; ms_out[2 * (which - 1) + 1] = ms[1]; }
-            if (ms[1] < ms[0]) std::swap(act, alt);
+            if (best) std::swap(*v[0], *v[best]);
         }
         for (auto& ev : e) cudaEventDestroy(ev);
         if (rc) return rc;
-        plan->stats[3] = (int64_t)plan->g1.tasks.size();
-        plan->stats[4] = (int64_t)plan->g2.tasks.size();
-        plan->stats[15] = plan->g1.tn;
-        plan->stats[22] = plan->g2.tn;
+        record_tiles(plan);
     }
     if (tn_out) {
-        tn_out[0] = plan->g1.tn;
-        tn_out[1] = plan->g2.tn;
+        tn_out[0] = tile_code(plan->g1);
+        tn_out[1] = tile_code(plan->g2);
     }
     return HEFF_OK;
 }
@@ -586,20 +661,19 @@ extern "C" int heff_plan_autotune(heff_plan* plan, const void* L, const void* W1
 extern "C" int heff_plan_select_tiles(heff_plan* plan, int32_t tn1, int32_t tn2) {
     heff::clear_error();
     if (!plan) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_select_tiles: null plan");
-    const int tn[2] = {tn1, tn2};
+    const int want[2] = {tn1, tn2};
     for (int which = 1; which <= 2; ++which) {
-        heff::GemmList& act = which == 1 ? plan->g1 : plan->g2;
-        heff::GemmList& alt = which == 1 ? plan->g1_alt : plan->g2_alt;
-        const int want = tn[which - 1];
-        if (want == 0 || want == act.tn) continue;
-        if (alt.tn != want || plan->opts.precision == HEFF_PREC_FP64)
-            return fail(HEFF_ERR_INVALID_ARG, "tile width %d is not available for GEMM %d", want, which);
-        std::swap(act, alt);
+        heff::GemmList* v[HEFF_TILE_VARIANTS];
+        gemm_variants(plan, which, v);
+        const int code = want[which - 1];
+        if (code == 0 || code == tile_code(*v[0])) continue;
+        int c = 1;
+        while (c < HEFF_TILE_VARIANTS && tile_code(*v[c]) != code) ++c;
+        if (c == HEFF_TILE_VARIANTS || plan->opts.precision == HEFF_PREC_FP64)
+            return fail(HEFF_ERR_INVALID_ARG, "tile variant %d is not available for GEMM %d", code, which);
+        std::swap(*v[0], *v[c]);
     }
-    plan->stats[3] = (int64_t)plan->g1.tasks.size();
-    plan->stats[4] = (int64_t)plan->g2.tasks.size();
-    plan->stats[15] = plan->g1.tn;
-    plan->stats[22] = plan->g2.tn;
+    record_tiles(plan);
     return HEFF_OK;
 }
 

@@ -128,6 +128,7 @@ struct GemmList {
     GemmTask* d_tasks = nullptr;
     KSeg* d_segs = nullptr;
     int tm = 0, tn = 0;
+    int cl = 1;             // CTAs per entry: 2 = tasks 2e, 2e + 1 share their B tile (cluster pair)
     double flops = 0;       // executed (valid m, n; padded K)
     double useful = 0;      // valid m, n and unpadded K
     // host only, one entry per task: output left sector a' and the task's flop counts
@@ -171,12 +172,13 @@ struct heff_plan {
     heff::MixTerm* d_terms = nullptr;
     heff::GemmList g1, g2;            // active task lists
     heff::GemmList g1_alt, g2_alt;    // the other tile width (tensor-core paths), see heff_plan_autotune
+    heff::GemmList g1_pair, g2_pair;  // N = 256 tiles in CTA pairs sharing B (tensor-core paths)
     int64_t stats[24] = {0};
     // tensor-map cache for the tensor-core path: two entries keyed by workspace pointer
     // (two streams alternating workspaces reuse their maps), replaced round-robin
     void* tmap_ws[2] = {nullptr, nullptr};
     int tmap_next = 0;
-    alignas(64) unsigned char tmaps[2][12][128];
+    alignas(64) unsigned char tmaps[2][13][128];
     int device = 0;
     int num_sms = 0;
     bool uploaded = false;    // false: created without a CUDA device (inspection only)
@@ -192,6 +194,8 @@ int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, 
 int launch_mix(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R,
                void* ws, void* stream);
 int launch_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream);
+// clusters of two tensor-core CTAs resident at once (tc_gemm.cu; num_sms / 2 without a device)
+int tc_pair_clusters(int num_sms, int precision);
 int plan_upload(heff_plan* p);
 void plan_free_device(heff_plan* p);
 void record_phase(heff_plan* p, int k, void* stream);

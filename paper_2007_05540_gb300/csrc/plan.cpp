@@ -16,6 +16,7 @@
 // with zero padding, so tiles never mix sectors.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
 #include <set>
 #include <stdexcept>
@@ -541,22 +542,83 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             P->stats[17] = (int64_t)c2;
         }
         for (heff::GemmList* G : {&P->g1, &P->g2, &P->g1_alt, &P->g2_alt}) keep_owned(*G, owned);
+        // ---- CTA pairs (tensor-core paths): N = 256 tiles with the same B rows, width and K
+        // segments go two to an entry, so that one read of each B box serves both CTAs of a
+        // cluster.  A tile left without a partner gets a ghost (no rows: it loads its half of
+        // B and computes nothing); tiles without segments (zero output blocks) pair among
+        // themselves or with an empty task.
+        auto make_pairs = [&](const heff::GemmList& G, heff::GemmList& Pr) {
+            Pr = heff::GemmList{};
+            Pr.tm = G.tm; Pr.tn = G.tn; Pr.cl = 2;
+            Pr.segs = G.segs;
+            Pr.flops = G.flops; Pr.useful = G.useful;
+            auto push = [&](const heff::GemmTask& k, int32_t owner, double f, double u) {
+                Pr.tasks.push_back(k); Pr.owner.push_back(owner);
+                Pr.task_flops.push_back(f); Pr.task_useful.push_back(u);
+            };
+            auto push_task = [&](size_t t) { push(G.tasks[t], G.owner[t], G.task_flops[t], G.task_useful[t]); };
+            std::map<std::vector<int64_t>, std::vector<size_t>> groups;
+            std::vector<size_t> zero;
+            for (size_t t = 0; t < G.tasks.size(); ++t) {
+                const heff::GemmTask& k = G.tasks[t];
+                if (k.seg_count == 0) { zero.push_back(t); continue; }
+                std::vector<int64_t> key = {k.b_row, k.n, k.ktotal};
+                for (int j = 0; j < k.seg_count; ++j) {
+                    key.push_back(G.segs[k.seg_begin + j].k0);
+                    key.push_back(G.segs[k.seg_begin + j].klen);
+                }
+                groups[key].push_back(t);
+            }
+            for (auto& kv : groups) {
+                const std::vector<size_t>& v = kv.second;
+                for (size_t i = 0; i < v.size(); i += 2) {
+                    push_task(v[i]);
+                    if (i + 1 < v.size()) {
+                        push_task(v[i + 1]);
+                    } else {
+                        heff::GemmTask gh = G.tasks[v[i]];
+                        gh.m = 0; gh.n_zero = 0; gh.c_off = 0;
+                        push(gh, -1, 0.0, 0.0);
+                    }
+                }
+            }
+            for (size_t i = 0; i < zero.size(); i += 2) {
+                push_task(zero[i]);
+                if (i + 1 < zero.size()) {
+                    push_task(zero[i + 1]);
+                } else {
+                    heff::GemmTask e{};
+                    e.ldc = 1;
+                    push(e, -1, 0.0, 0.0);
+                }
+            }
+        };
+        int ncl = nsm / 2;
+        if (tc) {
+            make_pairs(P->g1, P->g1_pair);
+            make_pairs(P->g2, P->g2_pair);
+            int ndev = 0;
+            if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) ncl = heff::tc_pair_clusters(nsm, opts->precision);
+            cudaGetLastError();
+        }
         // ---- static schedule of the persistent tensor-core kernels: CTA c of a grid of
         // min(nsm, tasks) runs tasks c, c + grid, c + 2 grid, ...  Assign the tasks by
         // longest-processing-time (each to the least loaded CTA, longest first; a tile's
         // time ~ (K blocks + a fixed overhead) x MMA width) and interleave the per-CTA lists
         // in that pattern, padding short lists with empty tasks (no rows, no segments).
+        // CTA pairs are scheduled the same way, an entry (two tasks) per cluster.
         if (tc && HEFF_LPT_SCHEDULE) {
-            for (heff::GemmList* G : {&P->g1, &P->g2, &P->g1_alt, &P->g2_alt}) {
-                const size_t nt = G->tasks.size();
+            for (heff::GemmList* G : {&P->g1, &P->g2, &P->g1_alt, &P->g2_alt, &P->g1_pair, &P->g2_pair}) {
+                const size_t CLn = (size_t)G->cl;
+                const size_t nt = G->tasks.size() / CLn;          // entries
                 if (nt == 0) continue;
-                const int grid = (int)std::min<size_t>((size_t)nsm, nt);
-                std::vector<double> work(nt);
-                for (size_t t = 0; t < nt; ++t) {
-                    int64_t k = 0;
-                    for (int s2 = 0; s2 < G->tasks[t].seg_count; ++s2) k += G->segs[G->tasks[t].seg_begin + s2].klen;
-                    work[t] = (double)(k / KPAD + 4) * ((G->tasks[t].n + 15) / 16 * 16);
-                }
+                const int grid = (int)std::min<size_t>((size_t)(CLn == 2 ? ncl : nsm), nt);
+                std::vector<double> work(nt, 0.0);
+                for (size_t t = 0; t < nt; ++t)
+                    for (size_t r = 0; r < CLn; ++r) {
+                        const heff::GemmTask& k = G->tasks[t * CLn + r];
+                        work[t] = std::max(work[t], (double)(k.ktotal / KPAD + 4) * ((k.n + 15) / 16 * 16));
+                    }
                 std::vector<size_t> ord(nt);
                 for (size_t t = 0; t < nt; ++t) ord[t] = t;
                 std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
@@ -572,22 +634,23 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                 for (auto& v : per) depth = std::max(depth, v.size());
                 heff::GemmList s2;
                 for (size_t j = 0; j < depth; ++j)
-                    for (int c = 0; c < grid; ++c) {
-                        if (j < per[c].size()) {
-                            const size_t t = per[c][j];
-                            s2.tasks.push_back(G->tasks[t]);
-                            s2.owner.push_back(G->owner[t]);
-                            s2.task_flops.push_back(G->task_flops[t]);
-                            s2.task_useful.push_back(G->task_useful[t]);
-                        } else {
-                            heff::GemmTask e{};
-                            e.ldc = 1;
-                            s2.tasks.push_back(e);
-                            s2.owner.push_back(-1);
-                            s2.task_flops.push_back(0.0);
-                            s2.task_useful.push_back(0.0);
+                    for (int c = 0; c < grid; ++c)
+                        for (size_t r = 0; r < CLn; ++r) {
+                            if (j < per[c].size()) {
+                                const size_t t = per[c][j] * CLn + r;
+                                s2.tasks.push_back(G->tasks[t]);
+                                s2.owner.push_back(G->owner[t]);
+                                s2.task_flops.push_back(G->task_flops[t]);
+                                s2.task_useful.push_back(G->task_useful[t]);
+                            } else {
+                                heff::GemmTask e{};
+                                e.ldc = 1;
+                                s2.tasks.push_back(e);
+                                s2.owner.push_back(-1);
+                                s2.task_flops.push_back(0.0);
+                                s2.task_useful.push_back(0.0);
+                            }
                         }
-                    }
                 G->tasks.swap(s2.tasks);
                 G->owner.swap(s2.owner);
                 G->task_flops.swap(s2.task_flops);

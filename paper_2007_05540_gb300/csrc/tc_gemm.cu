@@ -38,31 +38,43 @@
 namespace heff {
 namespace {
 
-constexpr int TC_THREADS = 192;
+// Warps: 0 TMA producer, 1 MMA issuer, then the epilogue: 8 warps for BF16X3 (two per
+// tensor-memory lane quarter, alternating 32-column chunks), 4 for TF32X3 (whose 32 x 32
+// fp32 store boxes need twice the shared memory per warp).
+#ifndef HEFF_EPI_WARPS_BF16
+#define HEFF_EPI_WARPS_BF16 8
+#endif
+template <int PREC> __host__ __device__ constexpr int tc_epi_warps() {
+    return PREC == HEFF_PREC_BF16X3 ? HEFF_EPI_WARPS_BF16 : 4;
+}
+template <int PREC> __host__ __device__ constexpr int tc_threads() { return 64 + 32 * tc_epi_warps<PREC>(); }
 constexpr int TM = 128;
 constexpr long long WAIT_CYCLES = 3ll << 30;   // ~1.5 s at 2 GHz
 
 // Shared-memory ring: STAGES x {A_hi, A_lo (128 rows), B_hi, B_lo (TN rows)}, each row SWZ
 // bytes of one K block (SWZ = 64: 32 bf16 / 16 fp32; SWZ = 128: 64 bf16 / 32 fp32), then
-// 8 KB per epilogue warp (TMA store boxes, or the 32 x 33 float transpose), then barriers.
+// 32 KB shared by the epilogue warps (per warp: one hi + lo pair of TMA store boxes, or the
+// 32 x 32 float transpose), then barriers.
 template <int TN, int STAGES, int SWZ>
 struct Smem {
     static constexpr int A_BYTES = TM * SWZ;
     static constexpr int B_BYTES = TN * SWZ;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int EPI_OFF = STAGES * STAGE_BYTES;  // 1024-byte aligned
-    static constexpr int EPI_WARP = 8192;
-    static constexpr int BAR_OFF = EPI_OFF + 4 * EPI_WARP;
+    static constexpr int EPI_BYTES = 32768;
+    static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
     static constexpr int TOTAL = BAR_OFF + 256 + 1024;    // + barriers, alignment slack
 };
-static_assert(32 * 33 * 4 <= 8192, "transpose buffer fits the epilogue slot");
+static_assert(32 * 32 * 4 <= 32768 / 8, "transpose buffer fits an epilogue slot");
 
 // TMA maps of one GEMM: the A operand with 64- and 128-row boxes, the B operand with 64-,
-// 128- and 256-row boxes (a tile loads the smallest box that covers its valid rows).
+// 128- and 256-row boxes (a tile loads the smallest box that covers its valid rows; each CTA
+// of a pair loads the smallest of 32, 64 or 128 rows that covers its half).
 struct TcMaps {
     CUtensorMap a[2];
     CUtensorMap b[3];
     CUtensorMap c;      // T store map: 32 x 32 boxes (GEMM 1 only)
+    CUtensorMap bq;     // B operand, 32-row box (a CTA pair's half of a narrow B tile)
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -156,6 +168,61 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// CTA-pair forms (cta_group::2): the MMA of a pair is issued by the even CTA and reads A
+// and its half of B from each CTA's shared memory at the same offsets; its commit arrives
+// on the barrier at this offset in both CTAs.
+template <int PREC>
+__device__ __forceinline__ void umma2(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (PREC == HEFF_PREC_BF16X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+    }
+}
+__device__ __forceinline__ void umma2_commit_both(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+        ::"r"(su32(bar)), "h"((uint16_t)3) : "memory");
+}
+
+// TMA load into this CTA's shared memory, completion signalled on a barrier of either CTA of
+// the pair (`bar` is a shared::cluster address).
+__device__ __forceinline__ void tma_load_pair(void* dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared::cluster address of this CTA's variable `p` in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of every CTA of the cluster (shared-memory writes before it are visible after).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Bulk tensor store of one shared-memory box; completion tracked by bulk async-groups.
 __device__ __forceinline__ void tma_store(const CUtensorMap* map, uint32_t src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
@@ -207,10 +274,18 @@ struct TcArgs {
     int* err;                             // sticky error flag in the workspace
 };
 
-template <int PREC, int TN, int STAGES, int SWZ>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// CL = 1: every CTA runs its own 128-row tiles.  CL = 2: the two CTAs of a cluster run the
+// two tiles of one entry (tasks 2e, 2e + 1: the same B rows and K segments) as one M = 256
+// tile with pair MMAs (tcgen05 cta_group::2): each CTA loads its own 128 A rows and half of
+// the B rows into its ring, the even CTA waits for both halves on its barrier and issues the
+// MMAs, whose commits release both rings and hand each CTA the accumulator of its own rows
+// in its own tensor memory.  Per CTA this halves the B operand in shared memory (ring
+// stages of 32 KB instead of 48 KB) and the shared-memory bytes the tensor core reads per
+// MMA.  A pair's second task may be a ghost (m = 0: computed, not stored).
+template <int PREC, int TN, int STAGES, int SWZ, int CL>
+__global__ void __launch_bounds__(tc_threads<PREC>(), 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
-    using S = Smem<TN, STAGES, SWZ>;
+    using S = Smem<TN / CL, STAGES, SWZ>;      // B rows per CTA: TN, or TN / 2 in a pair
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
@@ -223,22 +298,37 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], 4); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], tc_epi_warps<PREC>() * CL); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(2 * TN) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (CL == 1) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(su32(tmem_slot)), "r"(2 * TN) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        } else {                               // one warp of each CTA of the pair, collectively
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(su32(tmem_slot)), "r"(2 * TN) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (CL > 1) cluster_sync();  // the peer's barriers exist before anything reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const long total = (long)g.ntasks * g.nbatch;
+    const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
+    const long cid = (long)(blockIdx.x / CL), ncl = (long)(gridDim.x / CL);
+    const long nent = g.ntasks / CL;                                 // entries per batch
+    const long total = nent * g.nbatch;
     constexpr int KB = SWZ / (PREC == HEFF_PREC_BF16X3 ? 2 : 4);   // elements per K block
     constexpr int KSUB = SWZ / 32;                                   // MMAs (32-byte K) per block
+
+    // the even CTA's full barriers (pair: both CTAs' loads complete there) and its tempty
+    // barriers (pair: both CTAs' epilogues release the accumulators there)
+    const uint32_t full_pair = CL > 1 ? cluster_addr(full, 0) : 0u;
+    const uint32_t tempty_pair = CL > 1 ? cluster_addr(tempty, 0) : 0u;
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
@@ -246,17 +336,22 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         bool ok = true;
         // the next task and the next segment are loaded one step ahead, so their latency
         // overlaps with the current loads instead of draining the ring
-        GemmTask tn = blockIdx.x < total ? g.tasks[blockIdx.x % g.ntasks] : GemmTask{};
-        for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x) {
+        GemmTask tn = cid < total ? g.tasks[CL * (cid % nent) + rank] : GemmTask{};
+        for (long gi = cid; gi < total && ok; gi += ncl) {
             const GemmTask t = tn;
-            if (gi + gridDim.x < total) tn = g.tasks[(gi + gridDim.x) % g.ntasks];
-            const int b = g.b0 + (int)(gi / g.ntasks);
+            if (gi + ncl < total) tn = g.tasks[CL * ((gi + ncl) % nent) + rank];
+            const int b = g.b0 + (int)(gi / nent);
             const int ah = (int)(t.a_row + b * g.a_batch_rows), al = (int)(ah + g.a_plane_rows);
             const int bh = (int)(t.b_row + b * g.b_batch_rows), bl = (int)(bh + g.b_plane_rows);
             const int ia = t.m <= 64 ? 0 : 1, ib = t.n <= 64 ? 0 : (t.n <= 128 ? 1 : 2);
-            const CUtensorMap* ma = &maps.a[ia];
+            const CUtensorMap* ma = &maps.a[CL == 1 ? ia : 1];   // a pair always loads 128 A rows
             const CUtensorMap* mb = &maps.b[ib];
-            const uint32_t bytes = 2u * (uint32_t)((64 << ia) + (64 << ib)) * SWZ;
+            // pair: this CTA's half of the MMA's N columns, and the smallest box covering it
+            const int half = (t.n <= 16 ? 16 : (t.n + 15) & ~15) / 2;
+            const int hb = half <= 32 ? 0 : (half <= 64 ? 1 : 2);
+            const CUtensorMap* mh = hb == 0 ? &maps.bq : &maps.b[hb - 1];
+            const uint32_t bytes = CL == 1 ? 2u * (uint32_t)((64 << ia) + (64 << ib)) * SWZ
+                                           : (uint32_t)CL * 2u * (uint32_t)(128 + (32 << hb)) * SWZ;
             KSeg sn = t.seg_count > 0 ? g.segs[t.seg_begin] : KSeg{};
             for (int s = 0; s < t.seg_count && ok; ++s) {
                 const KSeg sg = sn;
@@ -264,17 +359,35 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                 for (int k = sg.k0; k < sg.k0 + sg.klen; k += KB) {
                     if (!(ok = mbar_wait(&empty[st], ph ^ 1, abort_flag, g.err))) break;
                     uint8_t* base = smem + st * S::STAGE_BYTES;
-                    mbar_expect_tx(&full[st], bytes);
-                    tma_load(base, ma, &full[st], k, ah);
-                    tma_load(base + S::A_BYTES, ma, &full[st], k, al);
-                    tma_load(base + 2 * S::A_BYTES, mb, &full[st], k, bh);
-                    tma_load(base + 2 * S::A_BYTES + S::B_BYTES, mb, &full[st], k, bl);
+                    if constexpr (CL == 1) {
+                        mbar_expect_tx(&full[st], bytes);
+                        tma_load(base, ma, &full[st], k, ah);
+                        tma_load(base + S::A_BYTES, ma, &full[st], k, al);
+                        tma_load(base + 2 * S::A_BYTES, mb, &full[st], k, bh);
+                        tma_load(base + 2 * S::A_BYTES + S::B_BYTES, mb, &full[st], k, bl);
+                    } else {
+                        // both CTAs' loads complete on the even CTA's barrier, which expects them all
+                        const uint32_t fb = full_pair + (uint32_t)(st * sizeof(uint64_t));
+                        if (rank == 0) mbar_expect_tx(&full[st], bytes);
+                        tma_load_pair(base, ma, fb, k, ah);
+                        tma_load_pair(base + S::A_BYTES, ma, fb, k, al);
+                        tma_load_pair(base + 2 * S::A_BYTES, mh, fb, k, bh + (int)rank * half);
+                        tma_load_pair(base + 2 * S::A_BYTES + S::B_BYTES, mh, fb, k, bl + (int)rank * half);
+                    }
                     if (++st == STAGES) { st = 0; ph ^= 1; }
                 }
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------ MMA issuer
+        if constexpr (CL > 1) {
+            // every stage released by the pair's last MMAs: no commit from the even CTA is
+            // still on its way to this CTA when it leaves
+            for (int s = 0; s < STAGES && ok; ++s) {
+                ok = mbar_wait(&empty[st], ph ^ 1, abort_flag, g.err);
+                if (++st == STAGES) { st = 0; ph ^= 1; }
+            }
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ------------------------------------------------ MMA issuer (the even CTA of a pair)
         constexpr uint32_t FMT = PREC == HEFF_PREC_BF16X3 ? 1u : 2u;
         // This thread feeds the tensor pipe: per K block it only waits, adds constant offsets
         // to precomputed descriptors and issues (no divisions, no descriptor packing).
@@ -285,20 +398,21 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         constexpr uint64_t O_ALO = S::A_BYTES >> 4, O_BHI = (2 * S::A_BYTES) >> 4;
         constexpr uint64_t O_BLO = (2 * S::A_BYTES + S::B_BYTES) >> 4, O_STAGE = S::STAGE_BYTES >> 4;
         bool ok = true;
-        GemmTask tn = blockIdx.x < total ? g.tasks[blockIdx.x % g.ntasks] : GemmTask{};
-        for (long gi = blockIdx.x; gi < total && ok; gi += gridDim.x) {
+        GemmTask tn = cid < total ? g.tasks[CL * (cid % nent) + rank] : GemmTask{};
+        for (long gi = cid; gi < total && ok; gi += ncl) {
             const GemmTask t = tn;
-            if (gi + gridDim.x < total) tn = g.tasks[(gi + gridDim.x) % g.ntasks];
+            if (gi + ncl < total) tn = g.tasks[CL * ((gi + ncl) % nent) + rank];
             if (t.seg_count == 0) {            // nothing to contract: the epilogue writes zeros
                 const uint32_t acc = ccount & 1, use = ccount >> 1;
                 if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
-                mbar_arrive(&tfull[acc]);
+                if constexpr (CL == 1) mbar_arrive(&tfull[acc]);
+                else umma2_commit_both(&tfull[acc]);
                 ++ccount;
                 continue;
             }
             const int nkb = t.ktotal / KB;
             const uint32_t nmma = t.n <= 16 ? 16u : (uint32_t)((t.n + 15) & ~15);
-            const uint32_t id = idesc(FMT, TM, nmma);
+            const uint32_t id = idesc(FMT, TM * CL, nmma);
             uint32_t first = 1, acc = 0, d = 0;
             int left = 0;                      // K blocks left in the current chunk
             // the ring holds the tile's K blocks in order: only their number matters here
@@ -319,15 +433,23 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
 #pragma unroll
                 for (int kk = 0; kk < KSUB; ++kk) {
                     const uint64_t o = (uint64_t)(kk * 32) >> 4;     // 32-byte step inside the row
-                    umma<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
-                    umma<PREC>(d, ahi + o, blo + o, id, 1u);
-                    umma<PREC>(d, alo + o, bhi + o, id, 1u);
+                    if constexpr (CL == 1) {
+                        umma<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
+                        umma<PREC>(d, ahi + o, blo + o, id, 1u);
+                        umma<PREC>(d, alo + o, bhi + o, id, 1u);
+                    } else {
+                        umma2<PREC>(d, ahi + o, bhi + o, id, first ? 0u : 1u);
+                        umma2<PREC>(d, ahi + o, blo + o, id, 1u);
+                        umma2<PREC>(d, alo + o, bhi + o, id, 1u);
+                    }
                     first = 0;
                 }
-                umma_commit(&empty[st]);
+                if constexpr (CL == 1) umma_commit(&empty[st]);
+                else umma2_commit_both(&empty[st]);
                 if (++st == STAGES) { st = 0; ph ^= 1; }
                 if (--left == 0) {
-                    umma_commit(&tfull[acc]);
+                    if constexpr (CL == 1) umma_commit(&tfull[acc]);
+                    else umma2_commit_both(&tfull[acc]);
                     ++ccount;
                 }
             }
@@ -335,23 +457,28 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
         // Each warp drains its 32 TMEM lanes (tile rows) 32 columns at a time (tcgen05.ld:
-        // thread = row).  T, full quarters: hi/lo split in registers, swizzled box in shared
-        // memory, two bulk tensor stores (hi plane, lo plane), double buffered for BF16X3.
-        // Otherwise: transpose through a padded 32 x 33 buffer and store row by row with
-        // consecutive lanes on consecutive columns.
+        // thread = row); the warps of a lane quarter take alternate 32-column chunks.  T, full
+        // quarters: hi/lo split in registers, swizzled box in shared memory, two bulk tensor
+        // stores (hi plane, lo plane).  Otherwise: transpose through a 32 x 32 buffer (XOR
+        // swizzled: conflict-free both ways) and store row by row with consecutive lanes on
+        // consecutive columns.
         using E = typename std::conditional<PREC == HEFF_PREC_BF16X3, __nv_bfloat16, float>::type;
+        constexpr int NEPI = tc_epi_warps<PREC>();
+        constexpr int NH = NEPI / 4;                                // warps per lane quarter
+        constexpr int SLOT = S::EPI_BYTES / NEPI;
         constexpr int BOX = 32 * 32 * (int)sizeof(E);              // one plane of a 32 x 32 box
-        constexpr int NBUF = PREC == HEFF_PREC_BF16X3 ? 2 : 1;      // boxes in the 8 KB slot
+        static_assert(2 * BOX <= SLOT, "a hi + lo pair of store boxes fits an epilogue slot");
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        uint8_t* slot = smem + S::EPI_OFF + q * S::EPI_WARP;
-        float (*stage)[33] = reinterpret_cast<float (*)[33]>(slot);
+        const int h = (warp - 2) >> 2;          // its chunk phase within the quarter
+        uint8_t* slot = smem + S::EPI_OFF + (warp - 2) * SLOT;
+        float* stage = reinterpret_cast<float*>(slot);
         const uint32_t slot_s = su32(slot);
         const int CH = g.kchunk > 0 ? g.kchunk : 0x7fffffff;
-        uint32_t ccount = 0, nstore = 0;
+        uint32_t ccount = 0;
         bool live = true;
-        for (long gi = blockIdx.x; gi < total && live; gi += gridDim.x) {
-            const GemmTask t = g.tasks[gi % g.ntasks];
-            const int brel = (int)(gi / g.ntasks), b = g.b0 + brel;
+        for (long gi = cid; gi < total && live; gi += ncl) {
+            const GemmTask t = g.tasks[CL * (gi % nent) + rank];
+            const int brel = (int)(gi / nent), b = g.b0 + brel;
             const int nch = (t.seg_count > 0 && CH != 0x7fffffff) ? (t.ktotal / KB + CH - 1) / CH : 1;
           for (int ch = 0; ch < nch; ++ch) {
             const uint32_t acc = ccount & 1, use = ccount >> 1;
@@ -365,7 +492,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                 x0 = (int)(t.c_off % t.ldc);
                 yh = (int)(t.c_off / t.ldc) + q * 32 + b * g.c_batch_rows;
             }
-            for (int c0 = 0; c0 < ncols; c0 += 32) {
+            for (int c0 = 32 * h; c0 < ncols; c0 += 32 * NH) {
                 uint32_t raw[32];
                 if (t.seg_count > 0) {
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * TN + c0, raw);
@@ -375,10 +502,10 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                 }
                 if (rows <= 0) continue;                       // warp-uniform
                 if (boxed) {
-                    // this buffer's previous bulk store must have finished reading it
-                    if (lane == 0) bulk_wait_read<NBUF - 1>();
+                    // the slot's previous bulk stores must have finished reading it
+                    if (lane == 0) bulk_wait_read<0>();
                     __syncwarp();
-                    const uint32_t hb = slot_s + (nstore % NBUF) * 2 * BOX, lb = hb + BOX;
+                    const uint32_t hb = slot_s, lb = hb + BOX;
                     const int nv = t.n - c0;                   // valid columns in this chunk
                     if constexpr (PREC == HEFF_PREC_BF16X3) {
                         // row = lane: 64 bytes per plane, 16-byte chunk j at j ^ ((row >> 1) & 3)
@@ -425,14 +552,13 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                         tma_store(&maps.c, lb, x0 + c0, yh + g.c_plane_rows);
                         bulk_commit();
                     }
-                    ++nstore;
                     continue;
                 }
                 // the transpose buffer overlaps the store boxes: no store may still read them
                 if (lane == 0) bulk_wait_read<0>();
                 __syncwarp();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) stage[lane][i] = __uint_as_float(raw[i]);
+                for (int i = 0; i < 32; ++i) stage[lane * 32 + (i ^ lane)] = __uint_as_float(raw[i]);
                 __syncwarp();
                 const int c = c0 + lane;                       // this lane's column
                 if (g.mode == 0) {
@@ -440,7 +566,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     E* lo = hi + g.c_plane_elems;
                     if (c < ncols) {
                         for (int rr = 0; rr < rows; ++rr) {
-                            const float f = c < t.n ? stage[rr][lane] : 0.f;
+                            const float f = c < t.n ? stage[rr * 32 + (lane ^ rr)] : 0.f;
                             const int64_t o = (int64_t)(q * 32 + rr) * t.ldc;
                             if constexpr (PREC == HEFF_PREC_BF16X3) {
                                 const __nv_bfloat16 h = __float2bfloat16_rn(f);
@@ -468,7 +594,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
 #pragma unroll
                             for (int u = 0; u < 8; ++u)
                                 if (r0 + u < rows)
-                                    y[(int64_t)(q * 32 + r0 + u) * t.ldc] = old[u] + (double)stage[r0 + u][lane];
+                                    y[(int64_t)(q * 32 + r0 + u) * t.ldc] =
+                                        old[u] + (double)stage[(r0 + u) * 32 + (lane ^ (r0 + u))];
                         }
                     } else {
                         float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o0;
@@ -480,7 +607,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
 #pragma unroll
                             for (int u = 0; u < 8; ++u)
                                 if (r0 + u < rows)
-                                    y[(int64_t)(q * 32 + r0 + u) * t.ldc] = old[u] + stage[r0 + u][lane];
+                                    y[(int64_t)(q * 32 + r0 + u) * t.ldc] =
+                                        old[u] + stage[(r0 + u) * 32 + (lane ^ (r0 + u))];
                         }
                     }
                 }
@@ -488,7 +616,10 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
+            if (lane == 0) {
+                if constexpr (CL == 1) mbar_arrive(&tempty[acc]);
+                else mbar_arrive_cluster(tempty_pair + (uint32_t)(acc * sizeof(uint64_t)));
+            }
             ++ccount;
           }
         }
@@ -497,9 +628,14 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     }
     tc_fence_before();
     __syncthreads();
+    // pair: both CTAs are done with the MMAs, their tensor memory and each other's barriers
+    if constexpr (CL > 1) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
+        if constexpr (CL == 1)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
     }
 }
 
@@ -554,17 +690,49 @@ static_assert(SWZ_TC / (int)sizeof(__nv_bfloat16) <= KPAD, "a K block must not s
 constexpr int KCHUNK_BF16 = HEFF_KCHUNK_BF16;
 constexpr int KCHUNK_TF32 = HEFF_KCHUNK_TF32;
 
-template <int PREC, int TN_TC>
-int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
-    constexpr int STAGES_TC = (192 * 1024) / (2 * (128 + TN_TC) * SWZ_TC);   // a 192 KB ring
-    using S = Smem<TN_TC, STAGES_TC, SWZ_TC>;
-    auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES_TC, SWZ_TC>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL);
-        if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        attr = true;
+template <int PREC, int TN_TC, int CL>
+struct TcKernel {
+    // a 192 KB ring; a CTA of a pair holds half of the B rows (TN_TC / CL)
+    static constexpr int STAGES = (192 * 1024) / (2 * (128 + TN_TC / CL) * SWZ_TC);
+    using S = Smem<TN_TC / CL, STAGES, SWZ_TC>;
+    static constexpr auto kern = tc_gemm_kernel<PREC, TN_TC, STAGES, SWZ_TC, CL>;
+
+    // shared-memory opt-in (once) and, for pairs, the clusters that fit on the device at once
+    static int setup(int num_sms, int* clusters) {
+        static bool done = false;
+        static int ncl = 0;
+        if (!done) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL);
+            if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            ncl = num_sms / CL;
+            if (CL > 1) {
+                cudaLaunchConfig_t cfg{};
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)(ncl * CL));
+                cfg.blockDim = dim3(tc_threads<PREC>());
+                cfg.dynamicSmemBytes = S::TOTAL;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                int n = 0;
+                if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < ncl) ncl = n;
+                cudaGetLastError();
+            }
+            done = true;
+        }
+        if (clusters) *clusters = ncl;
+        return HEFF_OK;
     }
+};
+
+template <int PREC, int TN_TC, int CL>
+int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, cudaStream_t st) {
+    using K = TcKernel<PREC, TN_TC, CL>;
+    using S = typename K::S;
+    const int nsm = p->num_sms > 0 ? p->num_sms : 148;
+    int max_cl = 0;
+    if (int rc = K::setup(nsm, &max_cl)) return rc;
     char* w = static_cast<char*>(ws);
     const int64_t B = p->opts.max_batch;
     int slot = p->tmap_ws[0] == ws ? 0 : (p->tmap_ws[1] == ws ? 1 : -1);
@@ -591,6 +759,13 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
         int rc = make_map(&m[10], w + p->off_t, PREC, (uint64_t)(2 * B * p->rows_t), (uint64_t)p->ld_t, 32u,
                           PREC == HEFF_PREC_BF16X3 ? 64 : 128);
         if (rc) return rc;
+        // [11] XT, [12] RW with 32-row boxes (halves of a 64-row B box for CTA pairs)
+        if ((rc = make_map(&m[11], w + p->off_xt, PREC, (uint64_t)(2 * B * p->rows_x), (uint64_t)p->ld_x, 32u,
+                           SWZ_TC)))
+            return rc;
+        if ((rc = make_map(&m[12], w + p->off_rw, PREC, (uint64_t)(2 * p->rows_rw), (uint64_t)p->ld_t, 32u,
+                           SWZ_TC)))
+            return rc;
         p->tmap_ws[slot] = ws;
     }
     const GemmList& gl = which == 1 ? p->g1 : p->g2;
@@ -600,6 +775,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
     maps.a[0] = m[sa]; maps.a[1] = m[sa + 1];
     maps.b[0] = m[sb]; maps.b[1] = m[sb + 1]; maps.b[2] = m[sb + 2];
     maps.c = m[10];
+    maps.bq = m[which == 1 ? 11 : 12];
     for (int b0 = 0; b0 < nbatch; b0 += MAXB) {
         const int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
         TcArgs g{};
@@ -626,10 +802,25 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
             g.kchunk = (PREC == HEFF_PREC_TF32X3 ? KCHUNK_TF32 : KCHUNK_BF16) * 64 / SWZ_TC;
             g.y_f64 = p->opts.io_dtype == HEFF_DTYPE_F64;
         }
-        const long total = (long)g.ntasks * nb;
-        int grid = p->num_sms > 0 ? p->num_sms : 148;
-        if (total < grid) grid = (int)total;
-        kern<<<grid, TC_THREADS, S::TOTAL, st>>>(maps, g);
+        const long total = (long)(g.ntasks / CL) * nb;        // entries (tiles, or pairs of tiles)
+        long units = max_cl;                                   // CTAs, or clusters of CL CTAs
+        if (total < units) units = total;
+        if (CL == 1) {
+            K::kern<<<(unsigned)units, tc_threads<PREC>(), S::TOTAL, st>>>(maps, g);
+        } else {
+            cudaLaunchConfig_t cfg{};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(units * CL));
+            cfg.blockDim = dim3(tc_threads<PREC>());
+            cfg.dynamicSmemBytes = S::TOTAL;
+            cfg.stream = st;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, K::kern, maps, g);
+            if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "tc_gemm cluster launch: %s", cudaGetErrorString(e));
+        }
         count_launches(1);
     }
     cudaError_t e = cudaGetLastError();
@@ -641,12 +832,22 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
 
 int launch_tc_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool wide = (which == 1 ? p->g1.tn : p->g2.tn) == 256;
+    const GemmList& gl = which == 1 ? p->g1 : p->g2;
+    const bool wide = gl.tn == 256, pair = gl.cl == 2;
     if (p->opts.precision == HEFF_PREC_BF16X3)
-        return wide ? launch_tc_t<HEFF_PREC_BF16X3, 256>(p, which, ws, y, nbatch, st)
-                    : launch_tc_t<HEFF_PREC_BF16X3, 128>(p, which, ws, y, nbatch, st);
-    return wide ? launch_tc_t<HEFF_PREC_TF32X3, 256>(p, which, ws, y, nbatch, st)
-                : launch_tc_t<HEFF_PREC_TF32X3, 128>(p, which, ws, y, nbatch, st);
+        return pair ? launch_tc_t<HEFF_PREC_BF16X3, 256, 2>(p, which, ws, y, nbatch, st)
+                    : wide ? launch_tc_t<HEFF_PREC_BF16X3, 256, 1>(p, which, ws, y, nbatch, st)
+                           : launch_tc_t<HEFF_PREC_BF16X3, 128, 1>(p, which, ws, y, nbatch, st);
+    return pair ? launch_tc_t<HEFF_PREC_TF32X3, 256, 2>(p, which, ws, y, nbatch, st)
+                : wide ? launch_tc_t<HEFF_PREC_TF32X3, 256, 1>(p, which, ws, y, nbatch, st)
+                       : launch_tc_t<HEFF_PREC_TF32X3, 128, 1>(p, which, ws, y, nbatch, st);
+}
+
+int tc_pair_clusters(int num_sms, int precision) {
+    int n = num_sms / 2;
+    if (precision == HEFF_PREC_BF16X3) TcKernel<HEFF_PREC_BF16X3, 256, 2>::setup(num_sms, &n);
+    else if (precision == HEFF_PREC_TF32X3) TcKernel<HEFF_PREC_TF32X3, 256, 2>::setup(num_sms, &n);
+    return n;
 }
 
 }  // namespace heff

@@ -453,12 +453,15 @@ def heff_apply_noalloc(plan, L, W1, W2, R, x, y, stream=None):
                                    _stream(stream)), "heff_apply_noalloc")
 
 
+TILE_256, TILE_128, TILE_PAIR_256, TILE_VARIANTS = 256, 128, 512, 3
+
+
 def heff_plan_autotune(plan, L, W1, W2, R, x, y, ws, stream=None, times=None):
-    """Pick the faster N tile (256 or 128) per GEMM on these inputs; returns (tn1, tn2).
-    If `times` is a list, the median times {GEMM 1 at 256, 128, GEMM 2 at 256, 128} (ms)
-    are appended to it."""
+    """Pick the fastest tile variant (TILE_256, TILE_128, TILE_PAIR_256) per GEMM on these
+    inputs; returns (variant of GEMM 1, variant of GEMM 2).  If `times` is a list, the
+    median times {GEMM 1: 256, 128, pairs; GEMM 2: 256, 128, pairs} (ms) are appended."""
     tn = (_i32 * 2)()
-    ms = (C.c_float * 4)()
+    ms = (C.c_float * (2 * TILE_VARIANTS))()
     _check(_lib.heff_plan_autotune(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y), _ptr(ws),
                                    _nbytes(ws), _stream(stream), tn, ms), "heff_plan_autotune")
     if times is not None:

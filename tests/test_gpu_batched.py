@@ -1,7 +1,8 @@
 """Batched applies (many x sharing L, W1, W2, R), the tile autotuner and CUDA-graph capture.
 
-* heff_plan_autotune picks a tile width per GEMM; the results are bitwise unchanged (a
-  tile's K accumulation order does not depend on the N tiling);
+* heff_plan_autotune picks a tile variant per GEMM, and every variant gives bitwise the
+  same results (a tile's K accumulation order does not depend on the N tiling or on CTA
+  pairing);
 * heff_apply_batched captured once in a CUDA graph and replayed gives bitwise the
   results of the uncaptured call, and each batch entry matches the oracle;
 * the same at the electron workload's full size with 32 vectors (sampled sectors).
@@ -44,10 +45,31 @@ def test_autotune_keeps_results_bitwise():
     before = _batched(plan, d, xs, ws)[0].cpu().numpy()
     y = torch.empty_like(xs[0])
     tn = heff.heff_plan_autotune(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs[0], y, ws)
-    assert all(t in (128, 256) for t in tn)
+    assert all(t in (heff.TILE_128, heff.TILE_256, heff.TILE_PAIR_256) for t in tn)
     after = _batched(plan, d, xs, ws)[0].cpu().numpy()
     print("autotuned tile widths", tn)
     assert np.array_equal(before, after)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("name", ["spin_m200", "electron_m256", "spin_j1j2_6x6_m200", "spin_m1024"])
+def test_tile_variants_bitwise_equal(name, prec):
+    """Every tile variant (N = 256, N = 128, N = 256 in CTA pairs sharing B through TMA
+    multicast) gives bitwise the same y for a batch of 3 (a tile's K order is the same in all
+    of them), and batch entry 0 matches the oracle."""
+    w, lays, plan, d, xs = _setup(name, 3, prec)
+    ws = plan.workspace()
+    out = {}
+    for code in (heff.TILE_256, heff.TILE_128, heff.TILE_PAIR_256):
+        heff.heff_plan_select_tiles(plan.handle, code, code)
+        out[code] = [t.cpu().numpy() for t in _batched(plan, d, xs, ws)]
+    for code in (heff.TILE_128, heff.TILE_PAIR_256):
+        for b in range(3):
+            assert np.array_equal(out[code][b], out[heff.TILE_256][b]), (code, b)
+    L, W1, W2, R, x = oh.problem_from_workload(w, 0)
+    y_ref = oracle_flat(lays[4], oh.heff_apply(L, W1, W2, R, x))
+    y = out[heff.TILE_PAIR_256][0].astype(np.float64)
+    assert np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref) < (1e-3 if prec == "bf16x3" else 1e-5)
 
 
 def test_batched_graph_capture_matches_eager_and_oracle():

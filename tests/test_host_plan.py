@@ -188,25 +188,54 @@ def test_row_shard_arguments_checked():
 
 
 def test_select_tiles_swaps_task_lists():
-    """Both tile widths are planned; selecting one swaps its task list in (the schedule
-    still reproduces the oracle), unknown widths and FP64 plans are refused."""
+    """All tile variants are planned; selecting one swaps its task list in (the schedule
+    still reproduces the oracle), unknown variants and FP64 plans are refused."""
     w = wl.workload_by_name("spin_m64")
     lays, bufs = library_problem(w)
     P = _plan(w, lays, bufs, "bf16x3", "f32")
     assert (P.stats[15], P.stats[22]) == (256, 256)
-    heff.heff_plan_select_tiles(P.handle, 128, 128)
-    st = heff.heff_plan_stats(P.handle)
-    assert (st[15], st[22]) == (128, 128)
-    P.stats = st
     L, W1, W2, R, x = oh.problem_from_workload(w)
     y_ref = oracle_flat(lays[4], oh.heff_apply(L, W1, W2, R, x))
-    y = interpret_plan(P, bufs, bufs["x"][0])
-    assert np.abs(y - y_ref).max() < 1e-12 * np.abs(y_ref).max()
+    for code in (heff.TILE_128, heff.TILE_PAIR_256, heff.TILE_256):
+        heff.heff_plan_select_tiles(P.handle, code, code)
+        st = heff.heff_plan_stats(P.handle)
+        assert (st[15], st[22]) == (code, code)
+        P.stats = st
+        y = interpret_plan(P, bufs, bufs["x"][0])
+        assert np.abs(y - y_ref).max() < 1e-12 * np.abs(y_ref).max()
     with pytest.raises(heff.HeffError):
         heff.heff_plan_select_tiles(P.handle, 64, 0)
     P64 = _plan(w, lays, bufs, "fp64", "f64")
     with pytest.raises(heff.HeffError):
         heff.heff_plan_select_tiles(P64.handle, 128, 0)
+
+
+@pytest.mark.parametrize("name", ["spin_m200", "electron_m96", "spin_m1024_s8"])
+def test_pair_entries_share_b_rows_and_segments(name):
+    """CTA-pair lists: tasks 2e and 2e + 1 load the same B rows with the same K segments (one
+    B box serves both); a ghost partner has no rows; every real tile of the single-CTA list
+    appears exactly once."""
+    w = wl.spin_heff_workload(1024, 8, 21, name=name) if name == "spin_m1024_s8" else wl.workload_by_name(name)
+    lays, bufs = library_problem(w)
+    P = _plan(w, lays, bufs, "bf16x3", "f32")
+    for which in (3, 5):
+        single = heff.heff_plan_export(P.handle, which)
+        heff.heff_plan_select_tiles(P.handle, heff.TILE_PAIR_256, heff.TILE_PAIR_256)
+        pairs = heff.heff_plan_export(P.handle, which)
+        segs = heff.heff_plan_export(P.handle, which + 1)
+        heff.heff_plan_select_tiles(P.handle, heff.TILE_256, heff.TILE_256)
+        assert len(pairs) % 2 == 0
+        seg = lambda t: segs[t["seg_begin"]:t["seg_begin"] + t["seg_count"]].tolist()
+        for a, b in zip(pairs[0::2], pairs[1::2]):
+            if a["seg_count"] == 0 or b["seg_count"] == 0:
+                assert a["seg_count"] == b["seg_count"] == 0          # no ring use on either side
+                continue
+            assert a["b_row"] == b["b_row"] and a["n"] == b["n"] and a["ktotal"] == b["ktotal"]
+            assert seg(a) == seg(b)
+            assert a["m"] > 0                                          # rank 0 is never a ghost
+        key = lambda t: (int(t["a_row"]), int(t["b_row"]), int(t["c_off"]), int(t["m"]), int(t["n"]))
+        real = sorted(key(t) for t in pairs if t["m"] > 0)
+        assert real == sorted(key(t) for t in single if t["m"] > 0)
 
 
 def test_product_state_reaches_total_charge():
