@@ -30,8 +30,8 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1"): (470.196224e6 + 286.387968e6, "9cb355059336568e"),
-    ("spin_m4096", "bf16x3", "gemm2"): (810.263040e6 + 44.315904e6, "9cb355059336568e"),
+    ("spin_m4096", "bf16x3", "gemm1", 256): (470.196224e6 + 286.387968e6, "9cb355059336568e"),
+    ("spin_m4096", "bf16x3", "gemm2", 256): (810.263040e6 + 44.315904e6, "9cb355059336568e"),
 }
 
 
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--tiles", default="",
+                    help="tile variants of GEMM 1 and GEMM 2 (256, 128 or 512 = CTA pairs), e.g. 512,256; "
+                         "skips the autotuner")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's default tile widths (for profiling: serialised launches under a "
                          "profiler would time the candidates differently)")
@@ -438,7 +441,11 @@ def run_ours(args):
         heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
 
     # one-time plan setup (outside the timed region): tile width per GEMM by measurement
-    if args.no_autotune:
+    tune_ms = None
+    if args.tiles:
+        tile_n = tuple(int(v) for v in args.tiles.split(","))
+        heff.heff_plan_select_tiles(plan.handle, *tile_n)
+    elif args.no_autotune:
         tile_n = (int(st[15]), int(st[22]) or int(st[15]))
     else:
         tune_ms = []
@@ -531,7 +538,7 @@ def run_ours(args):
                 "note": f"{passes} tensor-core products per useful multiply-add (hi/lo split)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    tr = NCU_TRAFFIC.get((args.workload, prec, dom))
+    tr = NCU_TRAFFIC.get((args.workload, prec, dom, int(tile_n[0 if dom == "gemm1" else 1])))
     roof["traffic"] = tr[0] if tr and tr[1] == _src_sha() else None
     roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     roof["launch_ms"] = g_ms[dom]
@@ -544,7 +551,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "m": int(w.alpha_d.sum()), "sectors": int(len(w.alpha_d)),
                    "mpo_k": int(w.W1.shape[0]), "d": int(w.W1.shape[1]), "precision": prec, "io_dtype": io,
                    "tile_variant": list(tile_n),
-                   "autotune_ms": [round(v, 4) for v in tune_ms] if not args.no_autotune else None,
+                   "autotune_ms": [round(v, 4) for v in tune_ms] if tune_ms is not None else None,
                    "l2": "flushed (512 MB write) between timed steps; working set > L2",
                    "parallelism": f"independent problems per rank x{world}"},
         "tflops_canonical": canonical * value / 1e12,
