@@ -30,8 +30,9 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1", 256): (470.196224e6 + 286.387968e6, "9cb355059336568e"),
-    ("spin_m4096", "bf16x3", "gemm2", 256): (810.263040e6 + 44.315904e6, "9cb355059336568e"),
+    ("spin_m4096", "bf16x3", "gemm1", 256): (468.778240e6 + 286.329088e6, "81432dd9ebe5846b"),
+    ("spin_m4096", "bf16x3", "gemm1", 512): (482.758912e6 + 287.741440e6, "81432dd9ebe5846b"),
+    ("spin_m4096", "bf16x3", "gemm2", 256): (802.190336e6 + 44.523008e6, "81432dd9ebe5846b"),
 }
 
 
