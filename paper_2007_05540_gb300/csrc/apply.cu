@@ -61,43 +61,60 @@ template <> struct Plane<HEFF_PREC_TF32X3> {
 };
 
 
+// ------------------------------------------------------------------ dependent launch
+// wait for the predecessor grid on the stream (no-op without programmatic launch), and let
+// the successor be scheduled onto SMs as this grid's blocks retire
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ pack x -> XT
-template <typename In, int PREC>
-__device__ __forceinline__ void pack_tile(const PackTile& t, int bz, const PtrBatch& xs, char* __restrict__ xt,
-                                          int64_t ld, int64_t plane_elems, int64_t batch_elems) {
-    using E = typename Plane<PREC>::T;
-    using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
-    __shared__ Acc s[32][33];
-    const In* x = static_cast<const In*>(xs.p[bz]);
-    E* hi = reinterpret_cast<E*>(xt) + (int64_t)bz * batch_elems;
-    E* lo = hi + plane_elems;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    // read rows a (stride m_b), columns b contiguous
-    for (int r = ty; r < 32; r += 8) {
-        int a = t.a0 + r, b = t.b0 + tx;
-        Acc v = 0;
-        if (a < t.m_a && b < t.m_b) v = (Acc)x[t.x_off + (int64_t)a * t.m_b + b];
-        s[r][tx] = v;
-    }
-    __syncthreads();
-    // write XT rows b, columns a contiguous (a in [m_a, a_pad) are zero padding)
-    for (int r = ty; r < 32; r += 8) {
-        int b = t.b0 + r, a = t.a0 + tx;
-        if (b < t.m_b && a < t.a_pad) {
-            E h, l;
-            Plane<PREC>::split(s[tx][r], h, l);
-            int64_t o = (t.xt_row0 + b) * ld + t.xt_col0 + a;
-            hi[o] = h;
-            if (PREC != HEFF_PREC_FP64) lo[o] = l;
-        }
-    }
-}
+// One warp per 32 x 32 tile (four tiles per block): the warp loads the tile's 32 rows a
+// (columns b contiguous, one element per lane, all loads in flight), transposes through
+// its own shared-memory tile, and writes XT rows b, columns a contiguous (a in [m_a, a_pad)
+// are the zero padding), two columns per lane and two rows per pass: every store
+// instruction writes two full 32-column row pieces of a plane.
+constexpr int PACK_WARPS = 4;
 
 template <typename In, int PREC>
-__global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, PtrBatch xs,
-                                                   char* __restrict__ xt, int64_t ld, int64_t plane_elems,
-                                                   int64_t batch_elems) {
-    pack_tile<In, PREC>(tiles[blockIdx.x], blockIdx.y, xs, xt, ld, plane_elems, batch_elems);
+__global__ void __launch_bounds__(32 * PACK_WARPS) pack_kernel(const PackTile* __restrict__ tiles, int ntiles,
+                                                               PtrBatch xs, char* __restrict__ xt, int64_t ld,
+                                                               int64_t plane_elems, int64_t batch_elems) {
+    using E = typename Plane<PREC>::T;
+    using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
+    __shared__ Acc s[PACK_WARPS][32][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ti = blockIdx.x * PACK_WARPS + warp;
+    if (ti >= ntiles) return;                       // warp-uniform; the block never synchronises
+    const PackTile t = tiles[ti];
+    const int bz = blockIdx.y;
+    Acc (*sw)[33] = s[warp];
+    pdl_wait();                                     // x may come from the previous kernel
+    pdl_trigger();
+    {
+        const In* x = static_cast<const In*>(xs.p[bz]) + t.x_off;
+        const int b = t.b0 + lane;
+        const bool bv = b < t.m_b;
+        const int na = t.m_a - t.a0;                // rows of x left in this tile (may be <= 0)
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            sw[r][lane] = (bv && r < na) ? (Acc)x[(int64_t)(t.a0 + r) * t.m_b + b] : (Acc)0;
+    }
+    __syncwarp();
+    E* hi = reinterpret_cast<E*>(xt) + (int64_t)bz * batch_elems;
+    E* lo = hi + plane_elems;
+    const int c = 2 * (lane & 15), h = lane >> 4;
+    const int nb = t.m_b - t.b0;                    // XT rows of this tile
+    const int64_t o0 = (t.xt_row0 + t.b0) * ld + t.xt_col0 + t.a0 + c;
+#pragma unroll 4
+    for (int r = h; r < 32; r += 2) {
+        if (r >= nb) break;
+        E h0, l0, h1, l1;
+        Plane<PREC>::split(sw[c][r], h0, l0);
+        Plane<PREC>::split(sw[c + 1][r], h1, l1);
+        const int64_t o = o0 + (int64_t)r * ld;
+        Plane<PREC>::store2(hi + o, h0, h1);
+        if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lo + o, l0, l1);
+    }
 }
 
 // ------------------------------------------------------------------ LW / RW preparation
@@ -107,6 +124,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ 
 #ifndef HEFF_MIX_ROWS
 #define HEFF_MIX_ROWS 1        // rows per warp and pass
 #endif
+
 struct MixArgs {
     const MixTile* tiles;
     const MixTerm* terms;
@@ -214,6 +232,7 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
 
 template <typename In, int PREC>
 __global__ void __launch_bounds__(256) mix_kernel(MixArgs a) {
+    pdl_trigger();                                  // the pack kernel may be scheduled behind it
     mix_tile<In, PREC>(a.tiles[blockIdx.x], a);
 }
 
@@ -334,9 +353,18 @@ static int64_t plane_elems_xt(const heff_plan* p) { return (int64_t)p->opts.max_
 
 template <typename In, int PREC>
 static void launch_pack_t(heff_plan* p, const PtrBatch& xs, int nb, char* ws, cudaStream_t st) {
-    dim3 grid((unsigned)p->pack.size(), nb);
-    pack_kernel<In, PREC><<<grid, 256, 0, st>>>(p->d_pack, xs, ws + p->off_xt, p->ld_x, plane_elems_xt(p),
-                                               p->rows_x * p->ld_x);
+    const int nt = (int)p->pack.size();
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3((unsigned)((nt + PACK_WARPS - 1) / PACK_WARPS), nb);
+    cfg.blockDim = dim3(32 * PACK_WARPS);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = HEFF_PDL ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, pack_kernel<In, PREC>, static_cast<const PackTile*>(p->d_pack), nt, xs,
+                       ws + p->off_xt, p->ld_x, plane_elems_xt(p), p->rows_x * p->ld_x);
 }
 
 int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, void* stream) {

@@ -22,6 +22,14 @@ constexpr int KPAD = HEFF_KPAD;
 
 inline int64_t pad_up(int64_t v, int64_t p) { return (v + p - 1) / p * p; }
 
+// Programmatic dependent launch of the matvec's kernels (pack, GEMM 1, GEMM 2): each may be
+// scheduled while its predecessor on the stream finishes, runs its prologue (barriers,
+// tensor memory), and waits (griddepcontrol.wait) before it touches global memory that
+// the predecessor or earlier work writes or reads.  0 launches them in plain stream order.
+#ifndef HEFF_PDL
+#define HEFF_PDL 1
+#endif
+
 int fail(int code, const char* fmt, ...);
 void clear_error();
 void count_launches(int64_t n);

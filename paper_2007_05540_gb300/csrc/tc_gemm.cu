@@ -318,6 +318,11 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     if constexpr (CL > 1) cluster_sync();  // the peer's barriers exist before anything reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // programmatic dependent launch: the prologue above touched only this CTA's own state;
+    // the operands written by the previous kernel on the stream are read from here on.
+    // The successor may then be scheduled onto SMs as these CTAs retire.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
     const long cid = (long)(blockIdx.x / CL), ncl = (long)(gridDim.x / CL);
     const long nent = g.ntasks / CL;                                 // entries per batch
@@ -805,21 +810,28 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
         const long total = (long)(g.ntasks / CL) * nb;        // entries (tiles, or pairs of tiles)
         long units = max_cl;                                   // CTAs, or clusters of CL CTAs
         if (total < units) units = total;
-        if (CL == 1) {
-            K::kern<<<(unsigned)units, tc_threads<PREC>(), S::TOTAL, st>>>(maps, g);
-        } else {
+        {
             cudaLaunchConfig_t cfg{};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+            cudaLaunchAttribute at[2];
+            int na = 0;
+            if (HEFF_PDL) {
+                at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                at[na].val.programmaticStreamSerializationAllowed = 1;
+                ++na;
+            }
+            if (CL > 1) {
+                at[na].id = cudaLaunchAttributeClusterDimension;
+                at[na].val.clusterDim.x = CL; at[na].val.clusterDim.y = 1; at[na].val.clusterDim.z = 1;
+                ++na;
+            }
             cfg.gridDim = dim3((unsigned)(units * CL));
             cfg.blockDim = dim3(tc_threads<PREC>());
             cfg.dynamicSmemBytes = S::TOTAL;
             cfg.stream = st;
             cfg.attrs = at;
-            cfg.numAttrs = 1;
+            cfg.numAttrs = na;
             cudaError_t e = cudaLaunchKernelEx(&cfg, K::kern, maps, g);
-            if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "tc_gemm cluster launch: %s", cudaGetErrorString(e));
+            if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "tc_gemm launch: %s", cudaGetErrorString(e));
         }
         count_launches(1);
     }
