@@ -316,9 +316,18 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
         "note": "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"}
     del Pj, dj, wsj, yj
 
-    # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles)
-    nb = 32
-    we, le, be = make_problem("electron_m2048", 0)
+    # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles): the
+    # range-5 chain window and the 4 x 8 Hubbard cylinder window
+    for name in ("electron_m2048", "electron_hubbard_4x8_m2048"):
+        out[name + "_batch32_graph"] = batched_graph(name, 32, dev, stream, flush)
+    return out
+
+
+def batched_graph(name, nb, dev, stream, flush):
+    """nb applies of one workload sharing L, W, R, captured once in a CUDA graph and replayed."""
+    import torch
+    from paper_2007_05540_gb300 import heff
+    we, le, be = make_problem(name, 0)
     xs_host = [le[4].assemble(lambda k: we.x_block(k, b)) for b in range(nb)]
     Pe = heff.Plan(*le, be["W1"], be["W2"], "bf16x3", "f32", max_batch=nb)
     de = {k: torch.from_numpy(np.asarray(be[k])).to(dev, torch.float32) for k in ("L", "W1", "W2", "R")}
@@ -339,11 +348,12 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
         g.replay()
     ms = _events_ms(g.replay, 10, torch.cuda.current_stream(), flush)
     fl = Pe.flops_canonical
-    out["electron_m2048_batch32_graph"] = {
-        "applies_per_s": nb * 1000.0 / ms, "ms_per_batch": ms, "tile_variant": list(tn),
-        "tflops_canonical": nb * fl / (ms * 1e-3) / 1e12, "flops_per_apply": fl,
-        "sectors": int(len(we.alpha_d)), "max_block": int(we.alpha_d.max()), "mpo_k": int(we.W1.shape[0])}
-    return out
+    res = {"applies_per_s": nb * 1000.0 / ms, "ms_per_batch": ms, "tile_variant": list(tn),
+           "tflops_canonical": nb * fl / (ms * 1e-3) / 1e12, "flops_per_apply": fl,
+           "sectors": int(len(we.alpha_d)), "max_block": int(we.alpha_d.max()), "mpo_k": int(we.W1.shape[0])}
+    del g, Pe, wse, xs, ys, de
+    torch.cuda.synchronize()
+    return res
 
 
 def env_update_timing(w, dev, stream):

@@ -230,8 +230,11 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
     }
 }
 
+#ifndef HEFF_MIX_MINB
+#define HEFF_MIX_MINB 6        // resident blocks per SM the register allocation must allow
+#endif
 template <typename In, int PREC>
-__global__ void __launch_bounds__(256) mix_kernel(MixArgs a) {
+__global__ void __launch_bounds__(256, HEFF_MIX_MINB) mix_kernel(MixArgs a) {
     pdl_trigger();                                  // the pack kernel may be scheduled behind it
     mix_tile<In, PREC>(a.tiles[blockIdx.x], a);
 }

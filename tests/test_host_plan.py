@@ -60,7 +60,8 @@ def _plan(w, lays, bufs, precision="fp64", io="f64"):
     return heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], precision, io)
 
 
-@pytest.mark.parametrize("name", ["spin_m24", "spin_m64", "electron_m40", "electron_m96", "spin_j1j2_6x6_m200"])
+@pytest.mark.parametrize("name", ["spin_m24", "spin_m64", "electron_m40", "electron_m96", "spin_j1j2_6x6_m200",
+                                  "electron_hubbard_4x8_m96"])
 def test_canonical_flops_match_oracle(name):
     w = wl.workload_by_name(name)
     lays, bufs = library_problem(w)
@@ -71,7 +72,8 @@ def test_canonical_flops_match_oracle(name):
 
 @pytest.mark.parametrize("name,prec", [("spin_m24", "fp64"), ("spin_m64", "fp64"),
                                        ("electron_m40", "fp64"), ("spin_m64", "bf16x3"),
-                                       ("electron_m96", "bf16x3")])
+                                       ("electron_m96", "bf16x3"), ("electron_hubbard_4x8_m96", "bf16x3"),
+                                       ("spin_m200", "tf32x3")])
 def test_plan_schedule_reproduces_oracle(name, prec):
     w = wl.workload_by_name(name)
     lays, bufs = library_problem(w)
@@ -248,3 +250,4 @@ def test_product_state_reaches_total_charge():
     assert tuple(map(int, el[st].sum(axis=0))) == (6, 0)
     with pytest.raises(ValueError):
         dmrg.product_state(sp, 3, (0,))          # odd chain cannot reach 2Sz = 0
+

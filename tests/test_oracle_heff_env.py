@@ -91,7 +91,7 @@ def test_heff_equals_projected_hamiltonian_hubbard(j, total):
     assert np.abs(K @ x.to_dense().reshape(-1) - yd).max() < 1e-12 * max(1.0, np.abs(yd).max())
 
 
-@pytest.mark.parametrize("name", ["spin_m64", "electron_m96"])
+@pytest.mark.parametrize("name", ["spin_m64", "electron_m96", "electron_hubbard_4x8_m96"])
 def test_block_apply_equals_dense_einsum(name):
     w = wl.workload_by_name(name)
     L, W1, W2, R, x = heff.problem_from_workload(w)
@@ -103,7 +103,7 @@ def test_block_apply_equals_dense_einsum(name):
     assert abs(np.linalg.norm(yd) - yb.norm()) < 1e-12 * np.linalg.norm(yd)
 
 
-@pytest.mark.parametrize("name", ["spin_m64", "electron_m96"])
+@pytest.mark.parametrize("name", ["spin_m64", "electron_m96", "electron_hubbard_4x8_m96"])
 def test_heff_hermitian_and_linear(name):
     w = wl.workload_by_name(name)
     L, W1, W2, R, u = heff.problem_from_workload(w, batch=0)

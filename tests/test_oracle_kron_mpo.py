@@ -97,6 +97,19 @@ def test_hubbard_mpo_equals_kron():
     assert np.abs(Hm - Hk).max() < 1e-12
 
 
+@pytest.mark.parametrize("Lx,Ly", [(3, 2), (2, 3)])
+def test_hubbard_cylinder_mpo_equals_kron(Lx, Ly):
+    # the nearest-neighbour hops of the snake-ordered cylinder (periodic in y) give the
+    # Hubbard cylinder of Section V; its MPO must contract to the Kronecker Hamiltonian
+    n = Lx * Ly
+    hops = wl.cylinder_hops(Lx, Ly, 1.0)
+    assert len(hops) == (Lx - 1) * Ly + Lx * (Ly if Ly > 2 else Ly - 1)
+    mpo = wl.hubbard_mpo(n, hops, 8.0)
+    Hm = kron.mpo_to_dense(mpo)
+    Hk = kron.hubbard_hamiltonian(n, hops, 8.0).toarray()
+    assert np.abs(Hm - Hk).max() < 1e-12
+
+
 @pytest.mark.parametrize("which", ["spin", "electron"])
 def test_mpo_charge_rule_and_transpose_symmetry(which):
     w = wl.spin_heff_workload(64, 8, 0) if which == "spin" else wl.electron_heff_workload(96, 3, 6, 24)
@@ -116,3 +129,7 @@ def test_bulk_window_bond_dims():
     from workloads.fill import spin_window, electron_window
     assert spin_window()["W1"].shape == (14, 2, 2, 14)
     assert electron_window()["W1"].shape == (22, 4, 4, 22)
+    # 4 x 8 Hubbard cylinder: at most four left sites with a hop across a bond, four
+    # fermion channels each, plus the start and done channels
+    win = wl.hubbard_lattice_window()
+    assert win["W1"].shape == (18, 4, 4, 18) and win["W2"].shape == (18, 4, 4, 18)

@@ -14,7 +14,7 @@ import numpy as np
 
 from .sectors import (binomial_sectors, paper_model_sectors, electron_sectors,
                       spin_phys, electron_phys)
-from .mpo import heisenberg_mpo, hubbard_mpo, chain_pairs, cylinder_pairs, bulk_window
+from .mpo import heisenberg_mpo, hubbard_mpo, chain_pairs, cylinder_pairs, cylinder_hops, bulk_window
 
 TAG_L, TAG_R, TAG_X, TAG_SITE = 1, 2, 3, 4
 
@@ -167,6 +167,16 @@ def electron_window(t=1.0, U=8.0, R=5):
     return bulk_window(mpo, R + 1)
 
 
+def hubbard_lattice_window(Lx=8, Ly=4, t=1.0, U=8.0):
+    """Two-site window of the snake-ordered Lx x Ly Hubbard cylinder MPO (nearest-neighbour
+    hopping t, on-site U; the electron lattice of Section V, here 4 x 8 as a 32-site MPS), at
+    the first bond triple with the largest total channel count."""
+    n = Lx * Ly
+    mpo = hubbard_mpo(n, cylinder_hops(Lx, Ly, t), U)
+    best = max(range(n - 1), key=lambda s: (mpo.bond_dim(s) + mpo.bond_dim(s + 1) + mpo.bond_dim(s + 2), -s))
+    return bulk_window(mpo, best)
+
+
 def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLINGS,
                        name=None, window=None):
     """Spin-1/2 two-site H_eff inputs.
@@ -192,11 +202,12 @@ def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLIN
         labels_m=tuple(win["labels_m"]))
 
 
-def electron_heff_workload(m, seed=0, n_center=16, max_block=256, name=None, span=5):
-    """Hubbard two-site H_eff inputs on (N, 2Sz) charges (d = 4, k = 22)."""
+def electron_heff_workload(m, seed=0, n_center=16, max_block=256, name=None, span=5, window=None):
+    """Hubbard two-site H_eff inputs on (N, 2Sz) charges (d = 4; k = 22 for the default
+    range-5 chain window, or the MPO window passed in)."""
     aq, ad = electron_sectors(m, seed, n_center, span, span, max_block=max_block)
     bq, bd = electron_sectors(m, seed + 1, n_center + 2, span, span, max_block=max_block)
-    win = electron_window()
+    win = electron_window() if window is None else window
     return HeffWorkload(
         name=name or f"electron_m{m}", alpha_q=aq, alpha_d=ad, beta_q=bq, beta_d=bd,
         phys=electron_phys(), W1=win["W1"], W2=win["W2"], ql=win["ql"], qm=win["qm"],
@@ -220,6 +231,11 @@ def workload_by_name(name):
         "spin_j1j2_6x6_m200": lambda: spin_heff_workload(200, 10, 7, name="spin_j1j2_6x6_m200",
                                                          window=lattice_window()),
         "electron_m2048": lambda: electron_heff_workload(2048, 0, name="electron_m2048"),
+        "electron_hubbard_4x8_m2048": lambda: electron_heff_workload(2048, 0, name="electron_hubbard_4x8_m2048",
+                                                                     window=hubbard_lattice_window()),
+        "electron_hubbard_4x8_m96": lambda: electron_heff_workload(96, 3, n_center=6, max_block=24,
+                                                                   name="electron_hubbard_4x8_m96",
+                                                                   window=hubbard_lattice_window()),
         "spin_m24": lambda: spin_heff_workload(24, 6, 9, name="spin_m24"),
         "spin_m64": lambda: spin_heff_workload(64, 8, 5, name="spin_m64"),
         "spin_m200": lambda: spin_heff_workload(200, 10, 7, name="spin_m200"),

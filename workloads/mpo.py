@@ -236,6 +236,12 @@ def cylinder_pairs(Lx, Ly, J1, J2=0.0):
     return [(p, q, J) for (p, q), J in sorted(acc.items())]
 
 
+def cylinder_hops(Lx, Ly, t=1.0):
+    """Nearest-neighbour hops ``(i, j, t)`` of a snake-ordered square cylinder (open in x,
+    periodic in y), for the Hubbard MPO."""
+    return cylinder_pairs(Lx, Ly, t, 0.0)
+
+
 def heisenberg_mpo(n_sites, pairs, field_z=0.0):
     """Heisenberg MPO for weighted pairs (optionally a uniform Sz field)."""
     from .sectors import spin_phys
