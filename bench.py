@@ -30,9 +30,8 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1", 256): (468.778240e6 + 286.329088e6, "81432dd9ebe5846b"),
-    ("spin_m4096", "bf16x3", "gemm1", 512): (482.758912e6 + 287.741440e6, "81432dd9ebe5846b"),
-    ("spin_m4096", "bf16x3", "gemm2", 256): (802.190336e6 + 44.523008e6, "81432dd9ebe5846b"),
+    ("spin_m4096", "bf16x3", "gemm1", 256): (470.334208e6 + 286.111488e6, "39073cda573c92f4"),
+    ("spin_m4096", "bf16x3", "gemm2", 256): (812.061440e6 + 45.017856e6, "39073cda573c92f4"),
 }
 
 
