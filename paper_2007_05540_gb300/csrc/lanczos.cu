@@ -26,7 +26,7 @@ namespace heff {
 namespace {
 
 constexpr int RT = 256;          // threads per reduction block
-constexpr int RB = 512;          // reduction blocks (partial sums per vector)
+constexpr int RB = 456;          // reduction blocks (partial sums per vector): 3 per SM on 152 SMs
 constexpr int VT = 8;            // vectors per multi-dot pass
 
 // State in the Lanczos workspace (doubles): [0] n_eff (as double), [1] active flag,
@@ -91,13 +91,28 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double* __restrict__
     double acc[VT];
 #pragma unroll
     for (int t = 0; t < VT; ++t) acc[t] = 0.0;
-    for (int64_t i = beg + threadIdx.x; i < end; i += RT) {
+    // two elements per iteration: 2 (nv + 1) loads in flight per thread
+    int64_t i = beg + threadIdx.x;
+    for (; i + RT < end; i += 2 * RT) {
+        const double w0 = w[i], w1 = w[i + RT];
+        double v0[VT], v1[VT];
+#pragma unroll
+        for (int t = 0; t < VT; ++t) {
+            v0[t] = t < nv ? V[(int64_t)(j0 + t) * n + i] : 0.0;
+            v1[t] = t < nv ? V[(int64_t)(j0 + t) * n + i + RT] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < VT; ++t) acc[t] = fma(v1[t], w1, fma(v0[t], w0, acc[t]));
+    }
+    for (; i < end; i += RT) {
         const double wi = w[i];
 #pragma unroll
         for (int t = 0; t < VT; ++t)
             if (t < nv) acc[t] = fma(V[(int64_t)(j0 + t) * n + i], wi, acc[t]);
     }
-    for (int t = 0; t < nv; ++t) {
+#pragma unroll
+    for (int t = 0; t < VT; ++t) {
+        if (t >= nv) break;                          // block-uniform
         double s = block_sum(acc[t], sh);
         if (threadIdx.x == 0) part[blockIdx.x * VT + t] = s;
     }
@@ -125,8 +140,22 @@ __global__ void __launch_bounds__(RT) combine_kernel(const double* __restrict__ 
     if (!ignore_active && state[1] == 0.0) return;
     for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = c[j];
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+    // two elements per iteration (their loads in flight together), then the remainder
+    const int64_t stride = (int64_t)gridDim.x * RT;
+    int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+        for (int j = 0; j < nv; ++j) {
+            a0 = fma(cs[j], V[(int64_t)j * n + i], a0);
+            a1 = fma(cs[j], V[(int64_t)j * n + i + stride], a1);
+        }
+        y[i] = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a0;
+        y[i + stride] = (beta_y == 0.0 ? 0.0 : beta_y * y[i + stride]) + sign * a1;
+    }
+    for (; i < n; i += stride) {
         double a = 0.0;
+#pragma unroll 8
         for (int j = 0; j < nv; ++j) a = fma(cs[j], V[(int64_t)j * n + i], a);
         y[i] = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a;
     }
@@ -433,11 +462,12 @@ extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, cons
          plan->nelem_x, lay.nmax};
     const int64_t n = z.n;
     const int G = grid_for(n);
+    const int GN = G < 1024 ? G : 1024;      // normalize: every block re-sums the RB partials
     int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
     if (rc) return rc;
     // v_0 = x0 / ||x0||
     sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, z.part);
-    normalize_kernel<<<G, RT, 0, st>>>(z.part, RB, x0, z.V, n, z.state, 0, 0, z.nmax);
+    normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x0, z.V, n, z.state, 0, 0, z.nmax);
     count_launches(2);
     for (int k = 0; k < n_iter; ++k) {
         double* vk = z.V + (int64_t)k * n;
@@ -457,7 +487,7 @@ extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, cons
         }
         set_alpha_kernel<<<1, 1, 0, st>>>(z.state, z.h, z.s, k);
         sumsq_kernel<<<RB, RT, 0, st>>>(z.w(), n, z.part);
-        normalize_kernel<<<G, RT, 0, st>>>(z.part, RB, z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, 1, k,
+        normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, 1, k,
                                            z.nmax);
         count_launches(3);
     }
@@ -465,7 +495,7 @@ extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, cons
     // x = V s (rows beyond n_eff have s = 0), then normalise
     combine_kernel<<<G, RT, 0, st>>>(z.V, n, z.nmax, z.s, 1.0, 0.0, x_out, z.state, 1);
     sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, z.part);
-    normalize_kernel<<<G, RT, 0, st>>>(z.part, RB, x_out, x_out, n, z.state, 2, 0, z.nmax);
+    normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x_out, x_out, n, z.state, 2, 0, z.nmax);
     count_launches(4);
     // result: [theta, residual estimate, n_eff, alpha..., beta...]
     cudaMemcpyAsync(result, z.state + 2, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st);
@@ -546,12 +576,13 @@ extern "C" int heff_davidson(heff_plan* plan, const void* L, const void* W1, con
     double* q = reinterpret_cast<double*>(base + lay.off_q);
     const int64_t n = plan->nelem_x;
     const int G = grid_for(n);
+    const int GN = G < 1024 ? G : 1024;      // normalize: every block re-sums the RB partials
     int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
     if (rc) return rc;
     dav_init_state_kernel<<<1, 32, 0, st>>>(state, tol);
     // v_0 = x0 / ||x0|| (sets active when x0 != 0), v^A_0 = A v_0
     sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, part);
-    normalize_kernel<<<G, RT, 0, st>>>(part, RB, x0, V, n, state, 0, 0, max_vecs);
+    normalize_kernel<<<GN, RT, 0, st>>>(part, RB, x0, V, n, state, 0, 0, max_vecs);
     count_launches(3);
     if ((rc = heff_apply_prepared(plan, V, VA, apply_ws, apply_ws_bytes, stream))) return rc;
     auto gram_schmidt = [&](int nv) {          // q -= V (V^T q) over v_0 .. v_{nv-1}
@@ -594,13 +625,13 @@ extern "C" int heff_davidson(heff_plan* plan, const void* L, const void* W1, con
         gram_schmidt(i + 1);
         double* vn = V + (int64_t)(i + 1) * n;
         sumsq_kernel<<<RB, RT, 0, st>>>(q, n, part);
-        normalize_kernel<<<G, RT, 0, st>>>(part, RB, q, vn, n, state, 3, 0, max_vecs);
+        normalize_kernel<<<GN, RT, 0, st>>>(part, RB, q, vn, n, state, 3, 0, max_vecs);
         count_launches(2);
         if ((rc = heff_apply_prepared(plan, vn, VA + (int64_t)(i + 1) * n, apply_ws, apply_ws_bytes, stream)))
             return rc;
     }
     sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, part);
-    normalize_kernel<<<G, RT, 0, st>>>(part, RB, x_out, x_out, n, state, 2, 0, max_vecs);
+    normalize_kernel<<<GN, RT, 0, st>>>(part, RB, x_out, x_out, n, state, 2, 0, max_vecs);
     count_launches(2);
     // result: [lambda, ||q||, vectors used]
     cudaMemcpyAsync(result, state + 2, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st);

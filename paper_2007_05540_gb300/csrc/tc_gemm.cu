@@ -21,8 +21,9 @@
 // chunking bounds the steps per accumulator.
 // T (GEMM 1) leaves through TMA: each warp splits 32 rows x 32 columns into hi/lo in
 // registers, writes them to a swizzled shared-memory box and issues bulk tensor stores;
-// quarters with fewer than 32 valid rows, and y (GEMM 2, per-block pitch), are stored
-// by the threads through a padded transpose.
+// quarters with fewer than 32 valid rows go through an XOR-swizzled transpose and leave
+// in 16-byte row pieces (several rows per store instruction); y (GEMM 2, per-block pitch)
+// leaves through the same transpose in 128-byte row stores.
 // Every mbarrier wait is bounded (about a second); on expiry the CTA raises the
 // workspace error flag, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
@@ -567,21 +568,45 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                 __syncwarp();
                 const int c = c0 + lane;                       // this lane's column
                 if (g.mode == 0) {
-                    E* hi = reinterpret_cast<E*>(g.C) + t.c_off + (int64_t)b * g.c_batch_elems + c;
+                    // T rows of a partial quarter: 16-byte stores, each lane one group of VEC
+                    // columns of one row, RPI rows per store instruction.  T offsets, pitches
+                    // and chunk starts are multiples of 32 elements and a tile's columns
+                    // (with its zero padding) end on a multiple of 32, so every group is
+                    // aligned and a chunk that starts inside the tile lies inside it.
+                    constexpr int VEC = 16 / (int)sizeof(E), LPR = 32 / VEC, RPI = 32 / LPR;
+                    const int cc = (lane % LPR) * VEC, rsub = lane / LPR;
+                    E* hi = reinterpret_cast<E*>(g.C) + t.c_off + (int64_t)b * g.c_batch_elems + c0 + cc;
                     E* lo = hi + g.c_plane_elems;
-                    if (c < ncols) {
-                        for (int rr = 0; rr < rows; ++rr) {
-                            const float f = c < t.n ? stage[rr * 32 + (lane ^ rr)] : 0.f;
-                            const int64_t o = (int64_t)(q * 32 + rr) * t.ldc;
+                    if (c0 < ncols) {
+                        for (int r0 = 0; r0 < rows; r0 += RPI) {
+                            const int rr = r0 + rsub;
+                            if (rr >= rows) break;
+                            uint32_t hv[4], lv[4];
                             if constexpr (PREC == HEFF_PREC_BF16X3) {
-                                const __nv_bfloat16 h = __float2bfloat16_rn(f);
-                                hi[o] = h;
-                                lo[o] = __float2bfloat16_rn(f - __bfloat162float(h));
+#pragma unroll
+                                for (int p = 0; p < 4; ++p) {
+                                    const int col = cc + 2 * p;
+                                    const float f0 = c0 + col < t.n ? stage[rr * 32 + (col ^ rr)] : 0.f;
+                                    const float f1 = c0 + col + 1 < t.n ? stage[rr * 32 + ((col + 1) ^ rr)] : 0.f;
+                                    const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+                                    const __nv_bfloat162 l = __floats2bfloat162_rn(f0 - __low2float(h),
+                                                                                   f1 - __high2float(h));
+                                    hv[p] = *reinterpret_cast<const uint32_t*>(&h);
+                                    lv[p] = *reinterpret_cast<const uint32_t*>(&l);
+                                }
                             } else {
-                                const float h = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xffffe000u);
-                                hi[o] = h;
-                                lo[o] = __uint_as_float((__float_as_uint(f - h) + 0x1000u) & 0xffffe000u);
+#pragma unroll
+                                for (int p = 0; p < 4; ++p) {
+                                    const int col = cc + p;
+                                    const float f = c0 + col < t.n ? stage[rr * 32 + (col ^ rr)] : 0.f;
+                                    const uint32_t h = (__float_as_uint(f) + 0x1000u) & 0xffffe000u;
+                                    hv[p] = h;
+                                    lv[p] = (__float_as_uint(f - __uint_as_float(h)) + 0x1000u) & 0xffffe000u;
+                                }
                             }
+                            const int64_t o = (int64_t)(q * 32 + rr) * t.ldc;
+                            *reinterpret_cast<uint4*>(hi + o) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                            *reinterpret_cast<uint4*>(lo + o) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                         }
                     }
                 } else if (c < t.n) {
