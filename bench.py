@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's default tile widths (for profiling: serialised launches under a "
                          "profiler would time the candidates differently)")
+    ap.add_argument("--lanczos-only", action="store_true",
+                    help="time only the FP64 Lanczos eigensolver (30 iterations, BF16x3 matvecs) on "
+                         "the workload and print its own JSON line (the profiling case of that step)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (other precisions, eigensolver, SVD, batched graph)")
     return ap.parse_args()
@@ -421,6 +424,35 @@ def backward_timing(dev, stream):
     return res
 
 
+# ------------------------------------------------------------------ eigensolver step alone
+def run_lanczos_only(args):
+    """FP64 Lanczos (30 iterations) with BF16x3 matvecs on one GPU: one warm-up run, then the
+    CUDA-event time of 3 runs (the L2 is not flushed: the basis vectors exceed it)."""
+    import torch
+    from paper_2007_05540_gb300 import heff
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    w, lays, bufs = make_problem(args.workload, 0)
+    Ll, W1l, W2l, Rl, xl = lays
+    n_iter = 30
+    d64 = {k: torch.from_numpy(np.asarray(bufs[k])).to(dev, torch.float64) for k in ("L", "W1", "W2", "R")}
+    x0 = torch.from_numpy(np.asarray(bufs["x"])).to(dev, torch.float64)
+    P = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], "bf16x3", "f64")
+    ws = P.workspace(dev)
+    lz = torch.empty(heff.heff_lanczos_workspace_size(P.handle, n_iter), dtype=torch.uint8, device=dev)
+    xv = torch.empty_like(x0)
+    r = torch.zeros(3 + 2 * (n_iter + 1), dtype=torch.float64, device=dev)
+
+    def f():
+        heff.heff_lanczos(P.handle, d64["L"], d64["W1"], d64["W2"], d64["R"], x0, n_iter, xv, r, ws, lz, stream)
+    f()
+    ms = _events_ms(f, 3, stream)
+    print(json.dumps({"workload": args.workload, "lanczos_iterations": n_iter, "matvec": "bf16x3",
+                      "ms": ms, "ritz": float(r[0].item()), "residual_estimate": float(r[1].item())}),
+          flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -619,5 +651,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.lanczos_only:
+        run_lanczos_only(a)
     else:
         run_ours(a)
