@@ -63,9 +63,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's default tile widths (for profiling: serialised launches under a "
                          "profiler would time the candidates differently)")
-    ap.add_argument("--lanczos-only", action="store_true",
-                    help="time only the FP64 Lanczos eigensolver (30 iterations, BF16x3 matvecs) on "
-                         "the workload and print its own JSON line (the profiling case of that step)")
+    ap.add_argument("--part", default="", choices=["", "lanczos", "svd", "env_update", "backward"],
+                    help="time one step of the DMRG bond update alone and print its own JSON line "
+                         "(the profiling cases): the FP64 Lanczos eigensolver (30 iterations, BF16x3 "
+                         "matvecs), the block SVD truncation, the environment update, the gradients")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (other precisions, eigensolver, SVD, batched graph)")
     return ap.parse_args()
@@ -424,7 +425,50 @@ def backward_timing(dev, stream):
     return res
 
 
-# ------------------------------------------------------------------ eigensolver step alone
+# ------------------------------------------------------------------ one step alone
+def run_part(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    if args.part == "lanczos":
+        return run_lanczos_only(args)
+    if args.part == "env_update":
+        w, _, _ = make_problem(args.workload, 0)
+        out = env_update_timing(w, dev, stream)
+    elif args.part == "backward":
+        out = backward_timing(dev, stream)
+    else:
+        out = svd_timing(args, dev, stream)
+    print(json.dumps({"part": args.part, "workload": args.workload, **out}), flush=True)
+
+
+def svd_timing(args, dev, stream):
+    """Block SVD truncation (to m, cutoff 1e-12) of the workload's two-site tensor x: the
+    host wall time of heff_svd_compute + heff_svd_truncate (they synchronise)."""
+    import torch
+    from paper_2007_05540_gb300 import heff
+    w, lays, bufs = make_problem(args.workload, 0)
+    xl = lays[4]
+    x = torch.from_numpy(np.asarray(bufs["x"])).to(dev, torch.float64)
+    x /= torch.linalg.norm(x)
+    s = heff.heff_svd_create(xl.handle)
+    try:
+        sws = torch.empty(heff.heff_svd_workspace_size(s), dtype=torch.uint8, device=dev)
+        heff.heff_svd_compute(s, x, sws, stream)                 # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        heff.heff_svd_compute(s, x, sws, stream)
+        q, dims, disc, nrm = heff.heff_svd_truncate(s, int(w.alpha_d.sum()), 1e-12, w.nq, 4096)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        sw32, sw64 = heff.heff_svd_info(s)
+    finally:
+        heff.heff_svd_destroy(s)
+    return {"ms": ms, "jacobi_sweeps": {"fp32": sw32, "fp64": sw64}, "kept": int(np.sum(dims)),
+            "sectors": int(len(dims)), "discarded_weight": float(disc)}
+
+
 def run_lanczos_only(args):
     """FP64 Lanczos (30 iterations) with BF16x3 matvecs on one GPU: one warm-up run, then the
     CUDA-event time of 3 runs (the L2 is not flushed: the basis vectors exceed it)."""
@@ -651,7 +695,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.lanczos_only:
-        run_lanczos_only(a)
+    elif a.part:
+        run_part(a)
     else:
         run_ours(a)

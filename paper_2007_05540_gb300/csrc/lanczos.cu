@@ -216,9 +216,13 @@ __global__ void set_alpha_kernel(double* state, const double* h1, const double* 
 // |beta_{n-1} s_{n-1}| (the Lanczos residual norm of the Ritz pair) to state[3], the
 // eigenvector to s; T holds 4 * nmax doubles of scratch.
 __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: the 32 lanes evaluate Sturm counts at 32 interior points of the bracket
+    // (multisection: each step shrinks it 33-fold), then lane 0 runs the inverse iteration
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const int n = (int)state[0];
-    for (int i = 0; i < nmax; ++i) s[i] = 0.0;
+    for (int i = lane; i < nmax; i += 32) s[i] = 0.0;
+    __syncwarp();                        // lane 0 writes s below: the zeros land first
     if (n <= 0) return;
     const double* al = state + 8;
     const double* be = state + 8 + nmax;
@@ -240,10 +244,18 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
         }
         return c;
     };
-    for (int it = 0; it < 200 && hi - lo > 4e-16 * scale; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (count_below(mid) >= 1) hi = mid; else lo = mid;
+    // the lowest eigenvalue stays in (lo, hi]: count_below(lo) = 0, count_below(hi) >= 1
+    for (int it = 0; it < 60 && hi - lo > 4e-16 * scale; ++it) {
+        const double step = (hi - lo) / 33.0;
+        const double x = lane == 31 ? hi - 0.5 * step : lo + (lane + 1) * step;
+        const unsigned below = __ballot_sync(0xffffffffu, count_below(x) >= 1);
+        const int k = below ? __ffs(below) - 1 : 32;             // first point with an eigenvalue below
+        const double xk = __shfl_sync(0xffffffffu, x, k < 32 ? k : 31);
+        const double xk1 = __shfl_sync(0xffffffffu, x, k > 0 ? (k < 32 ? k - 1 : 31) : 0);
+        if (k < 32) hi = xk;
+        if (k > 0) lo = xk1;
     }
+    if (lane != 0) return;
     const double theta = 0.5 * (lo + hi);
     // inverse iteration: (T - theta I) z_new = z, banded LU with partial pivoting.  A pivot
     // below tiny (theta is an eigenvalue to rounding, so one pivot is ~0: exactly 0 when

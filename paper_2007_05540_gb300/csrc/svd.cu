@@ -223,12 +223,24 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
             T* J = base + (F32 ? s.j32_off : s.j_off);
             T* cp = J + (int64_t)p * s.r;
             T* cq = J + (int64_t)q * s.r;
+            // (the column pieces of 4 iterations are loaded together: the pair's loops are
+            // bound by L2 latency; each lane's sums keep their order)
             T a = 0, b = 0, g = 0;
-            for (int i = lane; i < s.r; i += 32) {
-                const T u = cp[i], v = cq[i];
-                a = fma(u, u, a);
-                b = fma(v, v, b);
-                g = fma(u, v, g);
+            for (int i0 = lane; i0 < s.r; i0 += 128) {
+                T u[4], v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int i = i0 + 32 * t;
+                    u[t] = i < s.r ? cp[i] : (T)0;
+                    v[t] = i < s.r ? cq[i] : (T)0;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (i0 + 32 * t >= s.r) break;
+                    a = fma(u[t], u[t], a);
+                    b = fma(v[t], v[t], b);
+                    g = fma(u[t], v[t], g);
+                }
             }
             a = warp_sum_t(a); b = warp_sum_t(b); g = warp_sum_t(g);
             if (g == (T)0 || a == (T)0 || b == (T)0) continue;
@@ -240,19 +252,27 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double cd = 1.0 / sqrt(1.0 + t * t);
             const T c = (T)cd, sn = (T)(cd * t);
-            for (int i = lane; i < s.r; i += 32) {
-                const T u = cp[i], v = cq[i];
-                cp[i] = c * u - sn * v;
-                cq[i] = sn * u + c * v;
-            }
+            auto rotate = [&](T* x, T* y, int len) {
+                for (int i0 = lane; i0 < len; i0 += 128) {
+                    T u[4], v[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int i = i0 + 32 * t;
+                        u[t] = i < len ? x[i] : (T)0;
+                        v[t] = i < len ? y[i] : (T)0;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int i = i0 + 32 * t;
+                        if (i >= len) break;
+                        x[i] = c * u[t] - sn * v[t];
+                        y[i] = sn * u[t] + c * v[t];
+                    }
+                }
+            };
+            rotate(cp, cq, s.r);
             T* V = base + (F32 ? s.v32_off : s.v_off);
-            T* vp = V + (int64_t)p * s.k;
-            T* vq = V + (int64_t)q * s.k;
-            for (int i = lane; i < s.k; i += 32) {
-                const T u = vp[i], v = vq[i];
-                vp[i] = c * u - sn * v;
-                vq[i] = sn * u + c * v;
-            }
+            rotate(V + (int64_t)p * s.k, V + (int64_t)q * s.k, s.k);
         }
         if (!grid_barrier(bar, bar + 1, gridDim.x, err)) break;
     }
