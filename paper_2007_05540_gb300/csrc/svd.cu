@@ -13,7 +13,8 @@
 //
 // Precision: the GB300's FP64 rate is low, and a full FP64 Jacobi run needs ~18 sweeps of
 // ~12 r k^2 flops.  The sweeps therefore start on an FP32 copy (J32, V32) until the
-// columns are orthogonal to FP32 accuracy; V32 is made orthonormal in FP64 by two
+// columns are orthogonal to FP32 accuracy (block sweeps: pairs of 16-column blocks, each
+// rotated by one Jacobi sweep on its 32 x 32 Gram matrix, see svd_block_sweep_kernel); V32 is made orthonormal in FP64 by two
 // Newton-Schulz steps (V <- V (3 I - V^T V) / 2, each squaring the orthogonality error),
 // J <- J V in FP64, and FP64 Jacobi sweeps, accumulating into V, finish the
 // decomposition (quadratic convergence from the preconditioned start: 2-3 sweeps).  The
@@ -157,6 +158,9 @@ __global__ void svd_copy_w_kernel(const SvdSector* __restrict__ secs, double* __
 // second), after which the kernel sets err and returns.  Each block writes the largest
 // off-diagonal measure it saw to block_max[blockIdx.x].
 constexpr int SVD_SWEEP_NT = 256;
+#ifndef SVD_UNROLL
+#define SVD_UNROLL 8        // column pieces per lane loaded together in a pair's loops
+#endif
 constexpr long long SVD_BARRIER_CYCLES = 2ll << 30;
 
 __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks,
@@ -223,19 +227,20 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
             T* J = base + (F32 ? s.j32_off : s.j_off);
             T* cp = J + (int64_t)p * s.r;
             T* cq = J + (int64_t)q * s.r;
-            // (the column pieces of 4 iterations are loaded together: the pair's loops are
+            // (the column pieces of UJ iterations are loaded together: the pair's loops are
             // bound by L2 latency; each lane's sums keep their order)
+            constexpr int UJ = SVD_UNROLL;
             T a = 0, b = 0, g = 0;
-            for (int i0 = lane; i0 < s.r; i0 += 128) {
-                T u[4], v[4];
+            for (int i0 = lane; i0 < s.r; i0 += 32 * UJ) {
+                T u[UJ], v[UJ];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
+                for (int t = 0; t < UJ; ++t) {
                     const int i = i0 + 32 * t;
                     u[t] = i < s.r ? cp[i] : (T)0;
                     v[t] = i < s.r ? cq[i] : (T)0;
                 }
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
+                for (int t = 0; t < UJ; ++t) {
                     if (i0 + 32 * t >= s.r) break;
                     a = fma(u[t], u[t], a);
                     b = fma(v[t], v[t], b);
@@ -252,27 +257,34 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double cd = 1.0 / sqrt(1.0 + t * t);
             const T c = (T)cd, sn = (T)(cd * t);
-            auto rotate = [&](T* x, T* y, int len) {
-                for (int i0 = lane; i0 < len; i0 += 128) {
-                    T u[4], v[4];
+            // rotate the two columns of J and of V in one loop (both only need c, sn)
+            T* V = base + (F32 ? s.v32_off : s.v_off);
+            T* vp = V + (int64_t)p * s.k;
+            T* vq = V + (int64_t)q * s.k;
+            constexpr int UR = SVD_UNROLL / 2;
+            for (int i0 = lane; i0 < s.r; i0 += 32 * UR) {       // s.k <= s.r
+                T u[UR], v[UR], x[UR], y[UR];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int i = i0 + 32 * t;
-                        u[t] = i < len ? x[i] : (T)0;
-                        v[t] = i < len ? y[i] : (T)0;
+                for (int t = 0; t < UR; ++t) {
+                    const int i = i0 + 32 * t;
+                    u[t] = i < s.r ? cp[i] : (T)0;
+                    v[t] = i < s.r ? cq[i] : (T)0;
+                    x[t] = i < s.k ? vp[i] : (T)0;
+                    y[t] = i < s.k ? vq[i] : (T)0;
+                }
+#pragma unroll
+                for (int t = 0; t < UR; ++t) {
+                    const int i = i0 + 32 * t;
+                    if (i < s.r) {
+                        cp[i] = c * u[t] - sn * v[t];
+                        cq[i] = sn * u[t] + c * v[t];
                     }
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int i = i0 + 32 * t;
-                        if (i >= len) break;
-                        x[i] = c * u[t] - sn * v[t];
-                        y[i] = sn * u[t] + c * v[t];
+                    if (i < s.k) {
+                        vp[i] = c * x[t] - sn * y[t];
+                        vq[i] = sn * x[t] + c * y[t];
                     }
                 }
-            };
-            rotate(cp, cq, s.r);
-            T* V = base + (F32 ? s.v32_off : s.v_off);
-            rotate(V + (int64_t)p * s.k, V + (int64_t)q * s.k, s.k);
+            }
         }
         if (!grid_barrier(bar, bar + 1, gridDim.x, err)) break;
     }
@@ -285,6 +297,193 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
         for (int i = 0; i < warps; ++i) m = fmaxf(m, wm[i]);
         block_max[blockIdx.x] = m;
     }
+}
+
+// Block one-sided Jacobi sweep for the FP32 preconditioning phase.  The columns of each
+// sector are grouped into blocks of SVD_BW; a round pairs the blocks round-robin (a block
+// left without a partner, or the only block, is processed alone), and one thread block
+// takes one block pair: it forms the Gram matrix G = P^T P of the pair's <= 2 SVD_BW columns
+// (64-row tiles through shared memory), runs one cyclic Jacobi sweep on G (disjoint
+// rotations in parallel; each is the rotation the one-sided method would apply to that
+// column pair), accumulates the rotations in W, and updates the columns of J and V by
+// P <- P W.  One round per block pair instead of one per column pair: ~SVD_BW times fewer
+// grid barriers per sweep, and the work is in small dense products.  Each block writes the
+// largest off-diagonal ratio |G_ab| / sqrt(G_aa G_bb) it saw to block_max.
+constexpr int SVD_BW = 16, SVD_PC = 2 * SVD_BW;
+#ifndef SVD_TR_ROWS
+#define SVD_TR_ROWS 128
+#endif
+constexpr int SVD_TR = SVD_TR_ROWS;
+#ifndef HEFF_SVD_BLOCK
+#define HEFF_SVD_BLOCK 1    // FP32 phase by block sweeps (0: column-pair sweeps)
+#endif
+
+__device__ __forceinline__ int rr_pos(int j, int round, int n) { return j == 0 ? 0 : 1 + (j - 1 + round) % (n - 1); }
+
+#ifndef SVD_BT_THREADS
+#define SVD_BT_THREADS 512
+#endif
+constexpr int SVD_BT = SVD_BT_THREADS;    // threads of a block-pair CTA
+__global__ void __launch_bounds__(SVD_BT) svd_block_sweep_kernel(const SvdSector* __restrict__ secs, int nsec,
+                                                              const int* __restrict__ bpair_off, int nbb_all,
+                                                              float* __restrict__ base, float* __restrict__ block_max,
+                                                              unsigned int* __restrict__ bar, int* __restrict__ err) {
+    __shared__ float tile[SVD_TR][SVD_PC + 1];
+    __shared__ float G[SVD_PC][SVD_PC + 1];
+    __shared__ float W[SVD_PC][SVD_PC + 1];
+    __shared__ float rc[SVD_PC / 2], rs[SVD_PC / 2];
+    __shared__ int col[SVD_PC];
+    __shared__ float bmax;
+    const int tid = threadIdx.x;
+    const int npairs = bpair_off[nsec];
+    if (tid == 0) bmax = 0.f;
+    for (int round = 0; round < nbb_all - 1; ++round) {
+        for (int item = blockIdx.x; item < npairs; item += gridDim.x) {
+            int lo = 0, hi = nsec;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (bpair_off[mid] <= item) lo = mid; else hi = mid;
+            }
+            const SvdSector sc = secs[lo];
+            const int nb = (sc.k + SVD_BW - 1) / SVD_BW, nbb = nb + (nb & 1);
+            if (round >= (nbb > 1 ? nbb - 1 : 1)) continue;                 // block-uniform
+            const int pair = item - bpair_off[lo];
+            int bp = nbb > 1 ? rr_pos(pair, round, nbb) : 0;
+            int bq = nbb > 1 ? rr_pos(nbb - 1 - pair, round, nbb) : nbb;
+            if (bp >= nb) { const int t = bp; bp = bq; bq = t; }              // the real block first
+            if (bp >= nb) continue;
+            const int np = min(SVD_BW, sc.k - bp * SVD_BW);
+            const int nq = bq < nb ? min(SVD_BW, sc.k - bq * SVD_BW) : 0;
+            const int nc = np + nq;
+            if (tid < SVD_PC) col[tid] = tid < np ? bp * SVD_BW + tid : (tid < nc ? bq * SVD_BW + tid - np : -1);
+            float* J = base + sc.j32_off;
+            float* V = base + sc.v32_off;
+            __syncthreads();
+            // 1. G = P^T P: thread t owns entries (a, b) = (t / 16, 2 (t % 16) + u), u < 2
+            constexpr int GE = SVD_PC * SVD_PC / SVD_BT;                   // entries per thread
+            const int ga = tid / (SVD_PC / GE), gb0 = (tid % (SVD_PC / GE)) * GE;
+            float acc[GE];
+#pragma unroll
+            for (int u = 0; u < GE; ++u) acc[u] = 0.f;
+            for (int r0 = 0; r0 < sc.r; r0 += SVD_TR) {
+                for (int e = tid; e < SVD_TR * SVD_PC; e += SVD_BT) {
+                    const int a = e / SVD_TR, rr = e % SVD_TR;
+                    const int cidx = col[a];
+                    tile[rr][a] = (cidx >= 0 && r0 + rr < sc.r) ? J[(int64_t)cidx * sc.r + r0 + rr] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int rr = 0; rr < SVD_TR; ++rr) {
+                    const float x = tile[rr][ga];
+#pragma unroll
+                    for (int u = 0; u < GE; ++u) acc[u] = fmaf(x, tile[rr][gb0 + u], acc[u]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int u = 0; u < GE; ++u) {
+                const int b = gb0 + u;
+                G[ga][b] = (ga < nc && b < nc) ? acc[u] : (ga == b ? 1.f : 0.f);
+                W[ga][b] = ga == b ? 1.f : 0.f;
+            }
+            __syncthreads();
+            // off-diagonal measure before the rotations
+            {
+                float m = 0.f;
+#pragma unroll
+                for (int u = 0; u < GE; ++u) {
+                    const int b = gb0 + u;
+                    if (ga < b && b < nc) {
+                        const float d = sqrtf(G[ga][ga] * G[b][b]);
+                        if (d > 0.f) m = fmaxf(m, fabsf(G[ga][b]) / d);
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&bmax), __float_as_int(m));
+            }
+            // 2. one cyclic Jacobi sweep on G: SVD_PC - 1 rounds of SVD_PC / 2 disjoint rotations
+            for (int jr = 0; jr < SVD_PC - 1; ++jr) {
+                if (tid < SVD_PC / 2) {
+                    int a = rr_pos(tid, jr, SVD_PC), b = rr_pos(SVD_PC - 1 - tid, jr, SVD_PC);
+                    if (a > b) { const int t = a; a = b; b = t; }
+                    const float gab = G[a][b], gaa = G[a][a], gbb = G[b][b];
+                    float c = 1.f, sn = 0.f;
+                    if (gab != 0.f && gaa > 0.f && gbb > 0.f && fabsf(gab) > 1e-7f * sqrtf(gaa * gbb)) {
+                        const double zeta = ((double)gbb - gaa) / (2.0 * gab);
+                        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double cd = 1.0 / sqrt(1.0 + t * t);
+                        c = (float)cd;
+                        sn = (float)(cd * t);
+                    }
+                    rc[tid] = c;
+                    rs[tid] = sn;
+                }
+                __syncthreads();
+                // columns: G <- G R, W <- W R (item: pair j = idx / SVD_PC, row x = idx % SVD_PC)
+                for (int idx = tid; idx < (SVD_PC / 2) * SVD_PC; idx += SVD_BT) {
+                    const int j = idx / SVD_PC, x = idx % SVD_PC;
+                    int a = rr_pos(j, jr, SVD_PC), b = rr_pos(SVD_PC - 1 - j, jr, SVD_PC);
+                    if (a > b) { const int t = a; a = b; b = t; }
+                    const float c = rc[j], sn = rs[j];
+                    if (sn != 0.f) {
+                        const float ga_ = G[x][a], gb_ = G[x][b];
+                        G[x][a] = c * ga_ - sn * gb_;
+                        G[x][b] = sn * ga_ + c * gb_;
+                        const float wa = W[x][a], wb = W[x][b];
+                        W[x][a] = c * wa - sn * wb;
+                        W[x][b] = sn * wa + c * wb;
+                    }
+                }
+                __syncthreads();
+                // rows: G <- R^T G
+                for (int idx = tid; idx < (SVD_PC / 2) * SVD_PC; idx += SVD_BT) {
+                    const int j = idx / SVD_PC, x = idx % SVD_PC;
+                    int a = rr_pos(j, jr, SVD_PC), b = rr_pos(SVD_PC - 1 - j, jr, SVD_PC);
+                    if (a > b) { const int t = a; a = b; b = t; }
+                    const float c = rc[j], sn = rs[j];
+                    if (sn != 0.f) {
+                        const float ga_ = G[a][x], gb_ = G[b][x];
+                        G[a][x] = c * ga_ - sn * gb_;
+                        G[b][x] = sn * ga_ + c * gb_;
+                    }
+                }
+                __syncthreads();
+            }
+            // 3. P <- P W for the columns of J (r rows) and of V (k rows), 64-row tiles
+            for (int pass = 0; pass < 2; ++pass) {
+                float* M = pass == 0 ? J : V;
+                const int rows = pass == 0 ? sc.r : sc.k;
+                for (int r0 = 0; r0 < rows; r0 += SVD_TR) {
+                    for (int e = tid; e < SVD_TR * SVD_PC; e += SVD_BT) {
+                        const int a = e / SVD_TR, rr = e % SVD_TR;
+                        const int cidx = col[a];
+                        tile[rr][a] = (cidx >= 0 && r0 + rr < rows) ? M[(int64_t)cidx * rows + r0 + rr] : 0.f;
+                    }
+                    __syncthreads();
+                    float out[SVD_TR * SVD_PC / SVD_BT];
+#pragma unroll
+                    for (int u = 0; u < SVD_TR * SVD_PC / SVD_BT; ++u) {
+                        const int e = tid + SVD_BT * u, a = e / SVD_TR, rr = e % SVD_TR;
+                        float v = 0.f;
+#pragma unroll 8
+                        for (int bb = 0; bb < SVD_PC; ++bb) v = fmaf(tile[rr][bb], W[bb][a], v);
+                        out[u] = v;
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int u = 0; u < SVD_TR * SVD_PC / SVD_BT; ++u) {
+                        const int e = tid + SVD_BT * u, a = e / SVD_TR, rr = e % SVD_TR;
+                        const int cidx = col[a];
+                        if (cidx >= 0 && r0 + rr < rows) M[(int64_t)cidx * rows + r0 + rr] = out[u];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err)) break;
+    }
+    __syncthreads();
+    if (tid == 0) block_max[blockIdx.x] = bmax;
 }
 
 // largest slot value -> out[0] (one block; fixed order)
@@ -454,7 +653,7 @@ extern "C" int heff_svd_create(const heff_layout* x, heff_svd** out) {
         S->slot_ld = std::max(1, kk / 2);
         S->nslots = (int64_t)nsec * S->slot_ld;
         S->off_slots = ((size_t)S->ws_doubles * sizeof(double) + tab.size() * sizeof(int64_t) + 255) / 256 * 256;
-        S->off_f32 = (S->off_slots + (size_t)(S->nslots + 64 + nsec + 8) * sizeof(float) + 255) / 256 * 256;
+        S->off_f32 = (S->off_slots + (size_t)(S->nslots + 64 + 2 * nsec + 16) * sizeof(float) + 255) / 256 * 256;
         S->ws_bytes = S->off_f32 + (size_t)o32 * sizeof(float) + 1024;
     } catch (const std::bad_alloc&) {
         delete S;
@@ -551,9 +750,52 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
         }
         return HEFF_OK;
     };
+    // FP32 block sweeps: the same convergence test on the block pairs' Gram matrices
+    auto block_sweeps = [&](float* base, float tol, int max_sweeps, int& out) -> int {
+        out = 0;
+        std::vector<int> boff(1, 0);
+        int nbb_all = 2;
+        for (const SvdSector& sc : S->sec) {
+            const int nb = (sc.k + SVD_BW - 1) / SVD_BW, nbb = nb + (nb & 1);
+            boff.push_back(boff.back() + nbb / 2);
+            nbb_all = std::max(nbb_all, nbb);
+        }
+        int* d_boff = d_err + 2;
+        SVD_CK(cudaMemcpyAsync(d_boff, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        int dev = 0, nsm = 0, per_sm = 0;
+        SVD_CK(cudaGetDevice(&dev));
+        SVD_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        SVD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_block_sweep_kernel, SVD_BT, 0));
+        int grid = std::max(1, std::min(nsm * std::max(per_sm, 1), boff.back()));
+        grid = std::min<int>(grid, (int)S->nslots);
+        const SvdSector* secs = S->d_sec;
+        int nsec_i = nsec, nbb_i = nbb_all;
+        float* base_t = base;
+        while (out < max_sweeps) {
+            void* args[] = {(void*)&secs, (void*)&nsec_i, (void*)&d_boff, (void*)&nbb_i, (void*)&base_t,
+                            (void*)&slots, (void*)&d_bar, (void*)&d_err};
+            SVD_CK(cudaLaunchCooperativeKernel((const void*)svd_block_sweep_kernel, dim3(grid), dim3(SVD_BT), args, 0,
+                                               st));
+            svd_offmax_kernel<<<1, 256, 0, st>>>(slots, grid, offmax);
+            heff::count_launches(2);
+            float m = 0.f;
+            int e = 0;
+            SVD_CK(cudaMemcpyAsync(&m, offmax, sizeof(float), cudaMemcpyDeviceToHost, st));
+            SVD_CK(cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SVD_CK(cudaStreamSynchronize(st));
+            if (e) return fail(HEFF_ERR_TIMEOUT, "SVD block sweep: grid barrier timed out");
+            ++out;
+            if (m < tol) break;
+        }
+        return HEFF_OK;
+    };
     int rc;
     // FP32 preconditioning sweeps (to FP32 accuracy of the dot products)
-    if ((rc = sweeps(f32, 1e-5f, 30, S->fp32_sweeps))) return rc;
+    if (HEFF_SVD_BLOCK) {
+        if ((rc = block_sweeps(f32, 1e-5f, 30, S->fp32_sweeps))) return rc;
+    } else if ((rc = sweeps(f32, 1e-5f, 30, S->fp32_sweeps))) {
+        return rc;
+    }
     // V = orthonormalised double(V32), J = J V
     svd_v_to_f64_kernel<<<dim3(128, nsec), 256, 0, st>>>(S->d_sec, f32, ws);
     heff::count_launches(1);
