@@ -300,8 +300,28 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     # Rayleigh-quotient gradients: whole intermediates at m = 1024, streamed at m = 4096
     out["backward"] = backward_timing(dev, stream)
 
-    # the paper's own spin lattice: the 6 x 6 J1-J2 cylinder MPO window (k = 26) at m = 4096
-    wj, lj, bj = make_problem("spin_j1j2_6x6_m4096", 0)
+    # lattice MPO windows at m = 4096: the 6 x 6 J1-J2 cylinder (k = 26, the BASELINE stand-in's
+    # lattice) and the paper's 20 x 10 J1-J2 cylinder (k = 38, uncompressed)
+    for key, name, note in (
+            ("j1j2_6x6_lattice_m4096", "spin_j1j2_6x6_m4096",
+             "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"),
+            ("j1j2_20x10_lattice_m4096", "spin_j1j2_20x10_m4096",
+             "two-site window of the snake-ordered 20x10 J1-J2 (J2 = 0.5) cylinder MPO (the paper's spin "
+             "lattice), binomial sectors")):
+        out[key] = {**single_apply(name, dev, stream, flush), "note": note}
+
+    # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles): the
+    # range-5 chain window and the 4 x 8 Hubbard cylinder window
+    for name in ("electron_m2048", "electron_hubbard_4x8_m2048", "electron_tri_xc6_m2048"):
+        out[name + "_batch32_graph"] = batched_graph(name, 32, dev, stream, flush)
+    return out
+
+
+def single_apply(name, dev, stream, flush):
+    """One BF16x3 apply of a workload with autotuned tiles: CUDA-event mean of 10 (L2 flushed)."""
+    import torch
+    from paper_2007_05540_gb300 import heff
+    wj, lj, bj = make_problem(name, 0)
     Pj = heff.Plan(*lj, bj["W1"], bj["W2"], "bf16x3", "f32")
     dj = {k: torch.from_numpy(np.asarray(v)).to(dev, torch.float32) for k, v in bj.items()}
     wsj = Pj.workspace(dev)
@@ -313,17 +333,11 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     for _ in range(3):
         fj()
     msj = _events_ms(fj, 10, stream, flush)
-    out["j1j2_6x6_lattice_m4096"] = {
-        "applies_per_s": 1000.0 / msj, "ms": msj, "tile_variant": list(tnj), "mpo_k": int(wj.W1.shape[0]),
-        "flops_per_apply": Pj.flops_canonical, "tflops_canonical": Pj.flops_canonical / (msj * 1e-3) / 1e12,
-        "note": "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"}
+    res = {"applies_per_s": 1000.0 / msj, "ms": msj, "tile_variant": list(tnj), "mpo_k": int(wj.W1.shape[0]),
+           "flops_per_apply": Pj.flops_canonical, "tflops_canonical": Pj.flops_canonical / (msj * 1e-3) / 1e12}
     del Pj, dj, wsj, yj
-
-    # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles): the
-    # range-5 chain window and the 4 x 8 Hubbard cylinder window
-    for name in ("electron_m2048", "electron_hubbard_4x8_m2048"):
-        out[name + "_batch32_graph"] = batched_graph(name, 32, dev, stream, flush)
-    return out
+    torch.cuda.synchronize()
+    return res
 
 
 def batched_graph(name, nb, dev, stream, flush):

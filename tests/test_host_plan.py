@@ -61,7 +61,7 @@ def _plan(w, lays, bufs, precision="fp64", io="f64"):
 
 
 @pytest.mark.parametrize("name", ["spin_m24", "spin_m64", "electron_m40", "electron_m96", "spin_j1j2_6x6_m200",
-                                  "electron_hubbard_4x8_m96"])
+                                  "electron_hubbard_4x8_m96", "spin_j1j2_20x10_m200", "electron_tri_xc6_m96"])
 def test_canonical_flops_match_oracle(name):
     w = wl.workload_by_name(name)
     lays, bufs = library_problem(w)
@@ -73,7 +73,7 @@ def test_canonical_flops_match_oracle(name):
 @pytest.mark.parametrize("name,prec", [("spin_m24", "fp64"), ("spin_m64", "fp64"),
                                        ("electron_m40", "fp64"), ("spin_m64", "bf16x3"),
                                        ("electron_m96", "bf16x3"), ("electron_hubbard_4x8_m96", "bf16x3"),
-                                       ("spin_m200", "tf32x3")])
+                                       ("spin_m200", "tf32x3"), ("electron_tri_xc6_m96", "bf16x3")])
 def test_plan_schedule_reproduces_oracle(name, prec):
     w = wl.workload_by_name(name)
     lays, bufs = library_problem(w)

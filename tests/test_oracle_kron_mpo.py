@@ -110,6 +110,19 @@ def test_hubbard_cylinder_mpo_equals_kron(Lx, Ly):
     assert np.abs(Hm - Hk).max() < 1e-12
 
 
+@pytest.mark.parametrize("Lx,Ly", [(3, 2), (2, 3)])
+def test_triangular_hubbard_cylinder_mpo_equals_kron(Lx, Ly):
+    # the paper's electron lattice: triangular, six neighbours per bulk site (x, y and the
+    # (1, 1) diagonal), periodic in y; its MPO must contract to the Kronecker Hamiltonian
+    n = Lx * Ly
+    hops = wl.triangular_hops(Lx, Ly, 1.0)
+    assert len(hops) == (Ly if Ly > 2 else Ly - 1) * Lx + 2 * (Lx - 1) * Ly
+    mpo = wl.hubbard_mpo(n, hops, 8.5)
+    Hm = kron.mpo_to_dense(mpo)
+    Hk = kron.hubbard_hamiltonian(n, hops, 8.5).toarray()
+    assert np.abs(Hm - Hk).max() < 1e-12
+
+
 @pytest.mark.parametrize("which", ["spin", "electron"])
 def test_mpo_charge_rule_and_transpose_symmetry(which):
     w = wl.spin_heff_workload(64, 8, 0) if which == "spin" else wl.electron_heff_workload(96, 3, 6, 24)
@@ -133,3 +146,7 @@ def test_bulk_window_bond_dims():
     # fermion channels each, plus the start and done channels
     win = wl.hubbard_lattice_window()
     assert win["W1"].shape == (18, 4, 4, 18) and win["W2"].shape == (18, 4, 4, 18)
+    # the paper's lattices (uncompressed automaton MPOs): 20 x 10 J1-J2 spins, 6 x 6
+    # triangular Hubbard (XC6)
+    assert wl.lattice_window(20, 10)["W1"].shape == (38, 2, 2, 38)
+    assert wl.triangular_hubbard_window()["W1"].shape == (30, 4, 4, 30)

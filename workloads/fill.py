@@ -14,7 +14,8 @@ import numpy as np
 
 from .sectors import (binomial_sectors, paper_model_sectors, electron_sectors,
                       spin_phys, electron_phys)
-from .mpo import heisenberg_mpo, hubbard_mpo, chain_pairs, cylinder_pairs, cylinder_hops, bulk_window
+from .mpo import (heisenberg_mpo, hubbard_mpo, chain_pairs, cylinder_pairs, cylinder_hops, triangular_hops,
+                  bulk_window)
 
 TAG_L, TAG_R, TAG_X, TAG_SITE = 1, 2, 3, 4
 
@@ -177,6 +178,16 @@ def hubbard_lattice_window(Lx=8, Ly=4, t=1.0, U=8.0):
     return bulk_window(mpo, best)
 
 
+def triangular_hubbard_window(Lx=6, Ly=6, t=1.0, U=8.5):
+    """Two-site window of the snake-ordered Lx x Ly triangular Hubbard cylinder MPO (the
+    paper's electron lattice of Section V, 6 x 6 with U = 8.5), at the first bond triple
+    with the largest total channel count."""
+    n = Lx * Ly
+    mpo = hubbard_mpo(n, triangular_hops(Lx, Ly, t), U)
+    best = max(range(n - 1), key=lambda s: (mpo.bond_dim(s) + mpo.bond_dim(s + 1) + mpo.bond_dim(s + 2), -s))
+    return bulk_window(mpo, best)
+
+
 def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLINGS,
                        name=None, window=None):
     """Spin-1/2 two-site H_eff inputs.
@@ -230,6 +241,15 @@ def workload_by_name(name):
                                                           window=lattice_window()),
         "spin_j1j2_6x6_m200": lambda: spin_heff_workload(200, 10, 7, name="spin_j1j2_6x6_m200",
                                                          window=lattice_window()),
+        "spin_j1j2_20x10_m4096": lambda: spin_heff_workload(4096, 40, 0, name="spin_j1j2_20x10_m4096",
+                                                            window=lattice_window(20, 10)),
+        "spin_j1j2_20x10_m200": lambda: spin_heff_workload(200, 10, 7, name="spin_j1j2_20x10_m200",
+                                                           window=lattice_window(20, 10)),
+        "electron_tri_xc6_m2048": lambda: electron_heff_workload(2048, 0, name="electron_tri_xc6_m2048",
+                                                                 window=triangular_hubbard_window()),
+        "electron_tri_xc6_m96": lambda: electron_heff_workload(96, 3, n_center=6, max_block=24,
+                                                               name="electron_tri_xc6_m96",
+                                                               window=triangular_hubbard_window()),
         "electron_m2048": lambda: electron_heff_workload(2048, 0, name="electron_m2048"),
         "electron_hubbard_4x8_m2048": lambda: electron_heff_workload(2048, 0, name="electron_hubbard_4x8_m2048",
                                                                      window=hubbard_lattice_window()),

@@ -242,6 +242,37 @@ def cylinder_hops(Lx, Ly, t=1.0):
     return cylinder_pairs(Lx, Ly, t, 0.0)
 
 
+def triangular_hops(Lx, Ly, t=1.0):
+    """Nearest-neighbour hops ``(i, j, t)`` of a triangular lattice on a snake-ordered
+    cylinder (open in x, periodic in y): the square-grid bonds along x and y plus the
+    (1, 1) diagonal, six neighbours per bulk site.  Duplicate pairs (Ly <= 2) are merged."""
+    acc = {}
+
+    def add(p, q):
+        if p == q:
+            return
+        key = (min(p, q), max(p, q))
+        acc[key] = acc.get(key, 0.0) + t
+
+    seen = set()
+    for x in range(Lx):
+        for y in range(Ly):
+            nbrs = []
+            if Ly > 1:
+                nbrs.append((x, (y + 1) % Ly))
+            if x + 1 < Lx:
+                nbrs.append((x + 1, y))
+                if Ly > 1:
+                    nbrs.append((x + 1, (y + 1) % Ly))
+            for xx, yy in nbrs:
+                geo = (min((x, y), (xx, yy)), max((x, y), (xx, yy)))
+                if geo in seen:
+                    continue
+                seen.add(geo)
+                add(snake_index(x, y, Ly), snake_index(xx, yy, Ly))
+    return [(p, q, v) for (p, q), v in sorted(acc.items())]
+
+
 def heisenberg_mpo(n_sites, pairs, field_z=0.0):
     """Heisenberg MPO for weighted pairs (optionally a uniform Sz field)."""
     from .sectors import spin_phys
