@@ -300,8 +300,8 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     # Rayleigh-quotient gradients: whole intermediates at m = 1024, streamed at m = 4096
     out["backward"] = backward_timing(dev, stream)
 
-    # lattice MPO windows at m = 4096: the 6 x 6 J1-J2 cylinder (k = 26, the BASELINE stand-in's
-    # lattice) and the paper's 20 x 10 J1-J2 cylinder (k = 38, uncompressed)
+    # lattice MPO windows at m = 4096: the 6 x 6 J1-J2 cylinder (k = 26) and the paper's
+    # 20 x 10 J1-J2 cylinder (k = 38, uncompressed)
     for key, name, note in (
             ("j1j2_6x6_lattice_m4096", "spin_j1j2_6x6_m4096",
              "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"),

@@ -8,11 +8,12 @@
 // Every K block does three MMAs, A_hi.B_hi + A_hi.B_lo + A_lo.B_hi, accumulated in FP32
 // in tensor memory (the "3-product" split: error ~ 2^-16 (bf16) / 2^-22 (tf32) relative).
 //
-// Persistent kernel, one CTA (6 warps) per SM, static round-robin over the task list
-// (which the planner sorts longest-first):
+// Persistent kernel, one CTA per SM (10 warps in BF16x3, 6 in TF32x3), static round-robin
+// over the task list (which the planner orders as a longest-processing-time schedule):
 //   warp 0      one thread issues the TMA loads of a STAGES-deep shared-memory ring
 //   warp 1      allocates TMEM (2 x TN columns); one thread issues the MMAs
-//   warps 2..5  epilogue: TMEM -> registers -> global (T as hi/lo planes, or y)
+//   warps 2..   epilogue (8 warps in BF16x3, two per TMEM lane quarter on alternate
+//               32-column chunks; 4 in TF32x3): TMEM -> registers -> global
 // Accumulators are double buffered so a tile's epilogue overlaps the next tile's MMAs.
 // Long contractions (GEMM 2) are accumulated in chunks of kchunk K blocks: each chunk
 // starts a fresh accumulator and the epilogue adds the chunks into y in a fixed order with
