@@ -30,8 +30,8 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1", 256): (470.665216e6 + 286.232064e6, "4afd3b00d7ea9b83"),
-    ("spin_m4096", "bf16x3", "gemm2", 256): (805.746432e6 + 44.779776e6, "4afd3b00d7ea9b83"),
+    ("spin_m4096", "bf16x3", "gemm1", 256): (470.841088e6 + 286.662656e6, "a907a9e3a1579bb8"),
+    ("spin_m4096", "bf16x3", "gemm2", 256): (809.171968e6 + 45.061120e6, "a907a9e3a1579bb8"),
 }
 
 
