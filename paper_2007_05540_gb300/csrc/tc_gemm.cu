@@ -37,6 +37,11 @@
 
 #include "internal.h"
 
+// work order of batched launches: 1 = the batch entries of a task consecutively
+#ifndef HEFF_BATCH_INNER
+#define HEFF_BATCH_INNER 1
+#endif
+
 namespace heff {
 namespace {
 
@@ -329,6 +334,13 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     const long cid = (long)(blockIdx.x / CL), ncl = (long)(gridDim.x / CL);
     const long nent = g.ntasks / CL;                                 // entries per batch
     const long total = nent * g.nbatch;
+    // work item gi -> (entry, batch entry).  Batch-inner order: the batch entries of one
+    // task follow each other, so the CTAs that run them at the same time share its operand
+    // tiles (the A tile of GEMM 1, the B tile of GEMM 2) through L2.  With one batch entry
+    // both orders are the planner's order.
+    const long nbl = g.nbatch;
+    auto ent = [&](long gi) { return HEFF_BATCH_INNER ? gi / nbl : gi % nent; };
+    auto bat = [&](long gi) { return (int)(HEFF_BATCH_INNER ? gi % nbl : gi / nent); };
     constexpr int KB = SWZ / (PREC == HEFF_PREC_BF16X3 ? 2 : 4);   // elements per K block
     constexpr int KSUB = SWZ / 32;                                   // MMAs (32-byte K) per block
 
@@ -343,11 +355,11 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         bool ok = true;
         // the next task and the next segment are loaded one step ahead, so their latency
         // overlaps with the current loads instead of draining the ring
-        GemmTask tn = cid < total ? g.tasks[CL * (cid % nent) + rank] : GemmTask{};
+        GemmTask tn = cid < total ? g.tasks[CL * ent(cid) + rank] : GemmTask{};
         for (long gi = cid; gi < total && ok; gi += ncl) {
             const GemmTask t = tn;
-            if (gi + ncl < total) tn = g.tasks[CL * ((gi + ncl) % nent) + rank];
-            const int b = g.b0 + (int)(gi / nent);
+            if (gi + ncl < total) tn = g.tasks[CL * ent(gi + ncl) + rank];
+            const int b = g.b0 + bat(gi);
             const int ah = (int)(t.a_row + b * g.a_batch_rows), al = (int)(ah + g.a_plane_rows);
             const int bh = (int)(t.b_row + b * g.b_batch_rows), bl = (int)(bh + g.b_plane_rows);
             const int ia = t.m <= 64 ? 0 : 1, ib = t.n <= 64 ? 0 : (t.n <= 128 ? 1 : 2);
@@ -405,10 +417,10 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         constexpr uint64_t O_ALO = S::A_BYTES >> 4, O_BHI = (2 * S::A_BYTES) >> 4;
         constexpr uint64_t O_BLO = (2 * S::A_BYTES + S::B_BYTES) >> 4, O_STAGE = S::STAGE_BYTES >> 4;
         bool ok = true;
-        GemmTask tn = cid < total ? g.tasks[CL * (cid % nent) + rank] : GemmTask{};
+        GemmTask tn = cid < total ? g.tasks[CL * ent(cid) + rank] : GemmTask{};
         for (long gi = cid; gi < total && ok; gi += ncl) {
             const GemmTask t = tn;
-            if (gi + ncl < total) tn = g.tasks[CL * ((gi + ncl) % nent) + rank];
+            if (gi + ncl < total) tn = g.tasks[CL * ent(gi + ncl) + rank];
             if (t.seg_count == 0) {            // nothing to contract: the epilogue writes zeros
                 const uint32_t acc = ccount & 1, use = ccount >> 1;
                 if (!(ok = mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag, g.err))) break;
@@ -484,8 +496,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         uint32_t ccount = 0;
         bool live = true;
         for (long gi = cid; gi < total && live; gi += ncl) {
-            const GemmTask t = g.tasks[CL * (gi % nent) + rank];
-            const int brel = (int)(gi / nent), b = g.b0 + brel;
+            const GemmTask t = g.tasks[CL * ent(gi) + rank];
+            const int brel = bat(gi), b = g.b0 + brel;
             const int nch = (t.seg_count > 0 && CH != 0x7fffffff) ? (t.ktotal / KB + CH - 1) / CH : 1;
           for (int ch = 0; ch < nch; ++ch) {
             const uint32_t acc = ccount & 1, use = ccount >> 1;
