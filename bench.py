@@ -30,8 +30,8 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1", 256): (470.841088e6 + 286.662656e6, "a907a9e3a1579bb8"),
-    ("spin_m4096", "bf16x3", "gemm2", 256): (809.171968e6 + 45.061120e6, "a907a9e3a1579bb8"),
+    ("spin_m4096", "bf16x3", "gemm1", 256): (469.884160e6 + 286.141184e6, "6c8b25fec2408dfd"),
+    ("spin_m4096", "bf16x3", "gemm2", 256): (806.004736e6 + 45.000192e6, "6c8b25fec2408dfd"),
 }
 
 
