@@ -138,6 +138,24 @@ def test_mpo_charge_rule_and_transpose_symmetry(which):
     assert np.abs(W1 - W1t).max() == 0.0
 
 
+@pytest.mark.parametrize("name", ["spin_j1j2_6x6_m200", "spin_j1j2_20x10_m200", "electron_hubbard_4x8_m96",
+                                  "electron_tri_xc6_m96"])
+def test_lattice_windows_charge_rule_and_hermiticity(name):
+    # the lattice MPO windows obey the charge rule of every nonzero entry and are Hermitian
+    # under the channel transposition map, as the chain windows are
+    w = wl.workload_by_name(name)
+    for W, ql, qr in [(w.W1, w.ql, w.qm), (w.W2, w.qm, w.qr)]:
+        for wl_, t, s, wr in np.argwhere(W != 0):
+            assert np.array_equal(ql[wl_] + w.phys[t] - w.phys[s], qr[wr])
+    from workloads.fill import lattice_window
+    win = {"spin_j1j2_6x6_m200": lambda: lattice_window(), "spin_j1j2_20x10_m200": lambda: lattice_window(20, 10),
+           "electron_hubbard_4x8_m96": wl.hubbard_lattice_window,
+           "electron_tri_xc6_m96": wl.triangular_hubbard_window}[name]()
+    for W, c0, c1 in [(win["W1"], win["conj_l"], win["conj_m"]), (win["W2"], win["conj_m"], win["conj_r"])]:
+        Wt = W[c0][:, :, :, c1].transpose(0, 2, 1, 3)
+        assert np.abs(W - Wt).max() == 0.0
+
+
 def test_bulk_window_bond_dims():
     from workloads.fill import spin_window, electron_window
     assert spin_window()["W1"].shape == (14, 2, 2, 14)
