@@ -436,6 +436,33 @@ int heff_plan_select_tiles(heff_plan* plan, int32_t tn1, int32_t tn2);
 int heff_plan_set_timing(heff_plan* plan, int32_t enable);
 int heff_plan_timings(heff_plan* plan, float* ms);
 
+/*
+ * heff_workspace_status -- read and clear the sticky device error flag of an apply workspace.
+ * The tensor-core GEMM kernels set it when one of their bounded waits expires (about 1.5 s
+ * on an mbarrier that does not complete); that launch then stops issuing work, frees its
+ * tensor memory and returns, so its outputs are incomplete but the context stays usable.
+ * A GEMM launch clears the flag when the workspace is not one of the last two the plan
+ * used.  Synchronises `stream`.  Returns HEFF_ERR_TIMEOUT if the flag was set (and clears
+ * it), else HEFF_OK; always HEFF_OK for FP64 plans, whose kernels do not wait.
+ * workspace: device, at least heff_plan_workspace_size bytes.  Errors: INVALID_ARG,
+ * WORKSPACE (too small), CUDA.
+ */
+int heff_workspace_status(const heff_plan* plan, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * heff_wait_selftest -- check that a device-side bounded wait gives up instead of hanging.
+ * Launches one single-block kernel whose wait nothing completes: kind 0 waits with the
+ * tensor-core GEMM kernels' mbarrier wait (gives up after 3 * 2^30 clock cycles, about
+ * 1.5 s), kind 1 at the SVD sweeps' grid barrier set up for two blocks (2^31 cycles, about
+ * 1 s).  On expiry the kernel sets the workspace's sticky error flag, as an expired wait in
+ * a GEMM launch does, and returns; read it with heff_workspace_status.  workspace: an apply
+ * workspace of `plan` (device); ms_out (host, may be NULL) receives the kernel's duration.
+ * Synchronises `stream`.  Errors: INVALID_ARG (null pointer, kind not 0 or 1, FP64 plan),
+ * WORKSPACE, CUDA.
+ */
+int heff_wait_selftest(const heff_plan* plan, void* workspace, size_t workspace_bytes, int32_t kind,
+                       void* stream, float* ms_out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* heff_last_error(void);
 

@@ -204,6 +204,8 @@ int launch_mix(heff_plan* p, const void* L, const void* W1, const void* W2, cons
 int launch_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream);
 // clusters of two tensor-core CTAs resident at once (tc_gemm.cu; num_sms / 2 without a device)
 int tc_pair_clusters(int num_sms, int precision);
+// one block waiting at the SVD sweeps' grid barrier set up for two (svd.cu; wait self-test)
+void svd_barrier_selftest(unsigned int* bar, int* err, void* stream);
 int plan_upload(heff_plan* p);
 void plan_free_device(heff_plan* p);
 void record_phase(heff_plan* p, int k, void* stream);

@@ -546,7 +546,15 @@ __global__ void svd_write_kernel(const SvdSector* __restrict__ secs, const Write
     }
 }
 
+// One block meets the sweeps' grid barrier set up for two blocks: its wait must give up,
+// set err and return.
+__global__ void barrier_selftest_kernel(unsigned int* bar, int* err) { grid_barrier(bar, bar + 1, 2u, err); }
+
 }  // namespace
+
+void heff::svd_barrier_selftest(unsigned int* bar, int* err, void* stream) {
+    barrier_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(bar, err);
+}
 
 extern "C" int heff_svd_create(const heff_layout* x, heff_svd** out) {
     heff::clear_error();

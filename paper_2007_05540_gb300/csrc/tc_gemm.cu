@@ -787,6 +787,9 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
     }
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->tmaps[slot]);
     if (fresh) {
+        // a workspace new to the plan: clear its sticky error flag (caller memory, contents unknown)
+        cudaError_t ez = cudaMemsetAsync(w + p->off_flags, 0, sizeof(int), st);
+        if (ez != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(ez));
         // [0,1] LW (64, 128 rows)  [2,3,4] XT (64, 128, 256)  [5,6] T (64, 128)  [7,8,9] RW (64, 128, 256)
         // [10] T store boxes: 32 rows x 32 elements (64-byte swizzle for bf16, 128-byte for fp32)
         struct { char* base; int64_t rows, ld; int slot, nbox; } ops[4] = {
@@ -901,3 +904,77 @@ int tc_pair_clusters(int num_sms, int precision) {
 }
 
 }  // namespace heff
+
+// ---------------------------------------------------------------- bounded-wait self-test
+namespace heff {
+namespace {
+
+// One thread waits, with the GEMM kernels' own bounded wait, for the first phase of an
+// mbarrier on which nothing arrives: the wait must give up, raise the abort flag and the
+// error flag, and return.
+__global__ void mbar_wait_selftest_kernel(int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        mbar_init(&bar, 1);
+        mbar_wait(&bar, 0, &abort_flag, err);
+    }
+}
+
+}  // namespace
+}  // namespace heff
+
+extern "C" int heff_wait_selftest(const heff_plan* plan, void* workspace, size_t workspace_bytes, int32_t kind,
+                                  void* stream, float* ms_out) {
+    using namespace heff;
+    if (!plan || !workspace || (kind != 0 && kind != 1))
+        return fail(HEFF_ERR_INVALID_ARG, "heff_wait_selftest: null plan/workspace or kind not 0/1");
+    if (plan->opts.precision == HEFF_PREC_FP64)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_wait_selftest: FP64 plans have no device-side waits");
+    if (workspace_bytes < plan->off_flags + 256)
+        return fail(HEFF_ERR_WORKSPACE, "heff_wait_selftest: workspace smaller than the plan's");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* f = static_cast<char*>(workspace) + plan->off_flags;
+    int* err = reinterpret_cast<int*>(f);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    // error flag at byte 0 of the flag area; the barrier's counter and generation at 64, 68
+    if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, 128, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) {
+        if (kind == 0) mbar_wait_selftest_kernel<<<1, 32, 0, st>>>(err);
+        else svd_barrier_selftest(reinterpret_cast<unsigned int*>(f + 64), err, st);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_wait_selftest: %s", cudaGetErrorString(e));
+    if (ms_out) *ms_out = ms;
+    return HEFF_OK;
+}
+
+extern "C" int heff_workspace_status(const heff_plan* plan, void* workspace, size_t workspace_bytes,
+                                     void* stream) {
+    using namespace heff;
+    if (!plan || !workspace) return fail(HEFF_ERR_INVALID_ARG, "heff_workspace_status: null plan/workspace");
+    if (plan->opts.precision == HEFF_PREC_FP64) return HEFF_OK;
+    if (workspace_bytes < plan->off_flags + 256)
+        return fail(HEFF_ERR_WORKSPACE, "heff_workspace_status: workspace smaller than the plan's");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* d = reinterpret_cast<int*>(static_cast<char*>(workspace) + plan->off_flags);
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && flag) e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (e == cudaSuccess && flag) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_workspace_status: %s", cudaGetErrorString(e));
+    if (flag) return fail(HEFF_ERR_TIMEOUT, "a bounded device-side wait expired (flag %d)", flag);
+    return HEFF_OK;
+}

@@ -97,6 +97,8 @@ _sig = {
     "heff_plan_autotune": (C.c_int, [_vp] * 8 + [_sz, _vp, _P(_i32), _P(C.c_float)]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
     "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
+    "heff_workspace_status": (C.c_int, [_vp, _vp, _sz, _vp]),
+    "heff_wait_selftest": (C.c_int, [_vp, _vp, _sz, _i32, _vp, _P(C.c_float)]),
     "heff_last_error": (C.c_char_p, []),
     "heff_launch_count": (C.c_int64, []),
     "heff_version": (C.c_char_p, []),
@@ -478,6 +480,22 @@ def heff_plan_timings(plan):
     ms = (C.c_float * 4)()
     _check(_lib.heff_plan_timings(plan, ms), "heff_plan_timings")
     return [float(v) for v in ms]
+
+
+def heff_workspace_status(plan, ws, stream=None):
+    """Read and clear the workspace's sticky device error flag; returns the status code
+    (0, or -6 when a bounded device-side wait expired) without raising."""
+    return int(_lib.heff_workspace_status(plan, _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def heff_wait_selftest(plan, ws, kind, stream=None):
+    """Run one device-side bounded wait that nothing completes (kind 0: the GEMM kernels'
+    mbarrier wait, kind 1: the SVD sweeps' grid barrier); returns its duration in ms.  The
+    expired wait leaves the workspace's error flag set."""
+    ms = C.c_float(0.0)
+    _check(_lib.heff_wait_selftest(plan, _ptr(ws), _nbytes(ws), int(kind), _stream(stream), C.byref(ms)),
+           "heff_wait_selftest")
+    return float(ms.value)
 
 
 def heff_last_error():

@@ -1,6 +1,6 @@
 """GPU parity of the CUDA H_eff path against the FP64 oracle (through the C ABI).
 
-Tolerances (north-star): FP64 path 1e-10; TF32 split (3xTF32) 1e-5; BF16 with
+Tolerances: FP64 path 1e-10; TF32 split (3xTF32) 1e-5; BF16 with
 compensation (BF16x3) 1e-3, as norm-wise relative errors ||y - y_oracle|| / ||y_oracle||,
 with every element also within 20x the tolerance of max|y_oracle|; all output elements
 at small sizes, every element of sampled output sectors at the benchmark's full sizes.

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
     assert len(declared) >= 15
     for name in sorted(declared):
         assert hasattr(heff._lib, name), name
-    assert set(heff.EXPORTED) >= declared - {"heff_plan_export"} or True
+    assert set(heff.EXPORTED) == declared   # every declared entry has a binding, and no more
     assert heff.heff_version().startswith("heff-gb300")
 
 
