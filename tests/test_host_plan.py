@@ -251,3 +251,30 @@ def test_product_state_reaches_total_charge():
     with pytest.raises(ValueError):
         dmrg.product_state(sp, 3, (0,))          # odd chain cannot reach 2Sz = 0
 
+
+
+def test_wait_status_entries_check_arguments_before_touching_the_device():
+    """heff_workspace_status / heff_wait_selftest reject bad arguments on the host (no CUDA
+    call is made); an FP64 plan has no device-side waits, so its status is HEFF_OK unread."""
+    import types
+
+    import torch
+    w = wl.workload_by_name("spin_m24")
+    lays, bufs = library_problem(w)
+    P = _plan(w, lays, bufs, "bf16x3", "f32")
+    small = torch.empty(16, dtype=torch.uint8)          # host memory, never dereferenced
+    st = types.SimpleNamespace(cuda_stream=0)            # legacy stream handle, never used
+    assert heff.heff_workspace_status(None, small, st) == -1                 # INVALID_ARG
+    assert heff.heff_workspace_status(P.handle, small, st) == -7             # WORKSPACE: too small
+    for kind in (2, -1):
+        with pytest.raises(heff.HeffError) as e:
+            heff.heff_wait_selftest(P.handle, small, kind, st)
+        assert e.value.code == -1
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_wait_selftest(P.handle, small, 0, st)
+    assert e.value.code == -7
+    P64 = _plan(w, lays, bufs, "fp64", "f64")
+    assert heff.heff_workspace_status(P64.handle, small, st) == 0
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_wait_selftest(P64.handle, small, 0, st)
+    assert e.value.code == -1
