@@ -27,23 +27,32 @@ import numpy as np  # noqa: E402
 
 METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 
-# DRAM bytes (read + write) per launch from the ncu capture summarised in
-# profiles/tc_gemm_bf16x3_spin_m4096.md, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {
-    ("spin_m4096", "bf16x3", "gemm1", 256): (469.884160e6 + 286.141184e6, "6c8b25fec2408dfd"),
-    ("spin_m4096", "bf16x3", "gemm2", 256): (806.004736e6 + 45.000192e6, "6c8b25fec2408dfd"),
-}
+# ncu figures per launch of the four kernels of one apply (DRAM bytes read + written, and
+# the tensor pipe's active cycles in % of peak for the GEMMs), keyed by (workload,
+# precision, kernel, tile variant), from the committed ncu profile summary of the apply;
+# valid only while the device code they were measured on is unchanged (hash below).
+NCU_FIGURES = {}
+NCU_SRC_SHA = ""
 
 
 def _src_sha():
-    """Hash of the device code of tc_gemm.cu (everything before its host-side section), the
-    code the ncu traffic figures were measured on."""
+    """Hash of the device code of tc_gemm.cu and apply.cu (each file up to its host-side
+    section), the code the ncu figures were measured on."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2007_05540_gb300", "csrc", "tc_gemm.cu")
-    with open(p, "rb") as f:
-        txt = f.read()
-    cut = txt.find(b"// ---------------------------------------------------------------- host side")
-    return hashlib.sha256(txt[:cut] if cut >= 0 else txt).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name, mark in (("tc_gemm.cu", b"// ---------------------------------------------------------------- host side"),
+                       ("apply.cu", b"// ------------------------------------------------------------------ host side")):
+        with open(os.path.join(ROOT, "paper_2007_05540_gb300", "csrc", name), "rb") as f:
+            txt = f.read()
+        cut = txt.find(mark)
+        h.update(txt[:cut] if cut >= 0 else txt)
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(lays, io_bytes):
+    """Bytes one apply must move at least: read L, W1, W2, R and x, write y (io dtype)."""
+    Ll, W1l, W2l, Rl, xl = lays
+    return io_bytes * (Ll.nelem + W1l.nelem + W2l.nelem + Rl.nelem + 2 * xl.nelem)
 
 
 def parse():
@@ -164,8 +173,23 @@ def make_problem(name, batch):
     return w, lays, bufs
 
 
-def cpu_baseline(name, seconds, batch=0):
-    """The FP64 oracle (as it stands) on the host cores, on sampled output sectors."""
+def cpu_baseline(name, seconds, batch=0, threads=None):
+    """The FP64 oracle (as it stands) on the host cores, on sampled output sectors.
+
+    threads=None: all cores (NumPy's BLAS threads); threads=1: a child process with every
+    BLAS thread pool limited to one thread (the pools read their size at start-up)."""
+    if threads is not None:
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+        code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.cpu_baseline(%r, %r, %r)))" % (ROOT, name, float(seconds), int(batch)))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            return {"error": r.stderr[-300:]}
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        out["cores"] = int(threads)
+        return out
     import workloads as wl
     from oracle import heff as oh
     w = wl.workload_by_name(name)
@@ -638,20 +662,47 @@ def run_ours(args):
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": 1.25,
                 "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
                 "achieved": useful / (g_ms[dom] * 1e-3) / 1e12}
+        roof["frac"] = roof["achieved"] / roof["peak"]
     else:
+        # frac counts the method's useful flops (valid rows, columns and contraction of the
+        # kernel's tiles); the split issues three tensor-core products per useful
+        # multiply-add, so the tensor pipe is busy about three times that (tensor_pipe_frac)
         passes = 3
         base = peaks["bf16_tflops"] * (1.0 if prec == "bf16x3" else 0.5)
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": base,
                 "peak_source": ("bf16 burst, " if prec == "bf16x3" else "bf16 burst x 0.5 (nominal tf32/bf16), ")
                 + peak_src,
-                "achieved": passes * useful / (g_ms[dom] * 1e-3) / 1e12,
-                "note": f"{passes} tensor-core products per useful multiply-add (hi/lo split)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+                "achieved": useful / (g_ms[dom] * 1e-3) / 1e12}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["tensor_pipe_frac"] = passes * roof["frac"]
+        roof["note"] = (f"achieved/frac: useful flops of the kernel's tiles; tensor_pipe_frac: the {passes} "
+                        "tensor-core products per useful multiply-add of the hi/lo split")
+    # the whole apply: canonical flops of the method per step against the same peak
+    roof["apply_frac"] = canonical / (ms * 1e-3) / 1e12 / roof["peak"]
     roof["kernel"] = dom
-    tr = NCU_TRAFFIC.get((args.workload, prec, dom, int(tile_n[0 if dom == "gemm1" else 1])))
-    roof["traffic"] = tr[0] if tr and tr[1] == _src_sha() else None
-    roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     roof["launch_ms"] = g_ms[dom]
+    sha = _src_sha()
+    tiles = {"gemm1": int(tile_n[0]), "gemm2": int(tile_n[1]), "mix": 0, "pack": 0}
+    fig = {k: NCU_FIGURES.get((args.workload, prec, k, tiles[k])) for k in tiles}
+    fresh = sha == NCU_SRC_SHA
+    roof["traffic"] = fig[dom]["dram_bytes"] if fresh and fig[dom] else None
+    roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
+    alg = algorithmic_bytes(lays, 8 if io == "f64" else 4)
+    roof["algorithmic_bytes_per_apply"] = alg
+    if fresh and all(fig.values()):
+        roof["traffic_ratio"] = sum(f["dram_bytes"] for f in fig.values()) / alg
+        roof["ncu_tensor_pipe_pct"] = {k: fig[k].get("tensor_pct") for k in ("gemm1", "gemm2")}
+    else:
+        roof["traffic_ratio"] = None
+        roof["ncu_tensor_pipe_pct"] = None
+
+    # the apply an eigensolver pays per Krylov step: heff_apply_prepared (pack + GEMMs) with
+    # the operators prepared once
+    heff.heff_prepare(plan.handle, d["L"], d["W1"], d["W2"], d["R"], ws, stream)
+    for _ in range(3):
+        heff.heff_apply_prepared(plan.handle, d["x"], y, ws, stream)
+    prep_ms = max_over_ranks(_events_ms(lambda: heff.heff_apply_prepared(plan.handle, d["x"], y, ws, stream),
+                                        max(args.steps, 10), stream, flush), dev)
 
     out = {
         "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
@@ -667,6 +718,10 @@ def run_ours(args):
         "tflops_canonical": canonical * value / 1e12,
         "flops_per_apply": canonical,
         "phase_ms": {"prepare": phases[0], "pack": phases[1], "gemm1": phases[2], "gemm2": phases[3]},
+        "apply_prepared": {"value": world * 1000.0 / prep_ms, "unit": "applies/s", "ms": prep_ms,
+                           "tflops_canonical": canonical / (prep_ms * 1e-3) / 1e12,
+                           "note": "heff_apply_prepared (pack + GEMM 1 + GEMM 2; operators prepared once), "
+                                   "the matvec an eigensolver repeats"},
         "wall_s": wall,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "applies/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -678,6 +733,7 @@ def run_ours(args):
         out["extras"] = extras(args, w, lays, bufs, dev, stream, flush, value)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+        out["cpu_baseline"]["one_thread"] = cpu_baseline(args.workload, args.cpu_seconds / 2, threads=1)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -396,8 +396,11 @@ int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1, const voi
  *   HEFF_TILE_256       one CTA per 128 x 256 output tile (the default)
  *   HEFF_TILE_128       one CTA per 128 x 128 output tile
  *   HEFF_TILE_PAIR_256  128 x 256 tiles in pairs that share their B rows and K segments, run
- *                       by the two CTAs of a cluster: each CTA loads half of the B box,
- *                       multicast to both, so B is read once per pair
+ *                       by the two CTAs of a cluster as one M = 256 tile (tcgen05 pair MMAs,
+ *                       cta_group::2): each CTA loads its own 128 A rows and its own half of
+ *                       the B rows into its own shared memory, and both CTAs' loads complete
+ *                       on the even CTA's barrier, so B is read once per pair (no multicast
+ *                       load is issued)
  * Results are bitwise identical across variants (a tile's K order does not depend on them).
  */
 #define HEFF_TILE_256 256

@@ -12,7 +12,7 @@ import numpy as np
 from .blocks import BlockTensor
 from .heff import heff_apply
 from .env import left_boundary, right_boundary, extend_left, extend_right
-from .mps import random_mps, right_orthonormalize, two_site
+from .mps import random_mps, product_mps, right_orthonormalize, two_site
 from .eig import lanczos, davidson
 from .svd import svd_split
 
@@ -38,18 +38,29 @@ class _Shape:
 
 
 def dmrg(mpo, total, m_schedule, solver="lanczos", n_iter=30, cutoff=1e-12,
-         seed=0, davidson_vecs=2, m_init=8):
+         seed=0, davidson_vecs=2, m_init=8, states=None):
     """Run sweeps; ``m_schedule`` lists the bond cap of each full sweep.
+
+    The start is a random MPS with bond cap ``m_init`` brought to right-canonical form,
+    or, when ``states`` lists one local state per site (charges adding up to ``total``),
+    that product state (bond dimension 1, already canonical); two-site updates grow the
+    bonds from there.
 
     Returns a dict with the energy after every step, per-sweep energies and
     the final MPS.
     """
     n = mpo.n_sites
     nq = mpo.phys.shape[1]
-    sites = random_mps(mpo.phys, n, total, m_init, seed)
-    for k in range(n - 1, 0, -1):
-        sites = right_orthonormalize(sites, k)
-    sites[0].scale(1.0 / sites[0].norm())
+    if states is not None:
+        sites = product_mps(mpo.phys, states)
+        qt = sites[-1].indices[2].charges[0]
+        if not np.array_equal(qt, np.asarray(total).reshape(-1)):
+            raise ValueError(f"product state has total charge {tuple(qt)}, not {tuple(total)}")
+    else:
+        sites = random_mps(mpo.phys, n, total, m_init, seed)
+        for k in range(n - 1, 0, -1):
+            sites = right_orthonormalize(sites, k)
+        sites[0].scale(1.0 / sites[0].norm())
     Ls = [None] * (n + 1)
     Rs = [None] * (n + 2)
     Ls[0] = left_boundary(nq)

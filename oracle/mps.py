@@ -65,6 +65,26 @@ def random_mps(phys, n, total, m, seed):
     return sites
 
 
+def product_mps(phys, states):
+    """MPS of the product state with local state ``states[k]`` on site k (Section II-B: a
+    bond dimension 1 MPS): bond b has the single sector of the charge of sites < b, and
+    every site holds one 1 x 1 x 1 block equal to 1.  It is left- and right-canonical."""
+    phys = np.asarray(phys, dtype=np.int64)
+    nq = phys.shape[1]
+    phys_ix = Index(phys, np.ones(len(phys), dtype=np.int64))
+    q = np.zeros(nq, dtype=np.int64)
+    bonds = [Index(q.reshape(1, nq).copy(), [1])]
+    for st in states:
+        q = q + phys[int(st)]
+        bonds.append(Index(q.reshape(1, nq).copy(), [1]))
+    sites = []
+    for k, st in enumerate(states):
+        t = BlockTensor([bonds[k], phys_ix, bonds[k + 1]], (1, 1, -1))
+        t.blocks[(0, int(st), 0)] = np.ones((1, 1, 1))
+        sites.append(t)
+    return sites
+
+
 def _rows_by_right(T, j):
     """Stack the blocks (i, s, j) into one matrix [sum m_i x m_j]."""
     parts = [(key, blk[:, 0, :]) for key, blk in sorted(T.blocks.items()) if key[2] == j]

@@ -210,11 +210,13 @@ class GpuDMRG:
 
 
 def dmrg(mpo, total, m_schedule, precision="fp64", n_iter=20, cutoff=1e-12, device="cuda", solver="lanczos",
-         davidson_vecs=2):
+         davidson_vecs=2, states=None):
     """Run one full sweep per entry of ``m_schedule`` (the bond cap of that sweep); the
     eigensolver is Lanczos (n_iter steps) or Algorithm 1's Davidson (davidson_vecs vectors).
+    ``states`` (one local state per site) chooses the product state the sweeps start from.
     Returns dict(sweep_energies, energy, refined_energy, bond_dims, max_discarded)."""
-    run = GpuDMRG(mpo, total, precision, n_iter, cutoff, device=device, solver=solver, davidson_vecs=davidson_vecs)
+    run = GpuDMRG(mpo, total, precision, n_iter, cutoff, states=states, device=device, solver=solver,
+                  davidson_vecs=davidson_vecs)
     for m in m_schedule:
         run.sweep(int(m))
     out = {"sweep_energies": list(run.energies), "energy": run.energies[-1], "bond_dims": run.bond_dims(),

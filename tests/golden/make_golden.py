@@ -1,9 +1,16 @@
-"""Write tests/golden/ed_energies.json by exact diagonalisation (oracle only).
+"""Write the stored expected values under tests/golden/ (oracle only).
 
 Run from the repository root:  python tests/golden/make_golden.py
-Each entry records the model, its lattice and charge sector; the values come
-from ``oracle.kron`` (sparse Kronecker Hamiltonian + Lanczos eigensolver), whose
-builders are pinned by closed forms in tests/test_oracle_kron_mpo.py.
+
+ed_energies.json: exact ground energies; each entry records the model, its lattice
+and charge sector; the values come from ``oracle.kron`` (sparse Kronecker Hamiltonian
++ Lanczos eigensolver), whose builders are pinned by closed forms in
+tests/test_oracle_kron_mpo.py.
+
+dmrg_sweeps.json: the energy after every full sweep of the oracle's two-site DMRG
+(``oracle.dmrg``, Section II-C) on the 6 x 6 J1-J2 cylinder (J2 = 0.5, snake order,
+open in x and periodic in y) from the Neel product state, with the bond cap of each
+sweep, the Lanczos step count and the SVD cutoff recorded beside the values.
 """
 import json
 import os
@@ -14,6 +21,7 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl          # noqa: E402
 from oracle import kron         # noqa: E402
+from oracle import dmrg         # noqa: E402
 
 
 def main():
@@ -40,6 +48,23 @@ def main():
     with open(path, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
     print(json.dumps(out, indent=1))
+
+    sweeps = {}
+    Lx, Ly = 6, 6
+    n = Lx * Ly
+    mpo = wl.heisenberg_mpo(n, wl.cylinder_pairs(Lx, Ly, 1.0, 0.5))
+    states = [i % 2 for i in range(n)]            # up, down, up, ... along the snake: 2Sz = 0
+    schedule, n_iter, cutoff = [16, 32, 64, 64], 20, 1e-12
+    r = dmrg.dmrg(mpo, (0,), schedule, n_iter=n_iter, cutoff=cutoff, states=states)
+    sweeps["j1j2_cylinder_6x6_J2_0.5_neel_start"] = {
+        "model": "J1-J2 Heisenberg, J2/J1=0.5, 6x6 cylinder (open x, periodic y), snake order "
+                 "(Section V spin model)",
+        "sector": "2Sz=0", "states": states, "m_schedule": schedule, "lanczos_steps": n_iter,
+        "svd_cutoff": cutoff, "sweep_energies": [float(e) for e in r["sweep_energies"]]}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "dmrg_sweeps.json")
+    with open(path, "w") as f:
+        json.dump(sweeps, f, indent=1, sort_keys=True)
+    print(json.dumps(sweeps, indent=1))
 
 
 if __name__ == "__main__":

@@ -54,9 +54,10 @@ def test_autotune_keeps_results_bitwise():
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("name", ["spin_m200", "electron_m256", "spin_j1j2_6x6_m200", "spin_m1024"])
 def test_tile_variants_bitwise_equal(name, prec):
-    """Every tile variant (N = 256, N = 128, N = 256 in CTA pairs sharing B through TMA
-    multicast) gives bitwise the same y for a batch of 3 (a tile's K order is the same in all
-    of them), and batch entry 0 matches the oracle."""
+    """Every tile variant (N = 256, N = 128, N = 256 in CTA pairs that run one M = 256 tile
+    with pair MMAs, each CTA loading its own half of the B rows) gives bitwise the same y for
+    a batch of 3 (a tile's K order is the same in all of them), and batch entry 0 matches the
+    oracle."""
     w, lays, plan, d, xs = _setup(name, 3, prec)
     ws = plan.workspace()
     out = {}

@@ -58,6 +58,24 @@ def test_j1j2_cylinder_3x4_reaches_ed():
     assert abs(r["energy"] - E_ed) < 1e-9 * abs(E_ed)
 
 
+def test_j1j2_cylinder_6x6_sweeps_match_oracle():
+    """The paper's spin model on a 6 x 6 cylinder (36-site snake MPS): every sweep's energy
+    equals the oracle's two-site DMRG from the same Neel product state with the same bond
+    caps, Lanczos step count and SVD cutoff (tests/golden/dmrg_sweeps.json, written by the
+    oracle)."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "dmrg_sweeps.json")) as f:
+        g = json.load(f)["j1j2_cylinder_6x6_J2_0.5_neel_start"]
+    mpo = wl.heisenberg_mpo(36, wl.cylinder_pairs(6, 6, 1.0, 0.5))
+    r = dmrg.dmrg(mpo, (0,), g["m_schedule"], n_iter=g["lanczos_steps"], cutoff=g["svd_cutoff"],
+                  states=g["states"])
+    ref = g["sweep_energies"]
+    print(f"6x6 J1-J2: GPU {['%.12f' % e for e in r['sweep_energies']]}")
+    print(f"        oracle {['%.12f' % e for e in ref]}  bonds {r['bond_dims']}")
+    assert len(r["sweep_energies"]) == len(ref)
+    for e, e_ref in zip(r["sweep_energies"], ref):
+        assert abs(e - e_ref) < 1e-10 * abs(e_ref)
+
+
 def test_hubbard_chain_6_reaches_ed():
     n = 6
     mpo = wl.hubbard_mpo(n, [(i, i + 1, 1.0) for i in range(n - 1)], 8.0)

@@ -156,6 +156,40 @@ def test_dmrg_hubbard_equals_ed():
     assert abs(r["sweep_energies"][-1] - E_ed) < 1e-9 * abs(E_ed)
 
 
+def test_product_state_mps_is_the_basis_state_and_dmrg_from_it_reaches_ed():
+    # the Neel product state as an MPS contracts to one basis vector of the Kronecker basis,
+    # and two-site DMRG started from it reaches the exact ground energy (3 x 4 J1-J2)
+    Lx, Ly = 3, 4
+    n = Lx * Ly
+    states = [i % 2 for i in range(n)]
+    sites = mps.product_mps(wl.spin_phys(), states)
+    psi = mps.to_dense_state(sites)
+    idx = 0
+    for s in states:
+        idx = idx * 2 + s
+    assert np.array_equal(np.flatnonzero(psi), [idx]) and psi[idx] == 1.0
+    mpo = wl.heisenberg_mpo(n, wl.cylinder_pairs(Lx, Ly, 1.0, 0.5))
+    E_ed = _ed_golden()["j1j2_cylinder_3x4_J2_0.5_Sz0"]["E0"]
+    r = dmrg.dmrg(mpo, (0,), [16, 64, 64, 64], n_iter=25, states=states)
+    assert r["sweep_energies"][-1] >= E_ed - 1e-12 * abs(E_ed)
+    assert abs(r["sweep_energies"][-1] - E_ed) < 1e-9 * abs(E_ed)
+    with pytest.raises(ValueError):
+        dmrg.dmrg(mpo, (2,), [4], states=states)      # the product state has 2Sz = 0
+
+
+def test_golden_dmrg_sweeps_variational_and_decreasing():
+    # the stored 6 x 6 sweep energies do not increase from sweep to sweep, and the last lies
+    # below the energy of the Neel start state (DMRG improves on its start variationally)
+    with open(os.path.join(GOLDEN, "dmrg_sweeps.json")) as f:
+        g = json.load(f)["j1j2_cylinder_6x6_J2_0.5_neel_start"]
+    e = g["sweep_energies"]
+    assert all(b <= a + 1e-12 for a, b in zip(e, e[1:]))
+    pairs = wl.cylinder_pairs(6, 6, 1.0, 0.5)
+    # Neel energy along the snake: sum over bonds of J <Sz_i Sz_j> = +-J/4
+    neel = sum(J * (0.25 if (i % 2) == (j % 2) else -0.25) for i, j, J in pairs)
+    assert e[-1] < neel
+
+
 def test_golden_ed_values_reproduce():
     g = _ed_golden()
     n = 12
