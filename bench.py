@@ -31,8 +31,13 @@ METRIC = "H_eff applies/s at m=4096 (6x6 J1-J2 stand-in, U(1) Sz, k=14)"
 # the tensor pipe's active cycles in % of peak for the GEMMs), keyed by (workload,
 # precision, kernel, tile variant), from the committed ncu profile summary of the apply;
 # valid only while the device code they were measured on is unchanged (hash below).
-NCU_FIGURES = {}
-NCU_SRC_SHA = ""
+NCU_FIGURES = {
+    ("spin_m4096", "bf16x3", "mix", 0): {"dram_bytes": 195419392 + 334466560},
+    ("spin_m4096", "bf16x3", "pack", 0): {"dram_bytes": 24090368 + 10240},
+    ("spin_m4096", "bf16x3", "gemm1", 256): {"dram_bytes": 470653696 + 285800960, "tensor_pct": 51.45},
+    ("spin_m4096", "bf16x3", "gemm2", 256): {"dram_bytes": 808687872 + 42293504, "tensor_pct": 59.43},
+}
+NCU_SRC_SHA = "2e7c1653dc49f112"
 
 
 def _src_sha():
@@ -72,7 +77,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's default tile widths (for profiling: serialised launches under a "
                          "profiler would time the candidates differently)")
-    ap.add_argument("--part", default="", choices=["", "lanczos", "svd", "env_update", "backward"],
+    ap.add_argument("--part", default="", choices=["", "lanczos", "svd", "env_update", "backward", "energy"],
                     help="time one step of the DMRG bond update alone and print its own JSON line "
                          "(the profiling cases): the FP64 Lanczos eigensolver (30 iterations, BF16x3 "
                          "matvecs), the block SVD truncation, the environment update, the gradients")
@@ -304,6 +309,9 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
                 "energy_same_vector compares <v|K|v>/<v|v> of the FP64 Ritz vector under each matvec"}
     del Pt, wst
     del res, y
+    # ground energy of config 3, both paths converged (restarted Lanczos to a residual
+    # estimate of 1e-8 |E| from the same start vector)
+    out["energy_config3"] = ground_state_compare(args.workload, dev, stream)
     s = heff.heff_svd_create(xl.handle)
     sws = torch.empty(heff.heff_svd_workspace_size(s), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
@@ -327,18 +335,61 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     # lattice MPO windows at m = 4096: the 6 x 6 J1-J2 cylinder (k = 26) and the paper's
     # 20 x 10 J1-J2 cylinder (k = 38, uncompressed)
     for key, name, note in (
+            ("paper_block_model_m4096", "spin_paper_m4096",
+             "the block-size model of the paper's Table II, b_l = floor((m/4) 0.6^|l|): 27 sectors, centre "
+             "block 1024; range-4 chain MPO (k = 14)"),
             ("j1j2_6x6_lattice_m4096", "spin_j1j2_6x6_m4096",
              "two-site window of the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder MPO, binomial sectors"),
             ("j1j2_20x10_lattice_m4096", "spin_j1j2_20x10_m4096",
              "two-site window of the snake-ordered 20x10 J1-J2 (J2 = 0.5) cylinder MPO (the paper's spin "
-             "lattice), binomial sectors")):
+             "lattice), binomial sectors"),
+            ("j1j2_20x10_compressed_m4096", "spin_j1j2_20x10c_m4096",
+             "the same window of the 20x10 J1-J2 cylinder MPO compressed at the SVD cutoff 1e-13 "
+             "(k = 32), binomial sectors")):
         out[key] = {**single_apply(name, dev, stream, flush), "note": note}
 
     # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles): the
     # range-5 chain window and the 4 x 8 Hubbard cylinder window
-    for name in ("electron_m2048", "electron_hubbard_4x8_m2048", "electron_tri_xc6_m2048"):
+    for name in ("electron_m2048", "electron_hubbard_4x8_m2048", "electron_tri_xc6_m2048", "electron_tri_xc6c_m2048"):
         out[name + "_batch32_graph"] = batched_graph(name, 32, dev, stream, flush)
     return out
+
+
+def ground_state_compare(name, dev, stream, n_iter=120, cycles=6, tol=1e-8):
+    """heff_ground_state with BF16x3 matvecs (energy: the FP64 Rayleigh quotient of its Ritz
+    vector) and with FP64 matvecs, from the same start vector; host wall time of each (the
+    routine synchronises once per restart cycle)."""
+    import torch
+    from paper_2007_05540_gb300 import heff
+    w, lays, bufs = make_problem(name, 0)
+    d = {k: torch.from_numpy(np.asarray(bufs[k])).to(dev, torch.float64) for k in ("L", "W1", "W2", "R", "x")}
+    P64 = heff.Plan(*lays, bufs["W1"], bufs["W2"], "fp64", "f64")
+    Pb = heff.Plan(*lays, bufs["W1"], bufs["W2"], "bf16x3", "f64")
+    ws64, wsb = P64.workspace(dev), Pb.workspace(dev)
+    gs = torch.empty(heff.heff_ground_state_workspace_size(Pb.handle, n_iter), dtype=torch.uint8, device=dev)
+    x = torch.empty_like(d["x"])
+    out = {}
+    for key, P, P2, ws, ws2 in (("mixed", Pb, P64, wsb, ws64), ("fp64", P64, None, ws64, None)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = heff.heff_ground_state(P.handle, P2.handle if P2 is not None else None, d["L"], d["W1"], d["W2"],
+                                   d["R"], d["x"], n_iter, cycles, tol, x, ws, ws2, gs, stream)
+        torch.cuda.synchronize()
+        r["s"] = time.perf_counter() - t0
+        out[key] = r
+    E64, Em = out["fp64"]["energy"], out["mixed"]["energy"]
+    return {"workload": name, "E_fp64": E64, "E_mixed": Em, "rel_err": abs(Em - E64) / abs(E64),
+            "ritz_bf16x3": out["mixed"]["ritz"], "rel_err_ritz_bf16x3": abs(out["mixed"]["ritz"] - E64) / abs(E64),
+            "residual_fp64": {"mixed": out["mixed"]["residual_fp64"], "fp64": out["fp64"]["residual_fp64"]},
+            "residual_estimate": {"mixed": out["mixed"]["residual_estimate"],
+                                  "fp64": out["fp64"]["residual_estimate"]},
+            "cycles": {"mixed": out["mixed"]["cycles"], "fp64": out["fp64"]["cycles"]},
+            "matvecs": {"mixed": out["mixed"]["matvecs"], "fp64": out["fp64"]["matvecs"]},
+            "s": {"mixed": out["mixed"]["s"], "fp64": out["fp64"]["s"]},
+            "speedup": out["fp64"]["s"] / out["mixed"]["s"],
+            "note": f"restarted Lanczos ({n_iter} steps per cycle) until the residual estimate is <= {tol:g} |E|; "
+                    "mixed: BF16x3 matvecs, energy = FP64 Rayleigh quotient of its Ritz vector (one FP64 apply); "
+                    "residual_fp64 = ||K x - E x|| / |E| with FP64 matvecs"}
 
 
 def single_apply(name, dev, stream, flush):
@@ -476,6 +527,8 @@ def run_part(args):
         out = env_update_timing(w, dev, stream)
     elif args.part == "backward":
         out = backward_timing(dev, stream)
+    elif args.part == "energy":
+        out = ground_state_compare(args.workload, dev, stream)
     else:
         out = svd_timing(args, dev, stream)
     print(json.dumps({"part": args.part, "workload": args.workload, **out}), flush=True)

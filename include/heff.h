@@ -239,6 +239,36 @@ int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2,
                  size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes, void* stream);
 
 /*
+ * heff_ground_state -- lowest eigenpair of H_eff to a residual tolerance, with the energy
+ * evaluated in FP64 (the eigensolver of the two-site DMRG step, Section II-C and III, run
+ * to convergence; the FP64 refinement that lets split-precision matvecs give FP64-accurate
+ * energies).  Restarted Lanczos: each cycle runs n_iter steps of heff_lanczos from the
+ * previous cycle's Ritz vector (the first from x0), with matvecs in `plan`'s precision, until
+ * the cycle's residual estimate |beta_last s_last| / |theta| is <= tol or max_cycles cycles
+ * have run.  The energy is then the FP64 Rayleigh quotient <x|K|x> of the normalised Ritz
+ * vector x, computed with one apply of `plan64` (an HEFF_PREC_FP64 plan of the same layouts;
+ * NULL: `plan` itself when it is an FP64 plan, otherwise no FP64 step), together with the
+ * FP64 residual ||K x - E x|| / |E|.  L, W1, W2, R: device doubles (HEFF_DTYPE_F64 plans).
+ *   x0      device, nelem(x) doubles, nonzero start vector
+ *   x_out   device, nelem(x) doubles: the normalised Ritz vector (may alias x0)
+ *   result  HOST, 6 doubles: [0] energy (FP64 Rayleigh quotient, or the last Ritz value
+ *           without an FP64 plan), [1] last Ritz value (plan's precision), [2] last residual
+ *           estimate / |theta|, [3] cycles run, [4] Lanczos steps (matvecs) run, [5] FP64
+ *           residual ||K x - E x|| / |E| (-1 without an FP64 plan)
+ *   apply_ws / apply_ws64  the workspaces of plan / plan64 (apply_ws64 ignored when plan64
+ *           is NULL)
+ *   gs_ws   >= heff_ground_state_workspace_size bytes, 256-byte aligned, overwritten
+ * n_iter 1..126, max_cycles >= 1, tol >= 0.  Synchronises `stream` once per cycle (the
+ * residual test on the host) and once after the FP64 step.  Errors: INVALID_ARG,
+ * UNSUPPORTED (plan without HEFF_DTYPE_F64 tensors), WORKSPACE, CUDA.
+ */
+int heff_ground_state_workspace_size(const heff_plan* plan, int32_t n_iter, size_t* bytes);
+int heff_ground_state(heff_plan* plan, heff_plan* plan64, const void* L, const void* W1, const void* W2,
+                      const void* R, const double* x0, int32_t n_iter, int32_t max_cycles, double tol,
+                      double* x_out, double* result, void* apply_ws, size_t apply_ws_bytes, void* apply_ws64,
+                      size_t apply_ws64_bytes, void* gs_ws, size_t gs_ws_bytes, void* stream);
+
+/*
  * heff_davidson -- lowest eigenpair of H_eff by the Davidson routine of Algorithm 1
  * (no preconditioner; randomisation when re-orthogonalisation fails), all in FP64 on the
  * device except the matvecs (the plan's precision; HEFF_DTYPE_F64 tensors).  Per step i:

@@ -9,13 +9,15 @@
 namespace heff {
 
 void BList::add_block(int64_t c_off, int32_t ldc, int32_t m, int32_t n, const std::vector<BProd>& ps) {
-    for (int r0 = 0; r0 < m; r0 += 64)
-        for (int c0 = 0; c0 < n; c0 += 64) {
+    blocks.push_back(Block{c_off, ldc, m, n, (int32_t)block_prods.size(), (int32_t)ps.size()});
+    block_prods.insert(block_prods.end(), ps.begin(), ps.end());
+    for (int r0 = 0; r0 < m; r0 += tile_m)
+        for (int c0 = 0; c0 < n; c0 += tile_n) {
             BTile t{};
             t.c_off = c_off + (int64_t)r0 * ldc + c0;
             t.ldc = ldc;
-            t.m = m - r0 < 64 ? m - r0 : 64;
-            t.n = n - c0 < 64 ? n - c0 : 64;
+            t.m = m - r0 < tile_m ? m - r0 : tile_m;
+            t.n = n - c0 < tile_n ? n - c0 : tile_n;
             t.prod_begin = (int32_t)prods.size();
             t.prod_count = (int32_t)ps.size();
             for (const BProd& p : ps) {
@@ -27,6 +29,21 @@ void BList::add_block(int64_t c_off, int32_t ldc, int32_t m, int32_t n, const st
             }
             tiles.push_back(t);
         }
+}
+
+void BList::retile(int tm, int tn) {
+    std::vector<Block> bl;
+    std::vector<BProd> bp;
+    bl.swap(blocks);
+    bp.swap(block_prods);
+    tiles.clear();
+    prods.clear();
+    flops = 0;
+    tile_m = tm;
+    tile_n = tn;
+    for (const Block& k : bl)
+        add_block(k.c_off, k.ldc, k.m, k.n,
+                  std::vector<BProd>(bp.begin() + k.prod_begin, bp.begin() + k.prod_begin + k.prod_count));
 }
 
 int blist_upload(BList& b) {

@@ -110,13 +110,31 @@ struct BList {
     BProd* d_prods = nullptr;
     double flops = 0;
     bool accumulate = false;   // C += result instead of C = result
+    int tile_m = 64, tile_n = 64;   // output tile shape the block list is cut into
+    // the output blocks as added (products given for the block origin), kept for re-tiling
+    struct Block { int64_t c_off; int32_t ldc, m, n, prod_begin, prod_count; };
+    std::vector<Block> blocks;
+    std::vector<BProd> block_prods;
     // append the tiles of an m x n output block whose products are given for the block origin
     void add_block(int64_t c_off, int32_t ldc, int32_t m, int32_t n, const std::vector<BProd>& ps);
+    // cut every block again into tm x tn tiles (the device tables must be re-uploaded)
+    void retile(int tm, int tn);
 };
 int blist_upload(BList& b);
 void blist_free(BList& b);
 int launch_bgemm(const BList& b, const double* A, const double* B, double* C, const double* coef1,
                  const double* coef2, double scale, void* stream, const double* inv_scale = nullptr);
+// the same products on the tensor cores (BF16x3 split, FP32 accumulation; blockops_tc.cu):
+// needs 128 x 128 tiles (retile); err: device int raised when a bounded wait expires
+int launch_bgemm_tc(const BList& b, const double* A, const double* B, double* C, const double* coef1,
+                    const double* coef2, double scale, void* stream, const double* inv_scale, int* err);
+// run a block list in the given precision (HEFF_PREC_FP64: CUDA cores, HEFF_PREC_BF16X3: tensor cores)
+inline int launch_blist(int precision, const BList& b, const double* A, const double* B, double* C,
+                        const double* coef1, const double* coef2, double scale, void* stream,
+                        const double* inv_scale, int* err) {
+    return precision == HEFF_PREC_BF16X3 ? launch_bgemm_tc(b, A, B, C, coef1, coef2, scale, stream, inv_scale, err)
+                                         : launch_bgemm(b, A, B, C, coef1, coef2, scale, stream, inv_scale);
+}
 // out[j] = scale * sum over the dots d in [off[j], off[j+1]) of <X[x_off..], Y[y_off..]>
 // (dots sorted by output index; scratch holds one double per dot)
 struct BDot {

@@ -452,31 +452,26 @@ extern "C" int heff_lanczos_workspace_size(const heff_plan* plan, int32_t n_iter
     return HEFF_OK;
 }
 
-extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
-                            const double* x0, int32_t n_iter, double* x_out, double* result,
-                            void* apply_ws, size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes,
-                            void* stream) {
-    clear_error();
-    if (!plan || !L || !W1 || !W2 || !R || !x0 || !x_out || !result || !lz_ws)
-        return fail(HEFF_ERR_INVALID_ARG, "heff_lanczos: null argument");
-    if (plan->opts.io_dtype != HEFF_DTYPE_F64)
-        return fail(HEFF_ERR_UNSUPPORTED, "heff_lanczos needs a plan with HEFF_DTYPE_F64 tensors");
-    if (n_iter < 1 || n_iter > 126) return fail(HEFF_ERR_INVALID_ARG, "n_iter must be 1..126");
-    const LzLayout lay = lz_layout(plan->nelem_x, n_iter);
-    if (lz_ws_bytes < lay.bytes || reinterpret_cast<uintptr_t>(lz_ws) % 256)
-        return fail(HEFF_ERR_WORKSPACE, "Lanczos workspace of %zu bytes, needs %zu (256-byte aligned)",
-                    lz_ws_bytes, lay.bytes);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+namespace heff {
+namespace {
+
+Lz lz_view(const LzLayout& lay, void* lz_ws, int64_t n) {
     char* base = static_cast<char*>(lz_ws);
-    Lz z{reinterpret_cast<double*>(base + lay.off_state), reinterpret_cast<double*>(base + lay.off_h),
-         reinterpret_cast<double*>(base + lay.off_s), reinterpret_cast<double*>(base + lay.off_part),
-         reinterpret_cast<double*>(base + lay.off_T), reinterpret_cast<double*>(base + lay.off_V),
-         plan->nelem_x, lay.nmax};
+    return Lz{reinterpret_cast<double*>(base + lay.off_state), reinterpret_cast<double*>(base + lay.off_h),
+              reinterpret_cast<double*>(base + lay.off_s), reinterpret_cast<double*>(base + lay.off_part),
+              reinterpret_cast<double*>(base + lay.off_T), reinterpret_cast<double*>(base + lay.off_V), n,
+              lay.nmax};
+}
+
+// n_iter Lanczos steps from x0 on operators already prepared in apply_ws; x0 may alias x_out
+// (it is only read into the first basis vector).
+int lanczos_core(heff_plan* plan, const double* x0, int32_t n_iter, double* x_out, double* result,
+                 void* apply_ws, size_t apply_ws_bytes, const Lz& z, cudaStream_t st) {
+    void* stream = st;
     const int64_t n = z.n;
     const int G = grid_for(n);
     const int GN = G < 1024 ? G : 1024;      // normalize: every block re-sums the RB partials
-    int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
-    if (rc) return rc;
+    int rc;
     // v_0 = x0 / ||x0||
     sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, z.part);
     normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x0, z.V, n, z.state, 0, 0, z.nmax);
@@ -515,6 +510,152 @@ extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, cons
     cudaMemcpyAsync(result + 3, z.state + 8, sizeof(double) * 2 * z.nmax, cudaMemcpyDeviceToDevice, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_lanczos: %s", cudaGetErrorString(e));
+    return HEFF_OK;
+}
+
+}  // namespace
+}  // namespace heff
+
+extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
+                            const double* x0, int32_t n_iter, double* x_out, double* result,
+                            void* apply_ws, size_t apply_ws_bytes, void* lz_ws, size_t lz_ws_bytes,
+                            void* stream) {
+    clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x0 || !x_out || !result || !lz_ws)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_lanczos: null argument");
+    if (plan->opts.io_dtype != HEFF_DTYPE_F64)
+        return fail(HEFF_ERR_UNSUPPORTED, "heff_lanczos needs a plan with HEFF_DTYPE_F64 tensors");
+    if (n_iter < 1 || n_iter > 126) return fail(HEFF_ERR_INVALID_ARG, "n_iter must be 1..126");
+    const LzLayout lay = lz_layout(plan->nelem_x, n_iter);
+    if (lz_ws_bytes < lay.bytes || reinterpret_cast<uintptr_t>(lz_ws) % 256)
+        return fail(HEFF_ERR_WORKSPACE, "Lanczos workspace of %zu bytes, needs %zu (256-byte aligned)",
+                    lz_ws_bytes, lay.bytes);
+    int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
+    if (rc) return rc;
+    return lanczos_core(plan, x0, n_iter, x_out, result, apply_ws, apply_ws_bytes,
+                        lz_view(lay, lz_ws, plan->nelem_x), static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- ground state to a tolerance
+namespace heff {
+namespace {
+
+// part[b] = sum over block b's chunk of x[i] * y[i]  (mode 0), or of (y[i] - E x[i])^2 with
+// E = *e_dev (mode 1); two-stage with a fixed order, like the Lanczos reductions
+__global__ void __launch_bounds__(RT) rq_part_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                     int64_t n, const double* __restrict__ e_dev, int mode,
+                                                     double* __restrict__ part) {
+    __shared__ double sh[RT / 32];
+    const double E = mode ? *e_dev : 0.0;
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) {
+        if (mode == 0) {
+            a = fma(x[i], y[i], a);
+        } else {
+            const double r = y[i] - E * x[i];
+            a = fma(r, r, a);
+        }
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+__global__ void rq_finish_kernel(const double* __restrict__ part, int nb, double* out) {
+    __shared__ double sh[RT / 32];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) *out = v;
+}
+
+// ground-state workspace: the Lanczos workspace, then the cycle's result and 4 scalars
+size_t gs_result_off(const LzLayout& lay) { return lay.bytes; }
+size_t gs_bytes(const LzLayout& lay) {
+    return lay.bytes + (sizeof(double) * (3 + 2 * (size_t)lay.nmax + 8) + 255) / 256 * 256;
+}
+
+}  // namespace
+}  // namespace heff
+
+extern "C" int heff_ground_state_workspace_size(const heff_plan* plan, int32_t n_iter, size_t* bytes) {
+    clear_error();
+    if (!plan || !bytes || n_iter < 1 || n_iter > 126)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state_workspace_size: bad arguments (n_iter 1..126)");
+    *bytes = gs_bytes(lz_layout(plan->nelem_x, n_iter));
+    return HEFF_OK;
+}
+
+extern "C" int heff_ground_state(heff_plan* plan, heff_plan* plan64, const void* L, const void* W1,
+                                 const void* W2, const void* R, const double* x0, int32_t n_iter,
+                                 int32_t max_cycles, double tol, double* x_out, double* result,
+                                 void* apply_ws, size_t apply_ws_bytes, void* apply_ws64, size_t apply_ws64_bytes,
+                                 void* gs_ws, size_t gs_ws_bytes, void* stream) {
+    clear_error();
+    if (!plan || !L || !W1 || !W2 || !R || !x0 || !x_out || !result || !gs_ws)
+        return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state: null argument");
+    if (plan->opts.io_dtype != HEFF_DTYPE_F64)
+        return fail(HEFF_ERR_UNSUPPORTED, "heff_ground_state needs a plan with HEFF_DTYPE_F64 tensors");
+    if (n_iter < 1 || n_iter > 126 || max_cycles < 1 || !(tol >= 0.0))
+        return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state: n_iter 1..126, max_cycles >= 1, tol >= 0");
+    // the FP64 Rayleigh quotient: plan64, or the plan itself when it is the FP64 path
+    heff_plan* p64 = plan64 ? plan64 : (plan->opts.precision == HEFF_PREC_FP64 ? plan : nullptr);
+    void* ws64 = plan64 ? apply_ws64 : apply_ws;
+    const size_t ws64_bytes = plan64 ? apply_ws64_bytes : apply_ws_bytes;
+    if (p64) {
+        if (p64->opts.precision != HEFF_PREC_FP64 || p64->opts.io_dtype != HEFF_DTYPE_F64 ||
+            p64->nelem_x != plan->nelem_x)
+            return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state: plan64 must be an FP64 plan of the same layouts");
+        if (plan64 && !apply_ws64) return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state: null apply_ws64");
+    }
+    const LzLayout lay = lz_layout(plan->nelem_x, n_iter);
+    if (gs_ws_bytes < gs_bytes(lay) || reinterpret_cast<uintptr_t>(gs_ws) % 256)
+        return fail(HEFF_ERR_WORKSPACE, "ground-state workspace of %zu bytes, needs %zu (256-byte aligned)",
+                    gs_ws_bytes, gs_bytes(lay));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Lz z = lz_view(lay, gs_ws, plan->nelem_x);
+    double* res = reinterpret_cast<double*>(static_cast<char*>(gs_ws) + gs_result_off(lay));
+    double* scal = res + 3 + 2 * lay.nmax;          // [0] x.y, [1] |y - E x|^2
+    int rc = heff_prepare(plan, L, W1, W2, R, apply_ws, apply_ws_bytes, stream);
+    if (rc) return rc;
+    double theta = 0.0, est = 0.0;
+    int cycles = 0;
+    const double* start = x0;
+    for (; cycles < max_cycles;) {
+        if ((rc = lanczos_core(plan, start, n_iter, x_out, res, apply_ws, apply_ws_bytes, z, st))) return rc;
+        ++cycles;
+        start = x_out;                                // the next cycle restarts from the Ritz vector
+        double h[2];
+        cudaError_t e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_ground_state: %s", cudaGetErrorString(e));
+        theta = h[0];
+        est = h[1] / (fabs(theta) > 0.0 ? fabs(theta) : 1.0);
+        if (!(est > tol)) break;
+    }
+    result[0] = theta;
+    result[1] = theta;
+    result[2] = est;
+    result[3] = cycles;
+    result[4] = (double)cycles * n_iter;
+    result[5] = -1.0;
+    if (p64) {
+        // E = <x|K|x> (x is normalised) with an FP64 apply, and ||K x - E x|| / |E|
+        if (p64 != plan && (rc = heff_prepare(p64, L, W1, W2, R, ws64, ws64_bytes, stream))) return rc;
+        double* y = z.w();
+        if ((rc = heff_apply_prepared(p64, x_out, y, ws64, ws64_bytes, stream))) return rc;
+        const int64_t n = z.n;
+        rq_part_kernel<<<RB, RT, 0, st>>>(x_out, y, n, nullptr, 0, z.part);
+        rq_finish_kernel<<<1, RT, 0, st>>>(z.part, RB, scal);
+        rq_part_kernel<<<RB, RT, 0, st>>>(x_out, y, n, scal, 1, z.part);
+        rq_finish_kernel<<<1, RT, 0, st>>>(z.part, RB, scal + 1);
+        count_launches(4);
+        double h[2];
+        cudaError_t e = cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_ground_state: %s", cudaGetErrorString(e));
+        result[0] = h[0];
+        result[5] = sqrt(h[1]) / (fabs(h[0]) > 0.0 ? fabs(h[0]) : 1.0);
+    }
     return HEFF_OK;
 }
 

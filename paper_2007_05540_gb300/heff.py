@@ -93,6 +93,9 @@ _sig = {
     "heff_env_update": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_env_plan_destroy": (None, [_vp]),
     "heff_lanczos_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
+    "heff_ground_state_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
+    "heff_ground_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, C.c_double, _vp,
+                                     _P(C.c_double), _vp, _sz, _vp, _sz, _vp, _sz, _vp]),
     "heff_lanczos": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
     "heff_plan_autotune": (C.c_int, [_vp] * 8 + [_sz, _vp, _P(_i32), _P(C.c_float)]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
@@ -443,6 +446,27 @@ def heff_lanczos(plan, L, W1, W2, R, x0, n_iter, x_out, result, apply_ws, lz_ws,
     _check(_lib.heff_lanczos(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x0), int(n_iter),
                              _ptr(x_out), _ptr(result), _ptr(apply_ws), _nbytes(apply_ws), _ptr(lz_ws),
                              _nbytes(lz_ws), _stream(stream)), "heff_lanczos")
+
+
+def heff_ground_state_workspace_size(plan, n_iter):
+    b = _sz()
+    _check(_lib.heff_ground_state_workspace_size(plan, int(n_iter), C.byref(b)),
+           "heff_ground_state_workspace_size")
+    return b.value
+
+
+def heff_ground_state(plan, plan64, L, W1, W2, R, x0, n_iter, max_cycles, tol, x_out, apply_ws, apply_ws64,
+                      gs_ws, stream=None):
+    """Restarted Lanczos to a residual tolerance, energy by an FP64 Rayleigh quotient
+    (plan64, or None).  Returns dict(energy, ritz, residual_estimate, cycles, matvecs,
+    residual_fp64)."""
+    r = (C.c_double * 6)()
+    _check(_lib.heff_ground_state(plan, plan64, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x0), int(n_iter),
+                                  int(max_cycles), float(tol), _ptr(x_out), r, _ptr(apply_ws), _nbytes(apply_ws),
+                                  _ptr(apply_ws64), 0 if apply_ws64 is None else _nbytes(apply_ws64), _ptr(gs_ws),
+                                  _nbytes(gs_ws), _stream(stream)), "heff_ground_state")
+    return {"energy": r[0], "ritz": r[1], "residual_estimate": r[2], "cycles": int(r[3]), "matvecs": int(r[4]),
+            "residual_fp64": r[5]}
 
 
 NOALLOC_WORKSPACE_BYTES = 128 << 20   # HEFF_NOALLOC_WORKSPACE_BYTES in include/heff.h

@@ -199,3 +199,56 @@ def test_davidson_with_bf16x3_matvecs():
     res, x = _davidson(p, "bf16x3", 60, 1e-7)
     assert abs(res[0] - E0) < 1e-3 * abs(E0)
     assert abs(p.rayleigh_fp64(x) - E0) < 1e-8 * abs(E0)
+
+
+# ---------------------------------------------------------------- ground state to a tolerance
+def _ground_state(p, prec, refine, n_iter=120, cycles=8, tol=1e-9):
+    P = p.plan(prec)
+    P64 = p.plan("fp64") if refine else None
+    ws = P.workspace()
+    ws64 = P64.workspace() if refine else None
+    gs = torch.empty(heff.heff_ground_state_workspace_size(P.handle, n_iter), dtype=torch.uint8, device="cuda")
+    x = torch.empty_like(p.x0)
+    d = p.d
+    r = heff.heff_ground_state(P.handle, P64.handle if refine else None, d["L"], d["W1"], d["W2"], d["R"], p.x0,
+                               n_iter, cycles, tol, x, ws, ws64, gs)
+    return r, x
+
+
+@pytest.mark.parametrize("name", ["spin_m24", "electron_m40"])
+def test_ground_state_equals_lowest_eigenvalue_of_dense_K(name):
+    """Converged to the tolerance, the FP64 path's energy equals the lowest eigenvalue of the
+    oracle's dense K (Section II-C) to 1e-10, and the split-precision path with its FP64
+    Rayleigh quotient equals it to 1e-8."""
+    p = LzProblem(name)
+    L, W1, W2, R, x = oh.problem_from_workload(p.w)
+    K = oh.heff_matrix_dense(L.to_dense(), W1, W2, R.to_dense())
+    # the lowest eigenvalue restricted to the allowed blocks (K maps them into themselves)
+    mask = x.to_dense().reshape(-1) != 0
+    E_ex = np.linalg.eigvalsh(K[np.ix_(mask, mask)])[0]
+    r64, _ = _ground_state(p, "fp64", False, n_iter=60, cycles=10, tol=1e-11)
+    rb, _ = _ground_state(p, "bf16x3", True, n_iter=60, cycles=10, tol=1e-10)
+    print(f"{name}: exact {E_ex:.14f} fp64 {r64['energy']:.14f} ({r64['cycles']} cycles) bf16x3+fp64 RQ "
+          f"{rb['energy']:.14f} (Ritz {rb['ritz']:.14f}, FP64 residual {rb['residual_fp64']:.2e})")
+    assert abs(r64["energy"] - E_ex) < 1e-10 * abs(E_ex)
+    assert r64["residual_fp64"] < 1e-8
+    assert abs(rb["energy"] - E_ex) < 1e-8 * abs(E_ex)
+
+
+def test_ground_state_mixed_energy_within_1e8_of_fp64_path_m1024():
+    """The full m = 1024 spin workload (30 sectors, k = 14): both paths converged to a
+    residual estimate of 1e-9 |E| by restarted Lanczos from the same start vector; the
+    BF16x3 path's energy (its Ritz vector's FP64 Rayleigh quotient, one FP64 apply) is within
+    1e-8 relative of the FP64 path's, while its own Ritz value carries the split's bias."""
+    p = LzProblem("spin_m1024")
+    r64, x64 = _ground_state(p, "fp64", False)
+    rb, xb = _ground_state(p, "bf16x3", True)
+    rel = abs(rb["energy"] - r64["energy"]) / abs(r64["energy"])
+    print(f"m=1024: fp64 {r64['energy']:.14f} ({r64['matvecs']} matvecs, FP64 residual {r64['residual_fp64']:.2e}); "
+          f"bf16x3 {rb['energy']:.14f} ({rb['matvecs']} matvecs, Ritz {rb['ritz']:.14f}, FP64 residual "
+          f"{rb['residual_fp64']:.2e}); rel diff {rel:.2e}")
+    assert r64["residual_estimate"] <= 1e-9 and rb["residual_estimate"] <= 1e-9
+    assert r64["residual_fp64"] < 1e-7
+    assert rel <= 1e-8
+    # the same eigenvector: |<x_fp64|x_mixed>| = 1 to the split's accuracy
+    assert abs(abs(float(torch.dot(x64, xb))) - 1.0) < 1e-6

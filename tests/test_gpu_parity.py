@@ -71,7 +71,8 @@ def _compare(y, y_ref, tol, mask=None):
 
 
 SMALL = ["spin_m64", "spin_m200", "electron_m96", "electron_m256", "spin_m1024_s8", "spin_j1j2_6x6_m200",
-         "electron_hubbard_4x8_m96", "spin_j1j2_20x10_m200", "electron_tri_xc6_m96"]
+         "electron_hubbard_4x8_m96", "spin_j1j2_20x10_m200", "electron_tri_xc6_m96", "spin_j1j2_20x10c_m200",
+         "electron_tri_xc6c_m96"]
 
 
 def _workload(name):
@@ -161,8 +162,11 @@ def test_workspace_errors():
     assert e.value.code == -1
 
 
+# spin_paper_m4096: the Table II block-size model (27 sectors, centre block 1024 rows), the
+# largest single-sector GEMMs of any workload; sector 13 is the centre, 0 and 26 the edges
 FULL = [("spin_m4096", (0, 19, 20, 39)), ("spin_m1024", (0, 14, 15, 29)),
-        ("electron_m2048", (0, 30, 31, 60)), ("spin_j1j2_6x6_m4096", (0, 19, 20, 39))]
+        ("electron_m2048", (0, 30, 31, 60)), ("spin_j1j2_6x6_m4096", (0, 19, 20, 39)),
+        ("spin_paper_m4096", (0, 12, 13, 26)), ("spin_j1j2_20x10c_m4096", (0, 19, 20, 39))]
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp64"])

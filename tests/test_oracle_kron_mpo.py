@@ -139,7 +139,7 @@ def test_mpo_charge_rule_and_transpose_symmetry(which):
 
 
 @pytest.mark.parametrize("name", ["spin_j1j2_6x6_m200", "spin_j1j2_20x10_m200", "electron_hubbard_4x8_m96",
-                                  "electron_tri_xc6_m96"])
+                                  "electron_tri_xc6_m96", "spin_j1j2_20x10c_m200", "electron_tri_xc6c_m96"])
 def test_lattice_windows_charge_rule_and_hermiticity(name):
     # the lattice MPO windows obey the charge rule of every nonzero entry and are Hermitian
     # under the channel transposition map, as the chain windows are
@@ -150,10 +150,12 @@ def test_lattice_windows_charge_rule_and_hermiticity(name):
     from workloads.fill import lattice_window
     win = {"spin_j1j2_6x6_m200": lambda: lattice_window(), "spin_j1j2_20x10_m200": lambda: lattice_window(20, 10),
            "electron_hubbard_4x8_m96": wl.hubbard_lattice_window,
-           "electron_tri_xc6_m96": wl.triangular_hubbard_window}[name]()
+           "electron_tri_xc6_m96": wl.triangular_hubbard_window,
+           "spin_j1j2_20x10c_m200": lambda: lattice_window(20, 10, compress=True),
+           "electron_tri_xc6c_m96": lambda: wl.triangular_hubbard_window(compress=True)}[name]()
     for W, c0, c1 in [(win["W1"], win["conj_l"], win["conj_m"]), (win["W2"], win["conj_m"], win["conj_r"])]:
         Wt = W[c0][:, :, :, c1].transpose(0, 2, 1, 3)
-        assert np.abs(W - Wt).max() == 0.0
+        assert np.abs(W - Wt).max() < 1e-14
 
 
 def test_bulk_window_bond_dims():
@@ -168,3 +170,69 @@ def test_bulk_window_bond_dims():
     # triangular Hubbard (XC6)
     assert wl.lattice_window(20, 10)["W1"].shape == (38, 2, 2, 38)
     assert wl.triangular_hubbard_window()["W1"].shape == (30, 4, 4, 30)
+
+
+# ---------------------------------------------------------------- MPO compression (Section VI-B)
+def _operator_schmidt_rank(H, n, b, d):
+    """Rank of H as a sum of (operator on sites < b) x (operator on sites >= b): the minimal
+    MPO bond dimension at bond b, from the dense Hamiltonian."""
+    dl, dr = d ** b, d ** (n - b)
+    M = H.reshape(dl, dr, dl, dr).transpose(0, 2, 1, 3).reshape(dl * dl, dr * dr)
+    s = np.linalg.svd(M, compute_uv=False)
+    return int(np.sum(s > 1e-10 * s[0]))
+
+
+@pytest.mark.parametrize("case", ["j1j2_3x4", "tri_hubbard_2x3", "chain_range3"])
+def test_compressed_mpo_equals_kronecker_hamiltonian_with_minimal_bonds(case):
+    if case == "j1j2_3x4":
+        n, d = 12, 2
+        pairs = wl.cylinder_pairs(3, 4, 1.0, 0.5)
+        mpo, Hk = wl.heisenberg_mpo(n, pairs), kron.heisenberg_hamiltonian(n, pairs).toarray()
+        supports = [(i, j) for i, j, _ in pairs]
+    elif case == "tri_hubbard_2x3":
+        n, d = 6, 4
+        hops = wl.triangular_hops(2, 3, 1.0)
+        mpo, Hk = wl.hubbard_mpo(n, hops, 8.5), kron.hubbard_hamiltonian(n, hops, 8.5).toarray()
+        supports = [(i, j) for i, j, _ in hops] + [(i, i) for i in range(n)]
+    else:
+        n, d = 10, 2
+        pairs = wl.chain_pairs(n, [1.0, 0.5, 0.2])
+        mpo, Hk = wl.heisenberg_mpo(n, pairs), kron.heisenberg_hamiltonian(n, pairs).toarray()
+        supports = [(i, j) for i, j, _ in pairs]
+    c = wl.compress_mpo(mpo, 1e-13)
+    # the same operator ...
+    assert np.abs(kron.mpo_to_dense(c) - Hk).max() < 1e-12
+    # ... with the fewest channels any MPO of it can have at every bond: the operator
+    # Schmidt rank of H across the bond, plus the start / done channels the compression keeps
+    # even where their operator is zero (no term lies wholly right / left of the bond)
+    for b in range(1, n):
+        zero_done = not any(j < b for i, j in supports)
+        zero_start = not any(i >= b for i, j in supports)
+        assert c.bond_dim(b) <= mpo.bond_dim(b)
+        assert c.bond_dim(b) == _operator_schmidt_rank(Hk, n, b, d) + zero_done + zero_start, b
+    assert any(c.bond_dim(b) < mpo.bond_dim(b) for b in range(1, n))
+    # compressing again changes no bond
+    cc = wl.compress_mpo(c, 1e-13)
+    assert [cc.bond_dim(b) for b in range(n + 1)] == [c.bond_dim(b) for b in range(n + 1)]
+
+
+def test_compressed_mpo_charge_rule_and_transpose_symmetry():
+    for mpo in (wl.heisenberg_mpo(36, wl.cylinder_pairs(6, 6, 1.0, 0.5)),
+                wl.hubbard_mpo(36, wl.triangular_hops(6, 6, 1.0), 8.5)):
+        c = wl.compress_mpo(mpo)
+        for n in range(c.n_sites):
+            W, ql, qr = c.W[n], c.charges[n], c.charges[n + 1]
+            for wl_, t, s, wr in np.argwhere(W != 0):
+                assert np.array_equal(ql[wl_] + c.phys[t] - c.phys[s], qr[wr])
+            Wt = W[c.conj[n]][:, :, :, c.conj[n + 1]].transpose(0, 2, 1, 3)
+            assert np.abs(W - Wt).max() < 1e-14
+        assert c.start_index(0) == 0 and c.done_index(c.n_sites) == 0
+
+
+def test_compressed_paper_lattice_bond_dims():
+    # Section VI-B: the 6 x 6 triangular Hubbard MPO compressed at 1e-13 has k = 26; the
+    # paper's 20 x 10 J1-J2 cylinder ends near k = 30 (32 here: the J1-J2 couplings of a
+    # width-10 snake cylinder leave 10 independent open sites, 3 channels each, + 2)
+    assert wl.triangular_hubbard_window(compress=True)["W1"].shape == (26, 4, 4, 26)
+    assert wl.lattice_window(20, 10, compress=True)["W1"].shape == (32, 2, 2, 32)
+    assert wl.lattice_window(compress=True)["W1"].shape == (20, 2, 2, 20)

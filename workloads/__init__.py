@@ -12,7 +12,7 @@ from .sectors import (binomial_sectors, paper_model_sectors, electron_sectors,
                       spin_phys, electron_phys)
 from .mpo import (MPO, pair_term_mpo, heisenberg_pairs, chain_pairs,
                   cylinder_pairs, cylinder_hops, triangular_hops, snake_index, spin_ops, electron_ops,
-                  heisenberg_mpo, hubbard_mpo, bulk_window)
+                  heisenberg_mpo, hubbard_mpo, bulk_window, compress_mpo)
 from .fill import (gaussian_block, env_block, assemble_flat, HeffWorkload,
                    spin_heff_workload, electron_heff_workload, hubbard_lattice_window,
                    triangular_hubbard_window, lattice_window,
@@ -22,7 +22,7 @@ __all__ = [
     "binomial_sectors", "paper_model_sectors", "electron_sectors", "spin_phys",
     "electron_phys", "MPO", "pair_term_mpo", "heisenberg_pairs", "chain_pairs",
     "cylinder_pairs", "cylinder_hops", "triangular_hops", "snake_index", "spin_ops", "electron_ops", "heisenberg_mpo",
-    "hubbard_mpo", "bulk_window", "gaussian_block", "env_block", "assemble_flat",
+    "hubbard_mpo", "bulk_window", "compress_mpo", "gaussian_block", "env_block", "assemble_flat",
     "HeffWorkload", "spin_heff_workload", "electron_heff_workload", "hubbard_lattice_window",
     "triangular_hubbard_window", "lattice_window",
     "workload_by_name",

@@ -15,7 +15,7 @@ import numpy as np
 from .sectors import (binomial_sectors, paper_model_sectors, electron_sectors,
                       spin_phys, electron_phys)
 from .mpo import (heisenberg_mpo, hubbard_mpo, chain_pairs, cylinder_pairs, cylinder_hops, triangular_hops,
-                  bulk_window)
+                  bulk_window, compress_mpo)
 
 TAG_L, TAG_R, TAG_X, TAG_SITE = 1, 2, 3, 4
 
@@ -142,14 +142,22 @@ def spin_window(couplings=SPIN_COUPLINGS):
     return bulk_window(mpo, R + 1)
 
 
-def lattice_window(Lx=6, Ly=6, J1=1.0, J2=0.5):
-    """Two-site window of the snake-ordered Lx x Ly J1-J2 Heisenberg cylinder MPO (the
-    paper's spin lattice, Section V), at the first bond triple with the largest total
-    channel count (the MPO's k there: 26 on all three bonds for 6 x 6)."""
-    n = Lx * Ly
-    mpo = heisenberg_mpo(n, cylinder_pairs(Lx, Ly, J1, J2))
+def _widest_window(mpo):
+    """The two-site window at the first bond triple with the largest total channel count."""
+    n = mpo.n_sites
     best = max(range(n - 1), key=lambda s: (mpo.bond_dim(s) + mpo.bond_dim(s + 1) + mpo.bond_dim(s + 2), -s))
     return bulk_window(mpo, best)
+
+
+def lattice_window(Lx=6, Ly=6, J1=1.0, J2=0.5, compress=False):
+    """Two-site window of the snake-ordered Lx x Ly J1-J2 Heisenberg cylinder MPO (the
+    paper's spin lattice, Section V), at the first bond triple with the largest total
+    channel count (the MPO's k there: 26 on all three bonds for 6 x 6).  compress=True
+    takes the window of the MPO compressed at the paper's SVD cutoff of 1e-13 (Section VI-B;
+    k = 20 for 6 x 6, 32 for 20 x 10)."""
+    n = Lx * Ly
+    mpo = heisenberg_mpo(n, cylinder_pairs(Lx, Ly, J1, J2))
+    return _widest_window(compress_mpo(mpo) if compress else mpo)
 
 
 def electron_window(t=1.0, U=8.0, R=5):
@@ -178,14 +186,14 @@ def hubbard_lattice_window(Lx=8, Ly=4, t=1.0, U=8.0):
     return bulk_window(mpo, best)
 
 
-def triangular_hubbard_window(Lx=6, Ly=6, t=1.0, U=8.5):
+def triangular_hubbard_window(Lx=6, Ly=6, t=1.0, U=8.5, compress=False):
     """Two-site window of the snake-ordered Lx x Ly triangular Hubbard cylinder MPO (the
     paper's electron lattice of Section V, 6 x 6 with U = 8.5), at the first bond triple
-    with the largest total channel count."""
+    with the largest total channel count.  compress=True: of the MPO compressed at the SVD
+    cutoff 1e-13 (Section VI-B: k = 26, the paper's figure for this lattice)."""
     n = Lx * Ly
     mpo = hubbard_mpo(n, triangular_hops(Lx, Ly, t), U)
-    best = max(range(n - 1), key=lambda s: (mpo.bond_dim(s) + mpo.bond_dim(s + 1) + mpo.bond_dim(s + 2), -s))
-    return bulk_window(mpo, best)
+    return _widest_window(compress_mpo(mpo) if compress else mpo)
 
 
 def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLINGS,
@@ -247,6 +255,16 @@ def workload_by_name(name):
                                                            window=lattice_window(20, 10)),
         "electron_tri_xc6_m2048": lambda: electron_heff_workload(2048, 0, name="electron_tri_xc6_m2048",
                                                                  window=triangular_hubbard_window()),
+        # the paper's lattices with their MPOs compressed at the SVD cutoff 1e-13 (Section VI-B)
+        "spin_j1j2_20x10c_m4096": lambda: spin_heff_workload(4096, 40, 0, name="spin_j1j2_20x10c_m4096",
+                                                             window=lattice_window(20, 10, compress=True)),
+        "spin_j1j2_20x10c_m200": lambda: spin_heff_workload(200, 10, 7, name="spin_j1j2_20x10c_m200",
+                                                            window=lattice_window(20, 10, compress=True)),
+        "electron_tri_xc6c_m2048": lambda: electron_heff_workload(2048, 0, name="electron_tri_xc6c_m2048",
+                                                                  window=triangular_hubbard_window(compress=True)),
+        "electron_tri_xc6c_m96": lambda: electron_heff_workload(96, 3, n_center=6, max_block=24,
+                                                                name="electron_tri_xc6c_m96",
+                                                                window=triangular_hubbard_window(compress=True)),
         "electron_tri_xc6_m96": lambda: electron_heff_workload(96, 3, n_center=6, max_block=24,
                                                                name="electron_tri_xc6_m96",
                                                                window=triangular_hubbard_window()),

@@ -305,3 +305,165 @@ def bulk_window(mpo, site):
         "labels_l": mpo.channels[site], "labels_m": mpo.channels[site + 1],
         "labels_r": mpo.channels[site + 2],
     }
+
+
+def compress_mpo(mpo, cutoff=1e-13):
+    """SVD compression of an MPO's channels (Section VI-B: the electron MPO is compressed with
+    an SVD cutoff of 1e-13).
+
+    The ``start`` and ``done`` channels are kept as they are; the other channels of every
+    bond are replaced by a minimal set of linear combinations, charge sector by charge sector
+    (channels of one sector share their charge, so the charge rule of every entry is kept).
+    Pass 1 (left to right) makes the left operators of every bond independent: at site n the
+    columns of W[n] that belong to one sector, as vectors over (wl, t, s), are decomposed as
+    U S V^T; the singular values above ``cutoff`` times the bond's largest are kept, W[n]
+    takes U's columns and S V^T is carried into the rows of W[n+1].  Pass 2 (right to left)
+    does the same with the rows of W[n] as vectors over (t, s, wr), making the right operators
+    independent; W[n] takes V^T's rows and U S goes into the columns of W[n-1].  Each pass
+    multiplies the other side's operators by a matrix of full column rank, so independence
+    won in pass 1 survives pass 2, and the channel count of every bond ends at the rank of
+    the operator Schmidt decomposition of H across it.
+
+    Hermitian structure: the MPO obeys W[conj wl, s, t, conj wr] = W[wl, t, s, wr] with the
+    channel map ``conj`` (operator A <-> its transpose).  The factors of a sector q are
+    computed once and applied to the sector -q through the partner channels, so the new
+    channel j of sector q and channel j of sector -q are transposition partners (channels of
+    charge 0 must be their own partners).  Returns a new ``MPO`` with channel labels
+    ``("start",)``, ``("c", charge, j)``, ``("done",)``.
+    """
+    N = len(mpo.W)
+    W = [np.array(w, dtype=np.float64, copy=True) for w in mpo.W]
+    nq = mpo.charges[0].shape[1]
+    d = mpo.phys.shape[0]
+    special = [{w for w, lab in enumerate(mpo.channels[b]) if lab in (("start",), ("done",))}
+               for b in range(N + 1)]
+    # per bond: ordered list of (charge, [channel indices]) for the non-special channels, the
+    # charge-conjugation partner of every channel, and the special channels' indices
+    chan = [list(range(len(mpo.channels[b]))) for b in range(N + 1)]
+    q_of = [np.array(mpo.charges[b], dtype=np.int64) for b in range(N + 1)]
+    conj = [np.array(mpo.conj[b], dtype=np.int64) for b in range(N + 1)]
+
+    def sectors(b):
+        groups = {}
+        for w in chan[b]:
+            if w in special[b]:
+                continue
+            groups.setdefault(tuple(int(v) for v in q_of[b][w]), []).append(w)
+        return groups
+
+    def plan_bond(b, groups):
+        """Canonical sectors (q >= -q) with their partner lists; checks the partner map."""
+        out = []
+        for q, ws in sorted(groups.items()):
+            mq = tuple(-v for v in q)
+            if q < mq:
+                continue
+            partners = [int(conj[b][w]) for w in ws]
+            if any(p < 0 for p in partners):
+                raise ValueError(f"bond {b}: channel without a transposition partner")
+            if q == mq:
+                if partners != ws:
+                    raise ValueError(f"bond {b}: charge-0 channels must be their own partners")
+                out.append((q, ws, None))
+            else:
+                if sorted(partners) != sorted(groups.get(mq, [])):
+                    raise ValueError(f"bond {b}: partners of sector {q} are not sector {mq}")
+                out.append((q, ws, partners))
+        return out
+
+    def rebuild_bond(b, new_sectors, left_site, right_site, left_cols, right_rows):
+        """Replace the channels of bond b: new_sectors = [(q, count)] in order; left_cols[q] /
+        right_rows[q]: the new columns of W[b-1] ([k, d, d, count]) and rows of W[b]."""
+        keep = sorted(special[b])
+        st = [w for w in keep if mpo.channels[b][w] == ("start",)]
+        dn = [w for w in keep if mpo.channels[b][w] == ("done",)]
+        labels, charges, conjn, cols, rows = [], [], [], [], []
+        for w in st:
+            labels.append(("start",)); charges.append(q_of[b][w])
+            cols.append(W[b - 1][..., w:w + 1] if left_site else None)
+            rows.append(W[b][w:w + 1] if right_site else None)
+        base = {}
+        for q, cnt in new_sectors:
+            base[q] = len(labels)
+            for j in range(cnt):
+                labels.append(("c", q, j)); charges.append(np.array(q, dtype=np.int64))
+            cols.append(left_cols[q] if left_site else None)
+            rows.append(right_rows[q] if right_site else None)
+        for w in dn:
+            labels.append(("done",)); charges.append(q_of[b][w])
+            cols.append(W[b - 1][..., w:w + 1] if left_site else None)
+            rows.append(W[b][w:w + 1] if right_site else None)
+        for lab in labels:
+            if lab[0] == "c":
+                mq = tuple(-v for v in lab[1])
+                conjn.append(base[mq] + lab[2])
+            else:
+                conjn.append(len(conjn))
+        if left_site:
+            W[b - 1] = np.concatenate(cols, axis=3)
+        if right_site:
+            W[b] = np.concatenate(rows, axis=0)
+        q_of[b] = np.array(charges, dtype=np.int64).reshape(-1, nq)
+        conj[b] = np.array(conjn, dtype=np.int64)
+        chan[b] = list(range(len(labels)))
+        special[b] = {i for i, lab in enumerate(labels) if lab[0] != "c"}
+        return labels
+
+    labels = [list(mpo.channels[b]) for b in range(N + 1)]
+    # pass 1: left to right over the bonds 1..N-1 (right bond of site n = b - 1)
+    for b in range(1, N):
+        n = b - 1
+        groups = sectors(b)
+        canon = plan_bond(b, groups)
+        k_l = W[n].shape[0]
+        dec = {}
+        for q, ws, partners in canon:
+            M = W[n][..., ws].reshape(k_l * d * d, len(ws))
+            U, S, Vt = np.linalg.svd(M, full_matrices=False)
+            dec[q] = (ws, partners, U, S, Vt)
+        smax = max((v[3][0] for v in dec.values() if len(v[3])), default=0.0)
+        new_sectors, left_cols, right_rows = [], {}, {}
+        for q, (ws, partners, U, S, Vt) in sorted(dec.items()):
+            r = int(np.sum(S > cutoff * smax))
+            T = S[:r, None] * Vt[:r]                             # new row j = sum_i T[j, i] old row i
+            for qq, lst in ((q, ws),) + ((((tuple(-v for v in q)), partners),) if partners is not None else ()):
+                M = W[n][..., lst].reshape(k_l * d * d, len(lst))
+                # new columns: M T^+ (exact: M = U S V^T, T = S_r V_r^T); for the partner
+                # sector the same T applies to the partner channels
+                C = M @ (Vt[:r].T / S[:r][None, :])
+                left_cols[qq] = C.reshape(k_l, d, d, r)
+                right_rows[qq] = np.tensordot(T, W[b][lst], axes=(1, 0))
+        order = sorted(set(left_cols))
+        new_sectors = [(q, left_cols[q].shape[3]) for q in order]
+        labels[b] = rebuild_bond(b, new_sectors, True, True, left_cols, right_rows)
+    # pass 2: right to left over the bonds N-1..1 (left bond of site n = b)
+    for b in range(N - 1, 0, -1):
+        n = b
+        groups = sectors(b)
+        canon = plan_bond(b, groups)
+        k_r = W[n].shape[3]
+        dec = {}
+        for q, ws, partners in canon:
+            M = W[n][ws].reshape(len(ws), d * d * k_r)
+            U, S, Vt = np.linalg.svd(M, full_matrices=False)
+            dec[q] = (ws, partners, U, S, Vt)
+        smax = max((v[3][0] for v in dec.values() if len(v[3])), default=0.0)
+        left_cols, right_rows = {}, {}
+        for q, (ws, partners, U, S, Vt) in sorted(dec.items()):
+            r = int(np.sum(S > cutoff * smax))
+            T = U[:, :r] * S[None, :r]                           # old row i = sum_j T[i, j] new row j
+            for qq, lst in ((q, ws),) + ((((tuple(-v for v in q)), partners),) if partners is not None else ()):
+                M = W[n][lst].reshape(len(lst), d * d * k_r)
+                R_new = (U[:, :r].T / S[:r][:, None]) @ M         # T^+ M
+                right_rows[qq] = R_new.reshape(r, d, d, k_r)
+                left_cols[qq] = np.tensordot(W[b - 1][..., lst], T, axes=(3, 0))
+        order = sorted(set(left_cols))
+        new_sectors = [(q, left_cols[q].shape[3]) for q in order]
+        labels[b] = rebuild_bond(b, new_sectors, True, True, left_cols, right_rows)
+    charges = [np.asarray(q_of[b], dtype=np.int32).reshape(-1, nq) for b in range(N + 1)]
+    conjs = [np.asarray(conj[b], dtype=np.int32) for b in range(N + 1)]
+    # drop round-off below the cutoff's scale so that structurally zero blocks stay zero
+    for n in range(N):
+        scale = np.abs(W[n]).max()
+        W[n][np.abs(W[n]) < 1e-15 * scale] = 0.0
+    return MPO(W=W, channels=labels, charges=charges, conj=conjs, phys=mpo.phys, op_charge=dict(mpo.op_charge))
