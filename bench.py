@@ -8,9 +8,13 @@ environments, Gaussian two-site tensor (seed 2).  One step = one heff_apply (ope
 preparation + pack + the two grouped GEMMs) on inputs resident in HBM.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the
-host cores instead (bounded sample per step).  With torchrun (N > 1) every rank runs
-an independent problem (its own two-site tensor): weak scaling, no collective on the
-data path; the time is the maximum over ranks.
+host cores instead (bounded sample per step).  With torchrun (N > 1) the default is one
+apply spread over the ranks by row shards (the left sectors a' of y, assigned by
+longest-processing-time over their GEMM flops): each rank runs its shard's plan into a
+zeroed y and an all-reduce of y (NCCL) completes the apply on every rank (strong
+scaling).  ``--mode replicas`` instead runs an independent problem per rank (its own
+two-site tensor, no collective on the data path; weak scaling).  The time is the maximum
+over ranks.
 """
 import argparse
 import json
@@ -42,14 +46,15 @@ NCU_SRC_SHA = "2e7c1653dc49f112"
 
 def _src_sha():
     """Hash of the device code of tc_gemm.cu and apply.cu (each file up to its host-side
-    section), the code the ncu figures were measured on."""
+    section) and of the PTX wrappers they include, the code the ncu figures were measured on."""
     import hashlib
     h = hashlib.sha256()
     for name, mark in (("tc_gemm.cu", b"// ---------------------------------------------------------------- host side"),
-                       ("apply.cu", b"// ------------------------------------------------------------------ host side")):
+                       ("apply.cu", b"// ------------------------------------------------------------------ host side"),
+                       ("tc_ptx.cuh", b"")):
         with open(os.path.join(ROOT, "paper_2007_05540_gb300", "csrc", name), "rb") as f:
             txt = f.read()
-        cut = txt.find(mark)
+        cut = txt.find(mark) if mark else -1
         h.update(txt[:cut] if cut >= 0 else txt)
     return h.hexdigest()[:16]
 
@@ -63,6 +68,8 @@ def algorithmic_bytes(lays, io_bytes):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--mode", default="shard", choices=["shard", "replicas"],
+                    help="N > 1: row shards of one apply + all-reduce of y (default), or independent problems")
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -147,6 +154,17 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ ranks
+def sum_over_ranks(v, device):
+    """The sum of a per-rank float over the process group; the identity without one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def max_over_ranks(v, device):
     """The maximum of a per-rank float over the process group (the job's time is the
     slowest rank's); the identity without a process group."""
@@ -160,9 +178,23 @@ def max_over_ranks(v, device):
 
 
 def rank_batch(rank):
-    """Each rank's problem: the shared L, W, R of the workload and its own two-site tensor
-    (batch entry = rank), so ranks are independent (weak scaling, no data-path collective)."""
+    """Each rank's problem in replicas mode: the shared L, W, R of the workload and its own
+    two-site tensor (batch entry = rank), so ranks are independent (weak scaling, no
+    data-path collective)."""
     return int(rank)
+
+
+def sharded_step(apply_shard, y):
+    """One row-sharded apply: the other shards' y blocks are zero here, this rank writes its
+    own (apply_shard(y)), and the sum over the ranks (an all-reduce) is the whole y on every
+    rank.  Without a process group of more than one rank it is the plain apply."""
+    import torch.distributed as dist
+    multi = dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+    if multi:
+        y.zero_()
+    apply_shard(y)
+    if multi:
+        dist.all_reduce(y)
 
 
 # ------------------------------------------------------------------ problem
@@ -466,20 +498,29 @@ def env_update_timing(w, dev, stream):
     Wv = W_l.assemble(lambda k: w.W1[k])
     old = old_l.assemble(lambda k: w.L_block(k))
     plan = heff.heff_env_plan_create(old_l.handle, site_l.handle, W_l.handle, new_l.handle, Wv, "left")
+    out = {"m_old": m_new, "m_new": m_new,
+           "note": "left environment L[a',w,a] extended by one site; fp64: FP64 block products on CUDA cores, "
+                   "bf16x3: the same products on the tensor cores (BF16 hi/lo split, FP32 accumulation); "
+                   "rel_err_bf16x3: norm-wise against the FP64 result"}
     try:
         ws = torch.empty(heff.heff_env_workspace_size(plan), dtype=torch.uint8, device=dev)
         d = [torch.from_numpy(v).to(dev) for v in (old, site, Wv)]
-        env = torch.empty(new_l.nelem, dtype=torch.float64, device=dev)
-
-        def f():
-            heff.heff_env_update(plan, d[0], d[1], d[2], env, ws, stream)
-        f()
-        ms = _events_ms(f, 3, stream)
+        env = {p: torch.empty(new_l.nelem, dtype=torch.float64, device=dev) for p in ("fp64", "bf16x3")}
         fl = heff.heff_env_flops(plan)
+        out["flops"] = fl
+        for prec in ("fp64", "bf16x3"):
+            heff.heff_env_plan_set_precision(plan, prec)
+
+            def f(prec=prec):
+                heff.heff_env_update(plan, d[0], d[1], d[2], env[prec], ws, stream)
+            f()
+            ms = _events_ms(f, 3, stream)
+            out[prec] = {"ms": ms, "tflops": fl / (ms * 1e-3) / 1e12}
+        out["rel_err_bf16x3"] = float(torch.linalg.norm(env["bf16x3"] - env["fp64"]) / torch.linalg.norm(env["fp64"]))
+        out["status_bf16x3"] = heff.heff_env_status(plan, ws, stream)
     finally:
         heff.heff_env_plan_destroy(plan)
-    return {"ms": ms, "flops": fl, "tflops": fl / (ms * 1e-3) / 1e12, "m_old": m_new, "m_new": m_new,
-            "note": "left environment L[a',w,a] extended by one site (FP64 block products on CUDA cores)"}
+    return out
 
 
 def backward_timing(dev, stream):
@@ -490,27 +531,33 @@ def backward_timing(dev, stream):
     for name, limit in (("spin_m1024", 0), ("spin_m4096", 256 << 20)):
         w, lays, bufs = make_problem(name, 0)
         Ll, W1l, W2l, Rl, xl = lays
-        plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], "fp64", "f64")
         g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle, bufs["W1"],
                                        bufs["W2"], limit)
         try:
-            aws = plan.workspace(dev)
             gws = torch.empty(heff.heff_grad_workspace_size(g), dtype=torch.uint8, device=dev)
             d = {k: torch.from_numpy(np.asarray(v)).to(dev) for k, v in bufs.items()}
             rho = torch.empty((), dtype=torch.float64, device=dev)
-            outs = [torch.empty_like(d[k]) for k in ("x", "L", "R", "W1", "W2")]
+            res[name] = {"chunks": heff.heff_grad_chunks(g), "grad_workspace_MB": heff.heff_grad_workspace_size(g) / 1e6}
+            grads = {}
+            for prec in ("fp64", "bf16x3"):
+                # the apply inside (for rho and dx) and the block products in the same precision
+                plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, "f64")
+                aws = plan.workspace(dev)
+                heff.heff_grad_plan_set_precision(g, prec)
+                outs = [torch.empty_like(d[k]) for k in ("x", "L", "R", "W1", "W2")]
 
-            def f():
-                heff.heff_backward(g, plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], rho, *outs, aws,
-                                   gws, stream)
-            f()
-            ms = _events_ms(f, 2, stream)
-            res[name] = {"ms": ms, "chunks": heff.heff_grad_chunks(g),
-                         "grad_workspace_MB": heff.heff_grad_workspace_size(g) / 1e6,
-                         "apply": "fp64", "rho": float(rho)}
+                def f(plan=plan, aws=aws, outs=outs):
+                    heff.heff_backward(g, plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], rho, *outs, aws,
+                                       gws, stream)
+                f()
+                ms = _events_ms(f, 2, stream)
+                grads[prec] = outs
+                res[name][prec] = {"ms": ms, "rho": float(rho)}
+                del plan, aws
+            res[name]["rel_err_bf16x3"] = {k: float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for k, a, b in
+                                          zip(("dx", "dL", "dR", "dW1", "dW2"), grads["bf16x3"], grads["fp64"])}
         finally:
             heff.heff_grad_plan_destroy(g)
-        del plan
     return res
 
 
@@ -604,9 +651,11 @@ def run_ours(args):
     prec = args.precision
     io = "f64" if prec == "fp64" else "f32"
     dt = torch.float64 if io == "f64" else torch.float32
-    w, lays, bufs = make_problem(args.workload, rank_batch(rank))
+    shard = world > 1 and args.mode == "shard"
+    w, lays, bufs = make_problem(args.workload, 0 if shard else rank_batch(rank))
     Ll, W1l, W2l, Rl, xl = lays
-    plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, io)
+    plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, io,
+                     shard=(rank, world) if shard else None)
     st = plan.stats
     d = {k: torch.from_numpy(np.asarray(v)).to(dev, dt) for k, v in bufs.items()}
     ws = plan.workspace(dev)
@@ -614,8 +663,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
 
+    def apply_shard(out):
+        heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], out, ws, stream)
+
     def step():
-        heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y, ws, stream)
+        sharded_step(apply_shard, y)
 
     # one-time plan setup (outside the timed region): tile width per GEMM by measurement
     tune_ms = None
@@ -684,6 +736,17 @@ def run_ours(args):
 
     def e2e_step(k):
         j = k % 2
+        if shard:
+            # each rank: its inputs in, its shard, the all-reduce of y, y out
+            with torch.cuda.stream(streams[j]):
+                dj = {kk: t.to(dev, non_blocking=True) for kk, t in host.items()}
+                yj = torch.empty_like(dj["x"])
+
+                def ap(out, dj=dj):
+                    heff.heff_apply(plan.handle, dj["L"], dj["W1"], dj["W2"], dj["R"], dj["x"], out, wss[j], streams[j])
+                sharded_step(ap, yj)
+                y_host[j].copy_(yj, non_blocking=True)
+            return
         heff.heff_apply_host(plan.handle, host["L"], host["W1"], host["W2"], host["R"], host["x"], y_host[j],
                              staging[j], wss[j], streams[j])
     heff.heff_plan_set_timing(plan.handle, False)
@@ -706,7 +769,10 @@ def run_ours(args):
 
     peaks, peak_src = measured_peaks()
     canonical = plan.flops_canonical
-    value = world * 1000.0 / ms
+    per_step = 1 if shard else world          # applies completed by the job per step
+    if shard:                                 # a shard plan counts its own share
+        canonical = sum_over_ranks(canonical, dev)
+    value = per_step * 1000.0 / ms
     g_ms = {"gemm1": phases[2], "gemm2": phases[3]}
     dom = max(g_ms, key=g_ms.get)
     useful = float(st[18] if dom == "gemm1" else st[19])
@@ -752,14 +818,17 @@ def run_ours(args):
     # the apply an eigensolver pays per Krylov step: heff_apply_prepared (pack + GEMMs) with
     # the operators prepared once
     heff.heff_prepare(plan.handle, d["L"], d["W1"], d["W2"], d["R"], ws, stream)
+
+    def prep_step():
+        sharded_step(lambda out: heff.heff_apply_prepared(plan.handle, d["x"], out, ws, stream), y)
     for _ in range(3):
-        heff.heff_apply_prepared(plan.handle, d["x"], y, ws, stream)
-    prep_ms = max_over_ranks(_events_ms(lambda: heff.heff_apply_prepared(plan.handle, d["x"], y, ws, stream),
-                                        max(args.steps, 10), stream, flush), dev)
+        prep_step()
+    prep_ms = max_over_ranks(_events_ms(prep_step, max(args.steps, 10), stream, flush), dev)
 
     out = {
         "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": {"bf16x3": "bf16x3->f32", "tf32x3": "tf32x3->f32", "fp64": "f64"}[prec],
         "data": "synthetic (seeded; no dataset)",
         "config": {"workload": args.workload, "m": int(w.alpha_d.sum()), "sectors": int(len(w.alpha_d)),
@@ -767,16 +836,17 @@ def run_ours(args):
                    "tile_variant": list(tile_n),
                    "autotune_ms": [round(v, 4) for v in tune_ms] if tune_ms is not None else None,
                    "l2": "flushed (512 MB write) between timed steps; working set > L2",
-                   "parallelism": f"independent problems per rank x{world}"},
+                   "parallelism": (f"row shards of one apply x{world} (LPT over left sectors) + NCCL all-reduce of y"
+                                   if shard else f"independent problems per rank x{world}")},
         "tflops_canonical": canonical * value / 1e12,
         "flops_per_apply": canonical,
         "phase_ms": {"prepare": phases[0], "pack": phases[1], "gemm1": phases[2], "gemm2": phases[3]},
-        "apply_prepared": {"value": world * 1000.0 / prep_ms, "unit": "applies/s", "ms": prep_ms,
+        "apply_prepared": {"value": per_step * 1000.0 / prep_ms, "unit": "applies/s", "ms": prep_ms,
                            "tflops_canonical": canonical / (prep_ms * 1e-3) / 1e12,
                            "note": "heff_apply_prepared (pack + GEMM 1 + GEMM 2; operators prepared once), "
                                    "the matvec an eigensolver repeats"},
         "wall_s": wall,
-        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "applies/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": per_step * 1000.0 / e2e_ms, "unit": "applies/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": roof,

@@ -314,6 +314,23 @@ int heff_env_update(heff_env_plan* plan, const double* env_old, const double* si
 void heff_env_plan_destroy(heff_env_plan* plan);
 
 /*
+ * Arithmetic of the environment update's block products.  HEFF_PREC_FP64 (the default):
+ * FP64 on the CUDA cores.  HEFF_PREC_BF16X3: on the tensor cores, each operand element split
+ * into bf16 hi + lo and three products per K block, FP32 accumulation (about 1e-5 relative
+ * per product); the tensors stay FP64 buffers and the call sequence is unchanged.  Errors:
+ * INVALID_ARG, UNSUPPORTED (another precision), CUDA.
+ */
+int heff_env_plan_set_precision(heff_env_plan* plan, int32_t precision);
+
+/*
+ * Read and clear the sticky error flag of an environment-update workspace: HEFF_ERR_TIMEOUT
+ * when a bounded wait of a tensor-core product expired in the last update (its output is
+ * then incomplete; the context stays usable), else HEFF_OK (always for FP64 plans).
+ * Synchronises `stream`.  Errors: INVALID_ARG, WORKSPACE, CUDA.
+ */
+int heff_env_status(const heff_env_plan* plan, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Two-site tensor of the MPS (Fig. 1d; the starting vector of a bond's eigensolve in the
  * two-site sweep of Section II-C): x[a, s1, s2, b] = sum_c A[a, s1, c] B[c, s2, b].
  * A and B have flows (+1, +1, -1) and share the bond c; x is the (a, s1, s2, b) layout of
@@ -359,6 +376,17 @@ int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L, const dou
                   double* dL, double* dR, double* dW1, double* dW2, void* apply_ws,
                   size_t apply_ws_bytes, void* grad_ws, size_t grad_ws_bytes, void* stream);
 void heff_grad_plan_destroy(heff_grad_plan* g);
+
+/*
+ * Arithmetic of the gradients' block products (U, T1, dL, dR): HEFF_PREC_FP64 (the default,
+ * CUDA cores) or HEFF_PREC_BF16X3 (tensor cores, bf16 hi/lo split, FP32-accumulated; about
+ * 1e-5 relative).  The scalars, dx and the W gradients' reductions stay FP64; buffers stay
+ * FP64.  heff_grad_status reads and clears the gradient workspace's sticky error flag
+ * (HEFF_ERR_TIMEOUT when a bounded wait of a tensor-core product expired; synchronises).
+ * Errors: INVALID_ARG, UNSUPPORTED (another precision), WORKSPACE, CUDA.
+ */
+int heff_grad_plan_set_precision(heff_grad_plan* g, int32_t precision);
+int heff_grad_status(const heff_grad_plan* g, void* grad_ws, size_t grad_ws_bytes, void* stream);
 
 /*
  * Block SVD split of the two-site tensor with truncation (Section IV: the tensor is

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libheff.so")
-SOURCES = ["layout.cpp", "plan.cpp", "apply.cu", "tc_gemm.cu", "noalloc.cu", "lanczos.cu",
+SOURCES = ["layout.cpp", "plan.cpp", "apply.cu", "tc_gemm.cu", "noalloc.cu", "lanczos.cu", "blockops_tc.cu",
            "blockops.cu", "env.cu", "grad.cu", "svd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", "-Xptxas", "-v",

@@ -75,7 +75,7 @@ __device__ __forceinline__ void store_row(uint32_t hi, uint32_t lo, int r, const
     }
 }
 
-__global__ void __launch_bounds__(BT_THREADS, 1) bgemm_tc_kernel(BtArgs g) {
+__global__ void __launch_bounds__(BT_THREADS, 2) bgemm_tc_kernel(BtArgs g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + BT_BAR);

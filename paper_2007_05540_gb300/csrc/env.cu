@@ -23,8 +23,10 @@ using heff::BProd;
 
 struct heff_env_plan {
     int side = 0;
+    int precision = HEFF_PREC_FP64;   // of the block products
     BList step1, step2;
     int64_t ws_elems = 0;      // intermediate (X or Y) in doubles
+    size_t off_flag = 0;       // sticky error flag of the tensor-core products (one int)
     size_t ws_bytes = 0;
     bool uploaded = false;
 };
@@ -179,7 +181,8 @@ extern "C" int heff_env_plan_create(const heff_layout* env_old, const heff_layou
             }
         }
         P->ws_elems = ioff;
-        P->ws_bytes = (size_t)((ioff + 31) / 32 * 32) * sizeof(double) + 256;
+        P->off_flag = (size_t)((ioff + 31) / 32 * 32) * sizeof(double);
+        P->ws_bytes = P->off_flag + 256;
     } catch (const std::bad_alloc&) {
         delete P;
         return fail(HEFF_ERR_OOM, "out of host memory while planning the environment update");
@@ -225,9 +228,55 @@ extern "C" int heff_env_update(heff_env_plan* plan, const double* env_old, const
         return fail(HEFF_ERR_WORKSPACE, "environment workspace of %zu bytes, needs %zu (256-byte aligned)",
                     workspace_bytes, plan->ws_bytes);
     double* X = static_cast<double*>(workspace);
+    int* err = reinterpret_cast<int*>(static_cast<char*>(workspace) + plan->off_flag);
     int rc;
-    if ((rc = heff::launch_bgemm(plan->step1, env_old, site, X, nullptr, nullptr, 1.0, stream))) return rc;
-    return heff::launch_bgemm(plan->step2, site, X, env_new, W, nullptr, 1.0, stream);
+    if (plan->precision != HEFF_PREC_FP64) {
+        cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    if ((rc = heff::launch_blist(plan->precision, plan->step1, env_old, site, X, nullptr, nullptr, 1.0, stream,
+                                 nullptr, err)))
+        return rc;
+    return heff::launch_blist(plan->precision, plan->step2, site, X, env_new, W, nullptr, 1.0, stream, nullptr, err);
+}
+
+extern "C" int heff_env_plan_set_precision(heff_env_plan* plan, int32_t precision) {
+    heff::clear_error();
+    if (!plan) return fail(HEFF_ERR_INVALID_ARG, "heff_env_plan_set_precision: null plan");
+    if (precision != HEFF_PREC_FP64 && precision != HEFF_PREC_BF16X3)
+        return fail(HEFF_ERR_UNSUPPORTED, "environment updates run in HEFF_PREC_FP64 or HEFF_PREC_BF16X3");
+    if (precision == plan->precision) return HEFF_OK;
+    const int tile = precision == HEFF_PREC_FP64 ? 64 : 128;
+    heff::blist_free(plan->step1);
+    heff::blist_free(plan->step2);
+    plan->step1.retile(tile, tile);
+    plan->step2.retile(tile, tile);
+    plan->precision = precision;
+    if (plan->uploaded) {
+        int rc;
+        if ((rc = heff::blist_upload(plan->step1)) || (rc = heff::blist_upload(plan->step2))) {
+            plan->uploaded = false;
+            return rc;
+        }
+    }
+    return HEFF_OK;
+}
+
+extern "C" int heff_env_status(const heff_env_plan* plan, void* workspace, size_t workspace_bytes, void* stream) {
+    heff::clear_error();
+    if (!plan || !workspace) return fail(HEFF_ERR_INVALID_ARG, "heff_env_status: null argument");
+    if (plan->precision == HEFF_PREC_FP64) return HEFF_OK;
+    if (workspace_bytes < plan->ws_bytes) return fail(HEFF_ERR_WORKSPACE, "heff_env_status: workspace too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* d = reinterpret_cast<int*>(static_cast<char*>(workspace) + plan->off_flag);
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && flag) e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (e == cudaSuccess && flag) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_env_status: %s", cudaGetErrorString(e));
+    if (flag) return fail(HEFF_ERR_TIMEOUT, "a bounded device-side wait of the environment update expired");
+    return HEFF_OK;
 }
 
 extern "C" void heff_env_plan_destroy(heff_env_plan* plan) {

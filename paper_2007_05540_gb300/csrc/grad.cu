@@ -45,8 +45,9 @@ struct heff_grad_plan {
     std::vector<int32_t> dw1_off, dw1_terms;   // per W1 entry: pairs (G idx, W2 idx)
     std::vector<int32_t> dw2_off, dw2_terms;   // per W2 entry: pairs (G idx, W1 idx)
     int64_t nx = 0, nR = 0, nW1 = 0, nW2 = 0, ng = 0;
-    int64_t off_U = 0, off_W12 = 0, off_G = 0, off_sc = 0, off_part = 0;
+    int64_t off_U = 0, off_W12 = 0, off_G = 0, off_sc = 0, off_part = 0, off_flag = 0;
     size_t ws_bytes = 0;
+    int precision = HEFF_PREC_FP64;   // of the block products (U, T1, dL, dR)
     int64_t npart = 0;
     // device copies
     BDot* d_xdots = nullptr; int32_t* d_xoff = nullptr;
@@ -358,6 +359,7 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
         g->off_sc = o; o += 32;
         g->npart = std::max<int64_t>(max_gd, (int64_t)g->xdots.size());
         g->off_part = o; o += al(g->npart);
+        g->off_flag = o; o += 32;          // sticky error flag of the tensor-core products
         g->ws_bytes = (size_t)o * sizeof(double);
     } catch (const std::bad_alloc&) {
         delete g;
@@ -425,6 +427,9 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
     double* ws = static_cast<double*>(grad_ws);
     double *Ureg = ws + g->off_U, *W12 = ws + g->off_W12, *G = ws + g->off_G;
     double *sc = ws + g->off_sc, *part = ws + g->off_part;
+    int* err = reinterpret_cast<int*>(ws + g->off_flag);
+    if (g->precision != HEFF_PREC_FP64 && cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+        return fail(HEFF_ERR_CUDA, "heff_backward: memset failed");
     // y = K x into dx (dx is overwritten by the gradient below)
     int rc = heff_apply(plan, L, W1, W2, R, x, dx, apply_ws, apply_ws_bytes, stream);
     if (rc) return rc;
@@ -449,10 +454,11 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
         // U at the start of the shared region, T1 at the chunk's t_base: the lists hold
         // offsets within the region
         double *U = Ureg, *T1 = Ureg;
-        if ((rc = heff::launch_bgemm(c.U, x, R, U, nullptr, nullptr, 1.0, stream))) return rc;
-        if ((rc = heff::launch_bgemm(c.T1, L, x, T1, nullptr, nullptr, 1.0, stream))) return rc;
-        if ((rc = heff::launch_bgemm(c.dL, U, x, dL, W12, nullptr, 1.0, stream, sc))) return rc;
-        if ((rc = heff::launch_bgemm(c.dR, x, T1, dR, W12, nullptr, 1.0, stream, sc))) return rc;
+        const int pr = g->precision;
+        if ((rc = heff::launch_blist(pr, c.U, x, R, U, nullptr, nullptr, 1.0, stream, nullptr, err))) return rc;
+        if ((rc = heff::launch_blist(pr, c.T1, L, x, T1, nullptr, nullptr, 1.0, stream, nullptr, err))) return rc;
+        if ((rc = heff::launch_blist(pr, c.dL, U, x, dL, W12, nullptr, 1.0, stream, sc, err))) return rc;
+        if ((rc = heff::launch_blist(pr, c.dR, x, T1, dR, W12, nullptr, 1.0, stream, sc, err))) return rc;
         if ((rc = heff::launch_block_dots(c.d_gdots, (int)c.gdots.size(), c.d_goff, T1, U, G, (int)g->ng, part, 1.0,
                                           stream, streamed)))
             return rc;
@@ -466,6 +472,42 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
     heff::count_launches(4);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_backward: %s", cudaGetErrorString(e));
+    return HEFF_OK;
+}
+
+extern "C" int heff_grad_plan_set_precision(heff_grad_plan* g, int32_t precision) {
+    heff::clear_error();
+    if (!g) return fail(HEFF_ERR_INVALID_ARG, "heff_grad_plan_set_precision: null plan");
+    if (precision != HEFF_PREC_FP64 && precision != HEFF_PREC_BF16X3)
+        return fail(HEFF_ERR_UNSUPPORTED, "gradient block products run in HEFF_PREC_FP64 or HEFF_PREC_BF16X3");
+    if (precision == g->precision) return HEFF_OK;
+    const int tile = precision == HEFF_PREC_FP64 ? 64 : 128;
+    int rc = HEFF_OK;
+    for (GradChunk& c : g->chunks)
+        for (BList* b : {&c.U, &c.T1, &c.dL, &c.dR}) {
+            heff::blist_free(*b);
+            b->retile(tile, tile);
+            if (g->uploaded && !rc) rc = heff::blist_upload(*b);
+        }
+    g->precision = precision;
+    if (rc) g->uploaded = false;
+    return rc;
+}
+
+extern "C" int heff_grad_status(const heff_grad_plan* g, void* grad_ws, size_t grad_ws_bytes, void* stream) {
+    heff::clear_error();
+    if (!g || !grad_ws) return fail(HEFF_ERR_INVALID_ARG, "heff_grad_status: null argument");
+    if (g->precision == HEFF_PREC_FP64) return HEFF_OK;
+    if (grad_ws_bytes < g->ws_bytes) return fail(HEFF_ERR_WORKSPACE, "heff_grad_status: workspace too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* d = reinterpret_cast<int*>(static_cast<double*>(grad_ws) + g->off_flag);
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && flag) e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (e == cudaSuccess && flag) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "heff_grad_status: %s", cudaGetErrorString(e));
+    if (flag) return fail(HEFF_ERR_TIMEOUT, "a bounded device-side wait of the gradient products expired");
     return HEFF_OK;
 }
 

@@ -26,7 +26,9 @@
 // in 16-byte row pieces (several rows per store instruction); y (GEMM 2, per-block pitch)
 // leaves through the same transpose in 128-byte row stores.
 // Every mbarrier wait is bounded (about a second); on expiry the CTA raises the
-// workspace error flag, stops issuing work, frees its TMEM and returns.
+// workspace error flag and stops issuing work; the producer then waits (bounded) for the
+// loads it has already issued and the MMA issuer for the MMAs it has already issued, and
+// only then is the tensor memory freed and the CTA (with its ring) released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -36,6 +38,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 // work order of batched launches: 1 = the batch entries of a task consecutively
 #ifndef HEFF_BATCH_INNER
@@ -44,6 +47,8 @@
 
 namespace heff {
 namespace {
+
+using namespace ptx;
 
 // Warps: 0 TMA producer, 1 MMA issuer, then the epilogue: 8 warps for BF16X3 (two per
 // tensor-memory lane quarter, alternating 32-column chunks), 4 for TF32X3 (whose 32 x 32
@@ -56,7 +61,6 @@ template <int PREC> __host__ __device__ constexpr int tc_epi_warps() {
 }
 template <int PREC> __host__ __device__ constexpr int tc_threads() { return 64 + 32 * tc_epi_warps<PREC>(); }
 constexpr int TM = 128;
-constexpr long long WAIT_CYCLES = 3ll << 30;   // ~1.5 s at 2 GHz
 
 // Shared-memory ring: STAGES x {A_hi, A_lo (128 rows), B_hi, B_lo (TN rows)}, each row SWZ
 // bytes of one K block (SWZ = 64: 32 bf16 / 16 fp32; SWZ = 128: 64 bf16 / 32 fp32), then
@@ -83,47 +87,6 @@ struct TcMaps {
     CUtensorMap c;      // T store map: 32 x 32 boxes (GEMM 1 only)
     CUtensorMap bq;     // B operand, 32-row box (a CTA pair's half of a narrow B tile)
 };
-
-__device__ __forceinline__ uint32_t su32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase.  Returns false when the CTA has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
-    const uint32_t a = su32(bar);
-    if (mbar_try(a, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try(a, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_CYCLES) {
-            *abort_flag = 1;
-            atomicExch(err, 1);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
-}
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
@@ -170,10 +133,6 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
     }
 }
 
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
 
 // CTA-pair forms (cta_group::2): the MMA of a pair is issued by the even CTA and reads A
 // and its half of B from each CTA's shared memory at the same offsets; its commit arrives
@@ -196,6 +155,12 @@ __device__ __forceinline__ void umma2_commit_both(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
         ::"r"(su32(bar)), "h"((uint16_t)3) : "memory");
+}
+
+// Arrives on this CTA's barrier once every MMA of the pair issued before it has completed.
+__device__ __forceinline__ void umma2_commit_own(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
 }
 
 // TMA load into this CTA's shared memory, completion signalled on a barrier of either CTA of
@@ -242,27 +207,6 @@ __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 struct TcArgs {
     const GemmTask* tasks;
@@ -299,13 +243,15 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;      // [2]
     uint64_t* tempty = tfull + 2;          // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* drain = tempty + 2;          // the MMAs issued before an abort have completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], tc_epi_warps<PREC>() * CL); }
+        mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -352,6 +298,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
         uint32_t st = 0, ph = 0;               // ring stage and its phase parity
+        uint32_t issued = 0;                   // stages filled so far
         bool ok = true;
         // the next task and the next segment are loaded one step ahead, so their latency
         // overlaps with the current loads instead of draining the ring
@@ -393,8 +340,19 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                         tma_load_pair(base + 2 * S::A_BYTES, mh, fb, k, bh + (int)rank * half);
                         tma_load_pair(base + 2 * S::A_BYTES + S::B_BYTES, mh, fb, k, bl + (int)rank * half);
                     }
+                    ++issued;
                     if (++st == STAGES) { st = 0; ph ^= 1; }
                 }
+            }
+        }
+        if (!ok && rank == 0) {
+            // aborted: the loads already issued still write this CTA's ring (and, for a pair,
+            // the odd CTA's) and complete on these barriers; wait (bounded) for the last
+            // STAGES fills to land before the shared memory can go away
+            const uint32_t nf = issued < (uint32_t)STAGES ? issued : (uint32_t)STAGES;
+            for (uint32_t i = 1; i <= nf; ++i) {
+                const uint32_t f = issued - i;
+                mbar_wait_drain(&full[f % STAGES], (f / STAGES) & 1);
             }
         }
         if constexpr (CL > 1) {
@@ -472,6 +430,13 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     ++ccount;
                 }
             }
+        }
+        if (!ok) {
+            // aborted: wait (bounded) for the MMAs already issued, which read the ring(s) and
+            // write tensor memory, before either is released
+            if constexpr (CL == 1) umma_commit(drain);
+            else umma2_commit_own(drain);
+            mbar_wait_drain(drain, 0);
         }
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue

@@ -87,11 +87,15 @@ _sig = {
     "heff_grad_workspace_size": (C.c_int, [_vp, _P(_sz)]),
     "heff_backward": (C.c_int, [_vp] * 13 + [_vp, _sz, _vp, _sz, _vp]),
     "heff_grad_plan_destroy": (None, [_vp]),
+    "heff_grad_plan_set_precision": (C.c_int, [_vp, _i32]),
+    "heff_grad_status": (C.c_int, [_vp, _vp, _sz, _vp]),
     "heff_env_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _P(C.c_double), _i32, _P(_vp)]),
     "heff_env_workspace_size": (C.c_int, [_vp, _P(_sz)]),
     "heff_env_flops": (C.c_int, [_vp, _P(C.c_double)]),
     "heff_env_update": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_env_plan_destroy": (None, [_vp]),
+    "heff_env_plan_set_precision": (C.c_int, [_vp, _i32]),
+    "heff_env_status": (C.c_int, [_vp, _vp, _sz, _vp]),
     "heff_lanczos_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
     "heff_ground_state_workspace_size": (C.c_int, [_vp, _i32, _P(_sz)]),
     "heff_ground_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, C.c_double, _vp,
@@ -392,6 +396,16 @@ def heff_grad_plan_destroy(g):
     _lib.heff_grad_plan_destroy(g)
 
 
+def heff_grad_plan_set_precision(g, precision):
+    """"fp64" (default) or "bf16x3" (tensor-core block products; FP64 buffers)."""
+    _check(_lib.heff_grad_plan_set_precision(g, PREC[precision]), "heff_grad_plan_set_precision")
+
+
+def heff_grad_status(g, grad_ws, stream=None):
+    """Read and clear the gradient workspace's error flag; returns the status code (0 or -6)."""
+    return int(_lib.heff_grad_status(g, _ptr(grad_ws), _nbytes(grad_ws), _stream(stream)))
+
+
 def heff_env_plan_create(env_old, site, W, env_new, W_host, side):
     w = np.ascontiguousarray(W_host, dtype=np.float64)
     out = _vp()
@@ -419,6 +433,16 @@ def heff_env_update(plan, env_old, site, W, env_new, ws, stream=None):
 
 def heff_env_plan_destroy(plan):
     _lib.heff_env_plan_destroy(plan)
+
+
+def heff_env_plan_set_precision(plan, precision):
+    """"fp64" (default) or "bf16x3" (tensor-core block products; FP64 buffers)."""
+    _check(_lib.heff_env_plan_set_precision(plan, PREC[precision]), "heff_env_plan_set_precision")
+
+
+def heff_env_status(plan, ws, stream=None):
+    """Read and clear the env workspace's error flag; returns the status code (0 or -6)."""
+    return int(_lib.heff_env_status(plan, _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def heff_davidson_workspace_size(plan, max_vecs):

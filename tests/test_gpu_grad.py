@@ -31,7 +31,7 @@ def _dev(a):
 
 
 class GradRun:
-    def __init__(self, w, prec="fp64", ws_limit=0, problem=None, plan=None):
+    def __init__(self, w, prec="fp64", ws_limit=0, problem=None, plan=None, gprec="fp64"):
         self.w = w
         self.lays, self.bufs = problem if problem is not None else library_problem(w)
         Ll, W1l, W2l, Rl, xl = self.lays
@@ -39,6 +39,7 @@ class GradRun:
                                                             prec, "f64")
         self.g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle,
                                             self.bufs["W1"], self.bufs["W2"], ws_limit)
+        heff.heff_grad_plan_set_precision(self.g, gprec)
         self.aws = self.plan.workspace()
         self.gws = torch.empty(heff.heff_grad_workspace_size(self.g), dtype=torch.uint8, device="cuda")
 
@@ -200,3 +201,44 @@ def test_backward_streamed_at_m4096():
         sum(float(np.vdot(v, v)) for v in x.blocks.values())
     print(f"m=4096 rho {rho:.15f} oracle {rho_o:.15f}")
     assert abs(rho - rho_o) < 1e-11 * abs(rho_o)
+
+
+# ---------------------------------------------------------------- tensor-core block products
+@pytest.mark.parametrize("name", ["spin_m200", "electron_m256"])
+def test_backward_bf16x3_matches_oracle(name):
+    """BF16x3 apply and BF16x3 block products (FP32-accumulated): every gradient within the
+    BF16 path's 1e-3 of the oracle (norm-wise), Euler homogeneity to the same accuracy, and
+    the error flag clear."""
+    w = wl.workload_by_name(name)
+    r = GradRun(w, "bf16x3", gprec="bf16x3")
+    rho, (dx, dL, dR, dW1, dW2) = r.run()
+    assert heff.heff_grad_status(r.g, r.gws) == 0
+    L, W1, W2, R, x = oh.problem_from_workload(w)
+    ref = ograd.grad_all(L, W1, W2, R, x)
+    Ll, W1l, W2l, Rl, xl = r.lays
+    errs = {
+        "dx": _rel(dx, xl.assemble(lambda k: ref["dx"].blocks[k])),
+        "dL": _rel(dL, Ll.assemble(lambda k: ref["dL"].blocks[k])),
+        "dR": _rel(dR, Rl.assemble(lambda k: ref["dR"].blocks[k])),
+        "dW1": _rel(dW1, W1l.assemble(lambda k: ref["dW1"][k])),
+        "dW2": _rel(dW2, W2l.assemble(lambda k: ref["dW2"][k])),
+    }
+    print(name, "bf16x3", {k: f"{v:.1e}" for k, v in errs.items()}, f"rho err {abs(rho - ref['rho']):.1e}")
+    assert abs(rho - ref["rho"]) < 1e-3 * abs(ref["rho"])
+    for k, v in errs.items():
+        assert v < 1e-3, (k, v)
+    b = r.bufs
+    for g_, t_ in ((dL, b["L"]), (dR, b["R"]), (dW1, b["W1"]), (dW2, b["W2"])):
+        assert abs(float(np.dot(g_, t_)) - rho) < 1e-3 * abs(rho)
+
+
+def test_backward_bf16x3_streamed_at_m4096_close_to_fp64():
+    w = wl.workload_by_name("spin_m4096")
+    f64 = GradRun(w, ws_limit=256 << 20)
+    tc = GradRun(w, "bf16x3", ws_limit=256 << 20, problem=(f64.lays, f64.bufs), gprec="bf16x3")
+    r0, r1 = f64.run(), tc.run()
+    assert heff.heff_grad_status(tc.g, tc.gws) == 0
+    errs = [_rel(a, b) for a, b in zip(r1[1], r0[1])]
+    print("m=4096 bf16x3 vs fp64 gradients:", [f"{e:.1e}" for e in errs], f"rho {abs(r1[0] - r0[0]) / abs(r0[0]):.1e}")
+    assert abs(r1[0] - r0[0]) < 1e-3 * abs(r0[0])
+    assert max(errs) < 1e-3

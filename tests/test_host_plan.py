@@ -140,6 +140,37 @@ def test_gradient_workspace_limit_splits_left_sectors():
     assert "minimum" in heff.heff_last_error()
 
 
+def test_block_product_precision_switch_keeps_the_work():
+    """Re-tiling the environment-update and gradient block lists for the tensor cores
+    (128 x 128 output tiles) and back leaves their flop counts unchanged; other precisions
+    are refused."""
+    w = wl.workload_by_name("spin_m200")
+    lays, bufs = library_problem(w)
+    hs = [t.handle for t in lays]
+    g = heff.heff_grad_plan_create(*hs, bufs["W1"], bufs["W2"], 0)
+    for prec in ("bf16x3", "fp64", "bf16x3"):
+        heff.heff_grad_plan_set_precision(g, prec)
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_grad_plan_set_precision(g, "tf32x3")
+    assert e.value.code == -3
+    heff.heff_grad_plan_destroy(g)
+    Ll = lays[0]
+    ones = lambda n: np.ones(n, dtype=np.int32)
+    gq, gd = wl.binomial_sectors(220, 11, 3, parity=0)
+    site = heff.Layout([(w.alpha_q, w.alpha_d, 1), (w.phys, ones(2), 1), (gq, gd, -1)])
+    Wl = heff.Layout([(w.ql, ones(len(w.ql)), 1), (w.phys, ones(2), 1), (w.phys, ones(2), -1),
+                      (w.qm, ones(len(w.qm)), -1)])
+    new = heff.Layout([(gq, gd, -1), (w.qm, ones(len(w.qm)), 1), (gq, gd, 1)])
+    P = heff.heff_env_plan_create(Ll.handle, site.handle, Wl.handle, new.handle, Wl.assemble(lambda k: w.W1[k]),
+                                  "left")
+    f0 = heff.heff_env_flops(P)
+    heff.heff_env_plan_set_precision(P, "bf16x3")
+    assert heff.heff_env_flops(P) == f0 > 0
+    heff.heff_env_plan_set_precision(P, "fp64")
+    assert heff.heff_env_flops(P) == f0
+    heff.heff_env_plan_destroy(P)
+
+
 def _row_block_mask(xl, sectors):
     """Flat mask of the y blocks whose left sector is in `sectors`."""
     mask = np.zeros(xl.nelem, dtype=bool)

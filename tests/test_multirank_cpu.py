@@ -2,9 +2,10 @@
 
 * bench.py's weak-scaling coordination: each rank's problem shares L, W, R and has its
   own two-site tensor; the job time is the maximum over ranks;
-* the row-sharded apply: each rank plans its shard of y's left sectors, executes the
-  plan's tables on the CPU (the table interpreter of the host tests), and an all-reduce
-  of the zero-filled outputs gives the oracle's y on every rank.
+* the row-sharded apply through bench.py's own step (``sharded_step``: zero y, write this
+  rank's blocks, all-reduce): each rank plans its shard of y's left sectors and executes
+  the plan's tables on the CPU (the table interpreter of the host tests) in place of the
+  GPU apply; the all-reduced y equals the oracle's on every rank.
 """
 import os
 import socket
@@ -38,6 +39,7 @@ def _bench_worker(rank, world, port):
     try:
         import bench
         assert bench.max_over_ranks(1.0 + rank, "cpu") == float(world)
+        assert bench.sum_over_ranks(1.0 + rank, "cpu") == float(world * (world + 1) // 2)
         assert bench.rank_batch(rank) == rank
         # the ranks' two-site tensors differ, their environments agree
         _, lays, bufs = bench.make_problem("spin_m24", bench.rank_batch(rank))
@@ -63,11 +65,17 @@ def _shard_worker(rank, world, port, name):
         w = wl.workload_by_name(name)
         lays, bufs = library_problem(w)
         xl = lays[4]
+        import bench
         P = heff.Plan(*lays, bufs["W1"], bufs["W2"], "fp64", "f64", shard=(rank, world))
-        y = interpret_plan(P, bufs, bufs["x"][0])
-        y = np.where(np.isnan(y), 0.0, y)                  # blocks of other shards
-        t = torch.from_numpy(y)
-        dist.all_reduce(t)
+
+        def apply_shard(out):
+            # the shard plan's tables executed on the CPU: this rank's y blocks only
+            ys = interpret_plan(P, bufs, bufs["x"][0])
+            keep = ~np.isnan(ys)
+            out.numpy()[keep] = ys[keep]
+        # bench.py's row-sharded step: zero y, this rank's blocks, all-reduce
+        t = torch.full((xl.nelem,), float("nan"), dtype=torch.float64)
+        bench.sharded_step(apply_shard, t)
         L, W1, W2, R, x = oh.problem_from_workload(w)
         y_ref = oracle_flat(xl, oh.heff_apply(L, W1, W2, R, x))
         err = np.abs(t.numpy() - y_ref).max() / np.abs(y_ref).max()
