@@ -88,6 +88,8 @@ def parse():
                     help="time one step of the DMRG bond update alone and print its own JSON line "
                          "(the profiling cases): the FP64 Lanczos eigensolver (30 iterations, BF16x3 "
                          "matvecs), the block SVD truncation, the environment update, the gradients")
+    ap.add_argument("--block-precisions", default="fp64,bf16x3",
+                    help="--part env_update / backward: the block-product precisions to time")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (other precisions, eigensolver, SVD, batched graph)")
     return ap.parse_args()
@@ -480,7 +482,7 @@ def batched_graph(name, nb, dev, stream, flush):
     return res
 
 
-def env_update_timing(w, dev, stream):
+def env_update_timing(w, dev, stream, precs=("fp64", "bf16x3")):
     import torch
     import workloads as wl
     from workloads.fill import site_block
@@ -505,10 +507,10 @@ def env_update_timing(w, dev, stream):
     try:
         ws = torch.empty(heff.heff_env_workspace_size(plan), dtype=torch.uint8, device=dev)
         d = [torch.from_numpy(v).to(dev) for v in (old, site, Wv)]
-        env = {p: torch.empty(new_l.nelem, dtype=torch.float64, device=dev) for p in ("fp64", "bf16x3")}
+        env = {p: torch.empty(new_l.nelem, dtype=torch.float64, device=dev) for p in precs}
         fl = heff.heff_env_flops(plan)
         out["flops"] = fl
-        for prec in ("fp64", "bf16x3"):
+        for prec in precs:
             heff.heff_env_plan_set_precision(plan, prec)
 
             def f(prec=prec):
@@ -516,14 +518,16 @@ def env_update_timing(w, dev, stream):
             f()
             ms = _events_ms(f, 3, stream)
             out[prec] = {"ms": ms, "tflops": fl / (ms * 1e-3) / 1e12}
-        out["rel_err_bf16x3"] = float(torch.linalg.norm(env["bf16x3"] - env["fp64"]) / torch.linalg.norm(env["fp64"]))
-        out["status_bf16x3"] = heff.heff_env_status(plan, ws, stream)
+        if len(env) == 2:
+            out["rel_err_bf16x3"] = float(torch.linalg.norm(env["bf16x3"] - env["fp64"]) /
+                                          torch.linalg.norm(env["fp64"]))
+        out["status"] = heff.heff_env_status(plan, ws, stream)
     finally:
         heff.heff_env_plan_destroy(plan)
     return out
 
 
-def backward_timing(dev, stream):
+def backward_timing(dev, stream, precs=("fp64", "bf16x3")):
     import torch
     import workloads as wl
     from paper_2007_05540_gb300 import heff
@@ -534,28 +538,30 @@ def backward_timing(dev, stream):
         g = heff.heff_grad_plan_create(Ll.handle, W1l.handle, W2l.handle, Rl.handle, xl.handle, bufs["W1"],
                                        bufs["W2"], limit)
         try:
-            gws = torch.empty(heff.heff_grad_workspace_size(g), dtype=torch.uint8, device=dev)
             d = {k: torch.from_numpy(np.asarray(v)).to(dev) for k, v in bufs.items()}
             rho = torch.empty((), dtype=torch.float64, device=dev)
-            res[name] = {"chunks": heff.heff_grad_chunks(g), "grad_workspace_MB": heff.heff_grad_workspace_size(g) / 1e6}
+            res[name] = {"chunks": heff.heff_grad_chunks(g)}
             grads = {}
-            for prec in ("fp64", "bf16x3"):
+            for prec in precs:
                 # the apply inside (for rho and dx) and the block products in the same precision
                 plan = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], prec, "f64")
                 aws = plan.workspace(dev)
                 heff.heff_grad_plan_set_precision(g, prec)
+                gws = torch.empty(heff.heff_grad_workspace_size(g), dtype=torch.uint8, device=dev)
                 outs = [torch.empty_like(d[k]) for k in ("x", "L", "R", "W1", "W2")]
 
-                def f(plan=plan, aws=aws, outs=outs):
+                def f(plan=plan, aws=aws, outs=outs, gws=gws):
                     heff.heff_backward(g, plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], rho, *outs, aws,
                                        gws, stream)
                 f()
                 ms = _events_ms(f, 2, stream)
                 grads[prec] = outs
-                res[name][prec] = {"ms": ms, "rho": float(rho)}
-                del plan, aws
-            res[name]["rel_err_bf16x3"] = {k: float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for k, a, b in
-                                          zip(("dx", "dL", "dR", "dW1", "dW2"), grads["bf16x3"], grads["fp64"])}
+                res[name][prec] = {"ms": ms, "rho": float(rho), "grad_workspace_MB": gws.numel() / 1e6}
+                del plan, aws, gws
+            if len(grads) == 2:
+                res[name]["rel_err_bf16x3"] = {k: float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for k, a, b
+                                              in zip(("dx", "dL", "dR", "dW1", "dW2"), grads["bf16x3"],
+                                                     grads["fp64"])}
         finally:
             heff.heff_grad_plan_destroy(g)
     return res
@@ -569,11 +575,12 @@ def run_part(args):
     stream = torch.cuda.current_stream()
     if args.part == "lanczos":
         return run_lanczos_only(args)
+    precs = tuple(args.block_precisions.split(","))
     if args.part == "env_update":
         w, _, _ = make_problem(args.workload, 0)
-        out = env_update_timing(w, dev, stream)
+        out = env_update_timing(w, dev, stream, precs)
     elif args.part == "backward":
-        out = backward_timing(dev, stream)
+        out = backward_timing(dev, stream, precs)
     elif args.part == "energy":
         out = ground_state_compare(args.workload, dev, stream)
     else:

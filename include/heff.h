@@ -317,7 +317,9 @@ void heff_env_plan_destroy(heff_env_plan* plan);
  * Arithmetic of the environment update's block products.  HEFF_PREC_FP64 (the default):
  * FP64 on the CUDA cores.  HEFF_PREC_BF16X3: on the tensor cores, each operand element split
  * into bf16 hi + lo and three products per K block, FP32 accumulation (about 1e-5 relative
- * per product); the tensors stay FP64 buffers and the call sequence is unchanged.  Errors:
+ * per product); the tensors stay FP64 buffers (the update converts env_old and the site
+ * tensor to FP32 copies in the workspace, whose size covers both precisions) and the call
+ * sequence is unchanged.  Errors:
  * INVALID_ARG, UNSUPPORTED (another precision), CUDA.
  */
 int heff_env_plan_set_precision(heff_env_plan* plan, int32_t precision);
@@ -381,7 +383,11 @@ void heff_grad_plan_destroy(heff_grad_plan* g);
  * Arithmetic of the gradients' block products (U, T1, dL, dR): HEFF_PREC_FP64 (the default,
  * CUDA cores) or HEFF_PREC_BF16X3 (tensor cores, bf16 hi/lo split, FP32-accumulated; about
  * 1e-5 relative).  The scalars, dx and the W gradients' reductions stay FP64; buffers stay
- * FP64.  heff_grad_status reads and clears the gradient workspace's sticky error flag
+ * FP64.  With HEFF_PREC_BF16X3 the workspace also holds FP32 copies of x, L and R (the
+ * products' operands, converted once per call) and the intermediates in FP32, so
+ * heff_grad_workspace_size reports a larger size after the switch (a workspace limit given
+ * at plan creation bounds the FP64 layout).  heff_grad_status reads and clears the
+ * gradient workspace's sticky error flag
  * (HEFF_ERR_TIMEOUT when a bounded wait of a tensor-core product expired; synchronises).
  * Errors: INVALID_ARG, UNSUPPORTED (another precision), WORKSPACE, CUDA.
  */

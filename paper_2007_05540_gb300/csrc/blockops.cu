@@ -4,6 +4,9 @@
 // product a small dense GEMM, Section IV "list" algorithm).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "convert.cuh"
 #include "internal.h"
 
 namespace heff {
@@ -126,20 +129,23 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const BTile* __restrict__ ti
     }
 }
 
-// one CTA per dot: partial[d] = <X[x_off..], Y[y_off..]>
-__global__ void __launch_bounds__(256) block_dot_kernel(const BDot* __restrict__ dots, const double* __restrict__ X,
-                                                        const double* __restrict__ Y, double* __restrict__ partial) {
-    __shared__ double sh[8];
+// one CTA per dot: partial[d] = <X[x_off..], Y[y_off..]>, accumulated in the element type
+// (FP32 vectors come from the tensor-core products, whose values carry ~1e-5 anyway)
+template <typename T>
+__global__ void __launch_bounds__(256) block_dot_kernel(const BDot* __restrict__ dots, const T* __restrict__ X,
+                                                        const T* __restrict__ Y, double* __restrict__ partial) {
+    __shared__ T sh[8];
     const BDot d = dots[blockIdx.x];
-    double a = 0.0;
+    T a = 0;
     for (int64_t i = threadIdx.x; i < d.len; i += blockDim.x) a = fma(X[d.x_off + i], Y[d.y_off + i], a);
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
+        T s = 0;
         for (int w = 0; w < 8; ++w) s += sh[w];
-        partial[blockIdx.x] = s;
+        if constexpr (std::is_same<T, double>::value) partial[blockIdx.x] = s;
+        else partial[blockIdx.x] = f32_to_f64(s);
     }
 }
 
@@ -167,11 +173,12 @@ int launch_bgemm(const BList& b, const double* A, const double* B, double* C, co
     return HEFF_OK;
 }
 
-int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const double* X, const double* Y,
-                      double* out, int nout, double* scratch, double scale, void* stream, bool accumulate) {
+template <typename T>
+static int block_dots_t(const BDot* d_dots, int ndots, const int32_t* d_off, const T* X, const T* Y, double* out,
+                        int nout, double* scratch, double scale, void* stream, bool accumulate) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (ndots > 0) {
-        block_dot_kernel<<<ndots, 256, 0, st>>>(d_dots, X, Y, scratch);
+        block_dot_kernel<T><<<ndots, 256, 0, st>>>(d_dots, X, Y, scratch);
         count_launches(1);
     }
     gather_dots_kernel<<<(nout + 255) / 256, 256, 0, st>>>(d_off, scratch, out, nout, scale, accumulate ? 1 : 0);
@@ -179,6 +186,16 @@ int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "block dots launch: %s", cudaGetErrorString(e));
     return HEFF_OK;
+}
+
+int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const double* X, const double* Y,
+                      double* out, int nout, double* scratch, double scale, void* stream, bool accumulate) {
+    return block_dots_t(d_dots, ndots, d_off, X, Y, out, nout, scratch, scale, stream, accumulate);
+}
+
+int launch_block_dots_f32(const BDot* d_dots, int ndots, const int32_t* d_off, const float* X, const float* Y,
+                          double* out, int nout, double* scratch, double scale, void* stream, bool accumulate) {
+    return block_dots_t(d_dots, ndots, d_off, X, Y, out, nout, scratch, scale, stream, accumulate);
 }
 
 }  // namespace heff

@@ -11,6 +11,7 @@
 // block, the products whose MPO coefficient is nonzero in the host copy of W.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <new>
 #include <tuple>
@@ -21,12 +22,16 @@ using heff::fail;
 using heff::BList;
 using heff::BProd;
 
+// Workspace: [error flag, 256 B][intermediate X or Y][tensor-core precision only: FP32 copies
+// of env_old and of the site tensor].  The FP64 products keep the intermediate in FP64; the
+// tensor-core products read FP32 copies and keep it in FP32.
 struct heff_env_plan {
     int side = 0;
     int precision = HEFF_PREC_FP64;   // of the block products
     BList step1, step2;
-    int64_t ws_elems = 0;      // intermediate (X or Y) in doubles
-    size_t off_flag = 0;       // sticky error flag of the tensor-core products (one int)
+    int64_t ws_elems = 0;      // intermediate (X or Y) elements
+    int64_t n_env = 0, n_site = 0;
+    size_t off_x = 256, off_env32 = 0, off_site32 = 0;
     size_t ws_bytes = 0;
     bool uploaded = false;
 };
@@ -181,8 +186,14 @@ extern "C" int heff_env_plan_create(const heff_layout* env_old, const heff_layou
             }
         }
         P->ws_elems = ioff;
-        P->off_flag = (size_t)((ioff + 31) / 32 * 32) * sizeof(double);
-        P->ws_bytes = P->off_flag + 256;
+        P->n_env = env_old->nelem;
+        P->n_site = site->nelem;
+        auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+        const size_t fp64_bytes = P->off_x + al((size_t)ioff * sizeof(double));
+        P->off_env32 = P->off_x + al((size_t)ioff * sizeof(float));
+        P->off_site32 = P->off_env32 + al((size_t)P->n_env * sizeof(float));
+        const size_t tc_bytes = P->off_site32 + al((size_t)P->n_site * sizeof(float));
+        P->ws_bytes = std::max(fp64_bytes, tc_bytes);
     } catch (const std::bad_alloc&) {
         delete P;
         return fail(HEFF_ERR_OOM, "out of host memory while planning the environment update");
@@ -227,17 +238,24 @@ extern "C" int heff_env_update(heff_env_plan* plan, const double* env_old, const
     if (!workspace || workspace_bytes < plan->ws_bytes || reinterpret_cast<uintptr_t>(workspace) % 256)
         return fail(HEFF_ERR_WORKSPACE, "environment workspace of %zu bytes, needs %zu (256-byte aligned)",
                     workspace_bytes, plan->ws_bytes);
-    double* X = static_cast<double*>(workspace);
-    int* err = reinterpret_cast<int*>(static_cast<char*>(workspace) + plan->off_flag);
+    char* ws = static_cast<char*>(workspace);
+    int* err = reinterpret_cast<int*>(ws);
     int rc;
-    if (plan->precision != HEFF_PREC_FP64) {
-        cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), static_cast<cudaStream_t>(stream));
-        if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    if (plan->precision == HEFF_PREC_FP64) {
+        double* X = reinterpret_cast<double*>(ws + plan->off_x);
+        if ((rc = heff::launch_bgemm(plan->step1, env_old, site, X, nullptr, nullptr, 1.0, stream))) return rc;
+        return heff::launch_bgemm(plan->step2, site, X, env_new, W, nullptr, 1.0, stream);
     }
-    if ((rc = heff::launch_blist(plan->precision, plan->step1, env_old, site, X, nullptr, nullptr, 1.0, stream,
-                                 nullptr, err)))
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    float* X = reinterpret_cast<float*>(ws + plan->off_x);
+    float* E32 = reinterpret_cast<float*>(ws + plan->off_env32);
+    float* S32 = reinterpret_cast<float*>(ws + plan->off_site32);
+    if ((rc = heff::launch_convert_f64_f32(env_old, E32, plan->n_env, stream))) return rc;
+    if ((rc = heff::launch_convert_f64_f32(site, S32, plan->n_site, stream))) return rc;
+    if ((rc = heff::launch_bgemm_tc(plan->step1, E32, S32, X, false, nullptr, nullptr, 1.0, stream, nullptr, err)))
         return rc;
-    return heff::launch_blist(plan->precision, plan->step2, site, X, env_new, W, nullptr, 1.0, stream, nullptr, err);
+    return heff::launch_bgemm_tc(plan->step2, S32, X, env_new, true, W, nullptr, 1.0, stream, nullptr, err);
 }
 
 extern "C" int heff_env_plan_set_precision(heff_env_plan* plan, int32_t precision) {
@@ -268,7 +286,7 @@ extern "C" int heff_env_status(const heff_env_plan* plan, void* workspace, size_
     if (plan->precision == HEFF_PREC_FP64) return HEFF_OK;
     if (workspace_bytes < plan->ws_bytes) return fail(HEFF_ERR_WORKSPACE, "heff_env_status: workspace too small");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int* d = reinterpret_cast<int*>(static_cast<char*>(workspace) + plan->off_flag);
+    int* d = static_cast<int*>(workspace);
     int flag = 0;
     cudaError_t e = cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

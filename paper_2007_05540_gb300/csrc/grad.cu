@@ -46,7 +46,10 @@ struct heff_grad_plan {
     std::vector<int32_t> dw2_off, dw2_terms;   // per W2 entry: pairs (G idx, W1 idx)
     int64_t nx = 0, nR = 0, nW1 = 0, nW2 = 0, ng = 0;
     int64_t off_U = 0, off_W12 = 0, off_G = 0, off_sc = 0, off_part = 0, off_flag = 0;
-    size_t ws_bytes = 0;
+    size_t ws_bytes = 0;              // for the current precision
+    size_t ws_bytes_fp64 = 0, ws_bytes_tc = 0;
+    // tensor-core precision: FP32 copies of x, L and R after the FP64 part (double offsets)
+    int64_t nL = 0, off_x32 = 0, off_L32 = 0, off_R32 = 0;
     int precision = HEFF_PREC_FP64;   // of the block products (U, T1, dL, dR)
     int64_t npart = 0;
     // device copies
@@ -360,7 +363,13 @@ extern "C" int heff_grad_plan_create(const heff_layout* L, const heff_layout* W1
         g->npart = std::max<int64_t>(max_gd, (int64_t)g->xdots.size());
         g->off_part = o; o += al(g->npart);
         g->off_flag = o; o += 32;          // sticky error flag of the tensor-core products
-        g->ws_bytes = (size_t)o * sizeof(double);
+        g->ws_bytes_fp64 = (size_t)o * sizeof(double);
+        g->nL = L->nelem;
+        g->off_x32 = o; o += al((x->nelem + 1) / 2);
+        g->off_L32 = o; o += al((L->nelem + 1) / 2);
+        g->off_R32 = o; o += al((R->nelem + 1) / 2);
+        g->ws_bytes_tc = (size_t)o * sizeof(double);
+        g->ws_bytes = g->ws_bytes_fp64;
     } catch (const std::bad_alloc&) {
         delete g;
         return fail(HEFF_ERR_OOM, "out of host memory while planning the gradients");
@@ -428,7 +437,11 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
     double *Ureg = ws + g->off_U, *W12 = ws + g->off_W12, *G = ws + g->off_G;
     double *sc = ws + g->off_sc, *part = ws + g->off_part;
     int* err = reinterpret_cast<int*>(ws + g->off_flag);
-    if (g->precision != HEFF_PREC_FP64 && cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+    const bool tc = g->precision != HEFF_PREC_FP64;
+    float* x32 = reinterpret_cast<float*>(ws + g->off_x32);
+    float* L32 = reinterpret_cast<float*>(ws + g->off_L32);
+    float* R32 = reinterpret_cast<float*>(ws + g->off_R32);
+    if (tc && cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
         return fail(HEFF_ERR_CUDA, "heff_backward: memset failed");
     // y = K x into dx (dx is overwritten by the gradient below)
     int rc = heff_apply(plan, L, W1, W2, R, x, dx, apply_ws, apply_ws_bytes, stream);
@@ -444,6 +457,13 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
     // W12 on the device from the current MPO values
     pair_sum_kernel<<<(int)((g->ng + 255) / 256), 256, 0, st>>>(g->d_w12_off, g->d_w12_terms, W1, W2, W12, g->ng);
     heff::count_launches(1);
+    if (tc) {   // FP32 operand copies for the tensor-core products, converted once
+        int rc2;
+        if ((rc2 = heff::launch_convert_f64_f32(x, x32, g->nx, stream)) ||
+            (rc2 = heff::launch_convert_f64_f32(L, L32, g->nL, stream)) ||
+            (rc2 = heff::launch_convert_f64_f32(R, R32, g->nR, stream)))
+            return rc2;
+    }
     const bool streamed = g->chunks.size() > 1;
     if (streamed) {   // dR and G are sums over the chunks
         if (cudaMemsetAsync(dR, 0, (size_t)g->nR * sizeof(double), st) != cudaSuccess ||
@@ -453,12 +473,24 @@ extern "C" int heff_backward(heff_grad_plan* g, heff_plan* plan, const double* L
     for (const GradChunk& c : g->chunks) {
         // U at the start of the shared region, T1 at the chunk's t_base: the lists hold
         // offsets within the region
+        if (tc) {
+            // the tensor-core products on the FP32 copies; U and T1 in FP32 (the region holds
+            // the same element offsets in half the bytes)
+            float *U = reinterpret_cast<float*>(Ureg), *T1 = U;
+            if ((rc = heff::launch_bgemm_tc(c.U, x32, R32, U, false, nullptr, nullptr, 1.0, stream, nullptr, err)) ||
+                (rc = heff::launch_bgemm_tc(c.T1, L32, x32, T1, false, nullptr, nullptr, 1.0, stream, nullptr, err)) ||
+                (rc = heff::launch_bgemm_tc(c.dL, U, x32, dL, true, W12, nullptr, 1.0, stream, sc, err)) ||
+                (rc = heff::launch_bgemm_tc(c.dR, x32, T1, dR, true, W12, nullptr, 1.0, stream, sc, err)) ||
+                (rc = heff::launch_block_dots_f32(c.d_gdots, (int)c.gdots.size(), c.d_goff, T1, U, G, (int)g->ng,
+                                                  part, 1.0, stream, streamed)))
+                return rc;
+            continue;
+        }
         double *U = Ureg, *T1 = Ureg;
-        const int pr = g->precision;
-        if ((rc = heff::launch_blist(pr, c.U, x, R, U, nullptr, nullptr, 1.0, stream, nullptr, err))) return rc;
-        if ((rc = heff::launch_blist(pr, c.T1, L, x, T1, nullptr, nullptr, 1.0, stream, nullptr, err))) return rc;
-        if ((rc = heff::launch_blist(pr, c.dL, U, x, dL, W12, nullptr, 1.0, stream, sc, err))) return rc;
-        if ((rc = heff::launch_blist(pr, c.dR, x, T1, dR, W12, nullptr, 1.0, stream, sc, err))) return rc;
+        if ((rc = heff::launch_bgemm(c.U, x, R, U, nullptr, nullptr, 1.0, stream))) return rc;
+        if ((rc = heff::launch_bgemm(c.T1, L, x, T1, nullptr, nullptr, 1.0, stream))) return rc;
+        if ((rc = heff::launch_bgemm(c.dL, U, x, dL, W12, nullptr, 1.0, stream, sc))) return rc;
+        if ((rc = heff::launch_bgemm(c.dR, x, T1, dR, W12, nullptr, 1.0, stream, sc))) return rc;
         if ((rc = heff::launch_block_dots(c.d_gdots, (int)c.gdots.size(), c.d_goff, T1, U, G, (int)g->ng, part, 1.0,
                                           stream, streamed)))
             return rc;
@@ -490,6 +522,7 @@ extern "C" int heff_grad_plan_set_precision(heff_grad_plan* g, int32_t precision
             if (g->uploaded && !rc) rc = heff::blist_upload(*b);
         }
     g->precision = precision;
+    g->ws_bytes = precision == HEFF_PREC_FP64 ? g->ws_bytes_fp64 : g->ws_bytes_tc;
     if (rc) g->uploaded = false;
     return rc;
 }

@@ -124,17 +124,14 @@ int blist_upload(BList& b);
 void blist_free(BList& b);
 int launch_bgemm(const BList& b, const double* A, const double* B, double* C, const double* coef1,
                  const double* coef2, double scale, void* stream, const double* inv_scale = nullptr);
-// the same products on the tensor cores (BF16x3 split, FP32 accumulation; blockops_tc.cu):
-// needs 128 x 128 tiles (retile); err: device int raised when a bounded wait expires
-int launch_bgemm_tc(const BList& b, const double* A, const double* B, double* C, const double* coef1,
+// the same products on the tensor cores (BF16x3 split, FP32 accumulation; blockops_tc.cu)
+// on FP32 copies of the operands (launch_convert_f64_f32), with an FP32 (c_f64 false) or
+// FP64 output; needs 128 x 128 tiles (retile); err: device int raised when a bounded wait
+// expires
+int launch_bgemm_tc(const BList& b, const float* A, const float* B, void* C, bool c_f64, const double* coef1,
                     const double* coef2, double scale, void* stream, const double* inv_scale, int* err);
-// run a block list in the given precision (HEFF_PREC_FP64: CUDA cores, HEFF_PREC_BF16X3: tensor cores)
-inline int launch_blist(int precision, const BList& b, const double* A, const double* B, double* C,
-                        const double* coef1, const double* coef2, double scale, void* stream,
-                        const double* inv_scale, int* err) {
-    return precision == HEFF_PREC_BF16X3 ? launch_bgemm_tc(b, A, B, C, coef1, coef2, scale, stream, inv_scale, err)
-                                         : launch_bgemm(b, A, B, C, coef1, coef2, scale, stream, inv_scale);
-}
+// dst[i] = src[i] rounded to FP32 (round to nearest even, on the integer pipes)
+int launch_convert_f64_f32(const double* src, float* dst, int64_t n, void* stream);
 // out[j] = scale * sum over the dots d in [off[j], off[j+1]) of <X[x_off..], Y[y_off..]>
 // (dots sorted by output index; scratch holds one double per dot)
 struct BDot {
@@ -144,6 +141,8 @@ struct BDot {
 // (accumulate: out[j] += instead of out[j] =)
 int launch_block_dots(const BDot* d_dots, int ndots, const int32_t* d_off, const double* X, const double* Y,
                       double* out, int nout, double* scratch, double scale, void* stream, bool accumulate = false);
+int launch_block_dots_f32(const BDot* d_dots, int ndots, const int32_t* d_off, const float* X, const float* Y,
+                          double* out, int nout, double* scratch, double scale, void* stream, bool accumulate = false);
 
 constexpr int MAXB = 64;   // batch entries per launch (kernel parameter arrays)
 struct PtrBatch { const void* p[MAXB]; };
