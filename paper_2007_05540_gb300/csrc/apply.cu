@@ -14,6 +14,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "convert.cuh"
 #include "internal.h"
 
 using heff::fail;
@@ -39,7 +40,7 @@ template <> struct Plane<HEFF_PREC_BF16X3> {
         hi = __float2bfloat16_rn(f);
         lo = __float2bfloat16_rn(f - __bfloat162float(hi));
     }
-    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split((float)v, hi, lo); }
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split(f64_to_f32_rn(v), hi, lo); }
     static __device__ __forceinline__ void store2(T* p, T a, T b) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
     }
@@ -57,9 +58,17 @@ template <> struct Plane<HEFF_PREC_TF32X3> {
     static __device__ __forceinline__ void store2(T* p, T a, T b) {
         *reinterpret_cast<float2*>(p) = make_float2(a, b);
     }
-    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split((float)v, hi, lo); }
+    static __device__ __forceinline__ void split(double v, T& hi, T& lo) { split(f64_to_f32_rn(v), hi, lo); }
 };
 
+
+// Element conversion of the inputs: FP64 inputs of the split paths go to FP32 on the
+// integer pipes (the hardware double -> float conversion runs at GB300's FP64 rate).
+template <typename Acc, typename In>
+__device__ __forceinline__ Acc to_acc(In v) {
+    if constexpr (std::is_same<Acc, float>::value && std::is_same<In, double>::value) return f64_to_f32_rn(v);
+    else return (Acc)v;
+}
 
 // ------------------------------------------------------------------ dependent launch
 // wait for the predecessor grid on the stream (no-op without programmatic launch), and let
@@ -97,7 +106,7 @@ __global__ void __launch_bounds__(32 * PACK_WARPS) pack_kernel(const PackTile* _
         const int na = t.m_a - t.a0;                // rows of x left in this tile (may be <= 0)
 #pragma unroll
         for (int r = 0; r < 32; ++r)
-            sw[r][lane] = (bv && r < na) ? (Acc)x[(int64_t)(t.a0 + r) * t.m_b + b] : (Acc)0;
+            sw[r][lane] = (bv && r < na) ? to_acc<Acc>(x[(int64_t)(t.a0 + r) * t.m_b + b]) : (Acc)0;
     }
     __syncwarp();
     E* hi = reinterpret_cast<E*>(xt) + (int64_t)bz * batch_elems;
@@ -154,7 +163,7 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
     const int nt = t.term_count < 64 ? t.term_count : 64;
     for (int k = threadIdx.x; k < nt; k += blockDim.x) {
         MixTerm m = terms[t.term_begin + k];
-        coef[k] = (Acc)W[m.w_idx];
+        coef[k] = to_acc<Acc>(W[m.w_idx]);
         srco[k] = m.src_off;
     }
     __syncthreads();
@@ -192,7 +201,7 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
                 } else {                                      // rare: more than 64 terms
                     const MixTerm m = terms[t.term_begin + k];
                     s = src + m.src_off;
-                    cf = (Acc)W[m.w_idx];
+                    cf = to_acc<Acc>(W[m.w_idx]);
                 }
                 In v0[RW][U], v1[RW][U];
 #pragma unroll
@@ -207,8 +216,8 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
                 for (int i = 0; i < RW; ++i)
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        a0[i][u] += cf * (Acc)v0[i][u];
-                        a1[i][u] += cf * (Acc)v1[i][u];
+                        a0[i][u] += cf * to_acc<Acc>(v0[i][u]);
+                        a1[i][u] += cf * to_acc<Acc>(v1[i][u]);
                     }
             }
 #pragma unroll

@@ -37,6 +37,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "convert.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -603,7 +604,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                             for (int u = 0; u < 8; ++u)
                                 if (r0 + u < rows)
                                     y[(int64_t)(q * 32 + r0 + u) * t.ldc] =
-                                        old[u] + (double)stage[(r0 + u) * 32 + (lane ^ (r0 + u))];
+                                        old[u] + f32_to_f64(stage[(r0 + u) * 32 + (lane ^ (r0 + u))]);
                         }
                     } else {
                         float* y = static_cast<float*>(const_cast<void*>(g.y.p[brel])) + o0;
