@@ -379,12 +379,16 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
              "lattice), binomial sectors"),
             ("j1j2_20x10_compressed_m4096", "spin_j1j2_20x10c_m4096",
              "the same window of the 20x10 J1-J2 cylinder MPO compressed at the SVD cutoff 1e-13 "
-             "(k = 32), binomial sectors")):
+             "(k = 32, SVD basis), binomial sectors"),
+            ("j1j2_20x10_compressed_interpolative_m4096", "spin_j1j2_20x10ci_m4096",
+             "the same compression keeping a subset of the automaton's channels (k = 32, sparse W), "
+             "binomial sectors")):
         out[key] = {**single_apply(name, dev, stream, flush), "note": note}
 
     # 32 electron-model applies sharing L, W, R in one captured graph (autotuned tiles): the
     # range-5 chain window and the 4 x 8 Hubbard cylinder window
-    for name in ("electron_m2048", "electron_hubbard_4x8_m2048", "electron_tri_xc6_m2048", "electron_tri_xc6c_m2048"):
+    for name in ("electron_m2048", "electron_hubbard_4x8_m2048", "electron_tri_xc6_m2048", "electron_tri_xc6c_m2048",
+                 "electron_tri_xc6ci_m2048"):
         out[name + "_batch32_graph"] = batched_graph(name, 32, dev, stream, flush)
     return out
 

@@ -58,11 +58,12 @@ def test_j1j2_cylinder_3x4_reaches_ed():
     assert abs(r["energy"] - E_ed) < 1e-9 * abs(E_ed)
 
 
-def test_j1j2_cylinder_3x4_compressed_mpo_reaches_ed():
+@pytest.mark.parametrize("method", ["svd", "interpolative"])
+def test_j1j2_cylinder_3x4_compressed_mpo_reaches_ed(method):
     """The same lattice with its MPO compressed at the SVD cutoff 1e-13 (Section VI-B):
     fewer channels, the same Hamiltonian, the same ground energy."""
     pairs = wl.cylinder_pairs(3, 4, 1.0, 0.5)
-    mpo = wl.compress_mpo(wl.heisenberg_mpo(12, pairs))
+    mpo = wl.compress_mpo(wl.heisenberg_mpo(12, pairs), method=method)
     E_ed = _ed("j1j2_cylinder_3x4_J2_0.5_Sz0")
     r = dmrg.dmrg(mpo, (0,), [16, 32, 64, 64, 64], n_iter=25)
     print(f"3x4 J1-J2, compressed MPO (k <= {max(mpo.bond_dim(b) for b in range(13))}): {r['energy']:.12f} "

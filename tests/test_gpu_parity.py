@@ -72,7 +72,7 @@ def _compare(y, y_ref, tol, mask=None):
 
 SMALL = ["spin_m64", "spin_m200", "electron_m96", "electron_m256", "spin_m1024_s8", "spin_j1j2_6x6_m200",
          "electron_hubbard_4x8_m96", "spin_j1j2_20x10_m200", "electron_tri_xc6_m96", "spin_j1j2_20x10c_m200",
-         "electron_tri_xc6c_m96"]
+         "electron_tri_xc6c_m96", "spin_j1j2_20x10ci_m200", "electron_tri_xc6ci_m96"]
 
 
 def _workload(name):

@@ -139,7 +139,8 @@ def test_mpo_charge_rule_and_transpose_symmetry(which):
 
 
 @pytest.mark.parametrize("name", ["spin_j1j2_6x6_m200", "spin_j1j2_20x10_m200", "electron_hubbard_4x8_m96",
-                                  "electron_tri_xc6_m96", "spin_j1j2_20x10c_m200", "electron_tri_xc6c_m96"])
+                                  "electron_tri_xc6_m96", "spin_j1j2_20x10c_m200", "electron_tri_xc6c_m96",
+                                  "spin_j1j2_20x10ci_m200", "electron_tri_xc6ci_m96"])
 def test_lattice_windows_charge_rule_and_hermiticity(name):
     # the lattice MPO windows obey the charge rule of every nonzero entry and are Hermitian
     # under the channel transposition map, as the chain windows are
@@ -152,7 +153,9 @@ def test_lattice_windows_charge_rule_and_hermiticity(name):
            "electron_hubbard_4x8_m96": wl.hubbard_lattice_window,
            "electron_tri_xc6_m96": wl.triangular_hubbard_window,
            "spin_j1j2_20x10c_m200": lambda: lattice_window(20, 10, compress=True),
-           "electron_tri_xc6c_m96": lambda: wl.triangular_hubbard_window(compress=True)}[name]()
+           "electron_tri_xc6c_m96": lambda: wl.triangular_hubbard_window(compress=True),
+           "spin_j1j2_20x10ci_m200": lambda: lattice_window(20, 10, compress="interpolative"),
+           "electron_tri_xc6ci_m96": lambda: wl.triangular_hubbard_window(compress="interpolative")}[name]()
     for W, c0, c1 in [(win["W1"], win["conj_l"], win["conj_m"]), (win["W2"], win["conj_m"], win["conj_r"])]:
         Wt = W[c0][:, :, :, c1].transpose(0, 2, 1, 3)
         assert np.abs(W - Wt).max() < 1e-14
@@ -182,8 +185,9 @@ def _operator_schmidt_rank(H, n, b, d):
     return int(np.sum(s > 1e-10 * s[0]))
 
 
+@pytest.mark.parametrize("method", ["svd", "interpolative"])
 @pytest.mark.parametrize("case", ["j1j2_3x4", "tri_hubbard_2x3", "chain_range3"])
-def test_compressed_mpo_equals_kronecker_hamiltonian_with_minimal_bonds(case):
+def test_compressed_mpo_equals_kronecker_hamiltonian_with_minimal_bonds(case, method):
     if case == "j1j2_3x4":
         n, d = 12, 2
         pairs = wl.cylinder_pairs(3, 4, 1.0, 0.5)
@@ -199,7 +203,7 @@ def test_compressed_mpo_equals_kronecker_hamiltonian_with_minimal_bonds(case):
         pairs = wl.chain_pairs(n, [1.0, 0.5, 0.2])
         mpo, Hk = wl.heisenberg_mpo(n, pairs), kron.heisenberg_hamiltonian(n, pairs).toarray()
         supports = [(i, j) for i, j, _ in pairs]
-    c = wl.compress_mpo(mpo, 1e-13)
+    c = wl.compress_mpo(mpo, 1e-13, method=method)
     # the same operator ...
     assert np.abs(kron.mpo_to_dense(c) - Hk).max() < 1e-12
     # ... with the fewest channels any MPO of it can have at every bond: the operator
@@ -212,14 +216,15 @@ def test_compressed_mpo_equals_kronecker_hamiltonian_with_minimal_bonds(case):
         assert c.bond_dim(b) == _operator_schmidt_rank(Hk, n, b, d) + zero_done + zero_start, b
     assert any(c.bond_dim(b) < mpo.bond_dim(b) for b in range(1, n))
     # compressing again changes no bond
-    cc = wl.compress_mpo(c, 1e-13)
+    cc = wl.compress_mpo(c, 1e-13, method=method)
     assert [cc.bond_dim(b) for b in range(n + 1)] == [c.bond_dim(b) for b in range(n + 1)]
 
 
-def test_compressed_mpo_charge_rule_and_transpose_symmetry():
+@pytest.mark.parametrize("method", ["svd", "interpolative"])
+def test_compressed_mpo_charge_rule_and_transpose_symmetry(method):
     for mpo in (wl.heisenberg_mpo(36, wl.cylinder_pairs(6, 6, 1.0, 0.5)),
                 wl.hubbard_mpo(36, wl.triangular_hops(6, 6, 1.0), 8.5)):
-        c = wl.compress_mpo(mpo)
+        c = wl.compress_mpo(mpo, method=method)
         for n in range(c.n_sites):
             W, ql, qr = c.W[n], c.charges[n], c.charges[n + 1]
             for wl_, t, s, wr in np.argwhere(W != 0):
@@ -227,6 +232,17 @@ def test_compressed_mpo_charge_rule_and_transpose_symmetry():
             Wt = W[c.conj[n]][:, :, :, c.conj[n + 1]].transpose(0, 2, 1, 3)
             assert np.abs(W - Wt).max() < 1e-14
         assert c.start_index(0) == 0 and c.done_index(c.n_sites) == 0
+
+
+def test_interpolative_compression_keeps_w_sparse():
+    # the same channel counts as the SVD basis, with the kept channels the automaton's own:
+    # far fewer nonzeros per site tensor
+    mpo = wl.heisenberg_mpo(200, wl.cylinder_pairs(20, 10, 1.0, 0.5))
+    cs, ci = wl.compress_mpo(mpo, method="svd"), wl.compress_mpo(mpo, method="interpolative")
+    assert [cs.bond_dim(b) for b in range(201)] == [ci.bond_dim(b) for b in range(201)]
+    nnz = lambda m: sum(np.count_nonzero(w) for w in m.W)
+    assert nnz(ci) < 0.3 * nnz(cs)
+    assert all(lab[0] in ("start", "open", "done") for b in range(201) for lab in ci.channels[b])
 
 
 def test_compressed_paper_lattice_bond_dims():

@@ -142,6 +142,14 @@ def spin_window(couplings=SPIN_COUPLINGS):
     return bulk_window(mpo, R + 1)
 
 
+def _compressed(mpo, compress):
+    """compress: False (the automaton), True or "svd" (the SVD basis), "interpolative" (a
+    subset of the automaton's channels; the same channel counts with a sparser W)."""
+    if not compress:
+        return mpo
+    return compress_mpo(mpo, method="svd" if compress is True else compress)
+
+
 def _widest_window(mpo):
     """The two-site window at the first bond triple with the largest total channel count."""
     n = mpo.n_sites
@@ -157,7 +165,7 @@ def lattice_window(Lx=6, Ly=6, J1=1.0, J2=0.5, compress=False):
     k = 20 for 6 x 6, 32 for 20 x 10)."""
     n = Lx * Ly
     mpo = heisenberg_mpo(n, cylinder_pairs(Lx, Ly, J1, J2))
-    return _widest_window(compress_mpo(mpo) if compress else mpo)
+    return _widest_window(_compressed(mpo, compress))
 
 
 def electron_window(t=1.0, U=8.0, R=5):
@@ -193,7 +201,7 @@ def triangular_hubbard_window(Lx=6, Ly=6, t=1.0, U=8.5, compress=False):
     cutoff 1e-13 (Section VI-B: k = 26, the paper's figure for this lattice)."""
     n = Lx * Ly
     mpo = hubbard_mpo(n, triangular_hops(Lx, Ly, t), U)
-    return _widest_window(compress_mpo(mpo) if compress else mpo)
+    return _widest_window(_compressed(mpo, compress))
 
 
 def spin_heff_workload(m, nsec, seed=0, model="binomial", couplings=SPIN_COUPLINGS,
@@ -265,6 +273,16 @@ def workload_by_name(name):
         "electron_tri_xc6c_m96": lambda: electron_heff_workload(96, 3, n_center=6, max_block=24,
                                                                 name="electron_tri_xc6c_m96",
                                                                 window=triangular_hubbard_window(compress=True)),
+        # the same compressions keeping a subset of the automaton's channels (a sparser W)
+        "spin_j1j2_20x10ci_m4096": lambda: spin_heff_workload(
+            4096, 40, 0, name="spin_j1j2_20x10ci_m4096", window=lattice_window(20, 10, compress="interpolative")),
+        "spin_j1j2_20x10ci_m200": lambda: spin_heff_workload(
+            200, 10, 7, name="spin_j1j2_20x10ci_m200", window=lattice_window(20, 10, compress="interpolative")),
+        "electron_tri_xc6ci_m2048": lambda: electron_heff_workload(
+            2048, 0, name="electron_tri_xc6ci_m2048", window=triangular_hubbard_window(compress="interpolative")),
+        "electron_tri_xc6ci_m96": lambda: electron_heff_workload(
+            96, 3, n_center=6, max_block=24, name="electron_tri_xc6ci_m96",
+            window=triangular_hubbard_window(compress="interpolative")),
         "electron_tri_xc6_m96": lambda: electron_heff_workload(96, 3, n_center=6, max_block=24,
                                                                name="electron_tri_xc6_m96",
                                                                window=triangular_hubbard_window()),

@@ -307,9 +307,17 @@ def bulk_window(mpo, site):
     }
 
 
-def compress_mpo(mpo, cutoff=1e-13):
+def compress_mpo(mpo, cutoff=1e-13, method="svd"):
     """SVD compression of an MPO's channels (Section VI-B: the electron MPO is compressed with
     an SVD cutoff of 1e-13).
+
+    ``method="interpolative"`` gives the same channel counts but keeps a subset of the
+    original channels instead of rotating to singular vectors: in each pass the rank-revealing
+    (column-pivoted) QR of a sector's vectors picks the independent channels (the pivots whose
+    |R_ii| exceed the cutoff times the bond's largest), the others are written as combinations
+    of them, and only the neighbouring site's tensor absorbs those combinations.  The kept
+    channels' own rows (or columns) stay the automaton's sparse operators, so W stays far
+    sparser than in the SVD basis.
 
     The ``start`` and ``done`` channels are kept as they are; the other channels of every
     bond are replaced by a minimal set of linear combinations, charge sector by charge sector
@@ -410,6 +418,10 @@ def compress_mpo(mpo, cutoff=1e-13):
         return labels
 
     labels = [list(mpo.channels[b]) for b in range(N + 1)]
+    if method == "interpolative":
+        return _compress_interpolative(mpo, W, special, q_of, conj, sectors, plan_bond, cutoff)
+    if method != "svd":
+        raise ValueError(f"unknown compression method {method!r}")
     # pass 1: left to right over the bonds 1..N-1 (right bond of site n = b - 1)
     for b in range(1, N):
         n = b - 1
@@ -463,6 +475,86 @@ def compress_mpo(mpo, cutoff=1e-13):
     charges = [np.asarray(q_of[b], dtype=np.int32).reshape(-1, nq) for b in range(N + 1)]
     conjs = [np.asarray(conj[b], dtype=np.int32) for b in range(N + 1)]
     # drop round-off below the cutoff's scale so that structurally zero blocks stay zero
+    for n in range(N):
+        scale = np.abs(W[n]).max()
+        W[n][np.abs(W[n]) < 1e-15 * scale] = 0.0
+    return MPO(W=W, channels=labels, charges=charges, conj=conjs, phys=mpo.phys, op_charge=dict(mpo.op_charge))
+
+
+def _pivoted_subset(M, cutoff, scale):
+    """Rank-revealing selection on the columns of M: (kept column indices, C) with
+    M = M[:, kept] @ C (C[:, kept] = identity up to rounding)."""
+    import scipy.linalg as sl
+    if M.shape[1] == 0:
+        return [], np.zeros((0, 0))
+    _, R, piv = sl.qr(M, mode="economic", pivoting=True)
+    diag = np.abs(np.diag(R))
+    r = int(np.sum(diag > cutoff * scale)) if scale > 0 else 0
+    kept = sorted(int(p) for p in piv[:r])
+    if r == 0:
+        return [], np.zeros((0, M.shape[1]))
+    C, *_ = np.linalg.lstsq(M[:, kept], M, rcond=None)
+    C[np.abs(C) < 1e-14] = 0.0
+    for i, k in enumerate(kept):                      # exact identity on the kept columns
+        C[:, k] = 0.0
+        C[i, k] = 1.0
+    return kept, C
+
+
+def _compress_interpolative(mpo, W, special, q_of, conj, sectors, plan_bond, cutoff):
+    """The two passes of compress_mpo with a subset of the original channels kept."""
+    import scipy.linalg as sl
+    N = len(W)
+    d = mpo.phys.shape[0]
+    labels = [list(mpo.channels[b]) for b in range(N + 1)]
+
+    def largest(mats):
+        vals = [np.abs(np.diag(sl.qr(M, mode="r", pivoting=True)[0])).max() for M in mats if M.size]
+        return max(vals) if vals else 0.0
+
+    def apply(b, choice):
+        """choice[q] = (kept channel list, C) for every sector of bond b, including the -q
+        partners; rebuild bond b keeping the start / done channels and the kept ones."""
+        keep = sorted(special[b] | {w for q, (ks, _) in choice.items() for w in ks})
+        pos = {w: i for i, w in enumerate(keep)}
+        return keep, pos
+
+    for pass_ in (1, 2):
+        bonds = range(1, N) if pass_ == 1 else range(N - 1, 0, -1)
+        for b in bonds:
+            groups = sectors(b)
+            canon = plan_bond(b, groups)
+            mats = {}
+            for q, ws, partners in canon:
+                if pass_ == 1:       # columns of W[b-1] as vectors over (wl, t, s)
+                    mats[q] = W[b - 1][..., ws].reshape(-1, len(ws))
+                else:                # rows of W[b] as vectors over (t, s, wr): columns of the transpose
+                    mats[q] = W[b][ws].reshape(len(ws), -1).T
+            scale = largest(mats.values())
+            choice = {}
+            for q, ws, partners in canon:
+                kept_i, C = _pivoted_subset(mats[q], cutoff, scale)
+                choice[q] = ([ws[i] for i in kept_i], ws, C)
+                if partners is not None:
+                    choice[tuple(-v for v in q)] = ([partners[i] for i in kept_i], partners, C)
+            # combine: pass 1 moves the dropped columns' weight into the rows of W[b] of the
+            # kept channels (new row k = sum_j C[k, j] row j); pass 2 moves the dropped rows'
+            # weight into the columns of W[b-1] (new col k = sum_i col i C[k, i])
+            for q, (kept, ws, C) in choice.items():
+                if pass_ == 1:
+                    W[b][kept] = np.tensordot(C, W[b][ws], axes=(1, 0))
+                else:
+                    W[b - 1][..., kept] = np.tensordot(W[b - 1][..., ws], C.T, axes=(3, 0))
+            keep = sorted(special[b] | {w for (kept, _, _) in choice.values() for w in kept})
+            W[b - 1] = W[b - 1][..., keep]
+            W[b] = W[b][keep]
+            old_to_new = {w: i for i, w in enumerate(keep)}
+            q_of[b] = q_of[b][keep]
+            conj[b] = np.array([old_to_new[int(conj[b][w])] for w in keep], dtype=np.int64)
+            labels[b] = [labels[b][w] for w in keep]
+            special[b] = {old_to_new[w] for w in special[b]}
+    charges = [np.asarray(q_of[b], dtype=np.int32).reshape(-1, mpo.charges[0].shape[1]) for b in range(N + 1)]
+    conjs = [np.asarray(conj[b], dtype=np.int32) for b in range(N + 1)]
     for n in range(N):
         scale = np.abs(W[n]).max()
         W[n][np.abs(W[n]) < 1e-15 * scale] = 0.0
