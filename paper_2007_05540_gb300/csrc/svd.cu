@@ -359,40 +359,78 @@ __global__ void __launch_bounds__(SVD_BT) svd_block_sweep_kernel(const SvdSector
             float* J = base + sc.j32_off;
             float* V = base + sc.v32_off;
             __syncthreads();
-            // 1. G = P^T P: thread t owns entries (a, b) = (t / 16, 2 (t % 16) + u), u < 2
-            constexpr int GE = SVD_PC * SVD_PC / SVD_BT;                   // entries per thread
-            const int ga = tid / (SVD_PC / GE), gb0 = (tid % (SVD_PC / GE)) * GE;
-            float acc[GE];
+            // 1. G = P^T P, register-tiled: thread t takes the 4 x 4 block blk = t / 8 of G
+            //    (rows 4 (blk / 8) .., columns 4 (blk % 8) ..) over the tile rows g, g + 8, ...
+            //    (g = t % 8), and the 8 partial sums of a block (8 consecutive lanes) are added
+            //    by shuffles: 8 shared-memory loads per 16 FMAs
+            static_assert(SVD_PC == 32 && SVD_BT == 512 && SVD_TR % 8 == 0, "Gram tiling assumes 32 columns");
+            const int gblk = tid >> 3, gg = tid & 7;
+            const int ga0 = 4 * (gblk >> 3), gb0 = 4 * (gblk & 7);
+            float acc[4][4];
 #pragma unroll
-            for (int u = 0; u < GE; ++u) acc[u] = 0.f;
-            for (int r0 = 0; r0 < sc.r; r0 += SVD_TR) {
-                for (int e = tid; e < SVD_TR * SVD_PC; e += SVD_BT) {
-                    const int a = e / SVD_TR, rr = e % SVD_TR;
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            // tiles of SVD_TR rows; the next tile's loads are issued into registers before the
+            // current tile is used, so their latency overlaps the arithmetic
+            constexpr int TE = SVD_TR * SVD_PC / SVD_BT;                    // tile elements per thread
+            float nxt[TE];
+            auto load_tile = [&](const float* M, int rows, int r0) {
+#pragma unroll
+                for (int u = 0; u < TE; ++u) {
+                    const int e = tid + SVD_BT * u, a = e / SVD_TR, rr = e % SVD_TR;
                     const int cidx = col[a];
-                    tile[rr][a] = (cidx >= 0 && r0 + rr < sc.r) ? J[(int64_t)cidx * sc.r + r0 + rr] : 0.f;
+                    nxt[u] = (cidx >= 0 && r0 + rr < rows) ? M[(int64_t)cidx * rows + r0 + rr] : 0.f;
                 }
-                __syncthreads();
-#pragma unroll 8
-                for (int rr = 0; rr < SVD_TR; ++rr) {
-                    const float x = tile[rr][ga];
+            };
+            auto stage_tile = [&]() {
 #pragma unroll
-                    for (int u = 0; u < GE; ++u) acc[u] = fmaf(x, tile[rr][gb0 + u], acc[u]);
+                for (int u = 0; u < TE; ++u) {
+                    const int e = tid + SVD_BT * u;
+                    tile[e % SVD_TR][e / SVD_TR] = nxt[u];
+                }
+            };
+            load_tile(J, sc.r, 0);
+            for (int r0 = 0; r0 < sc.r; r0 += SVD_TR) {
+                stage_tile();
+                __syncthreads();
+                if (r0 + SVD_TR < sc.r) load_tile(J, sc.r, r0 + SVD_TR);
+#pragma unroll 4
+                for (int rr = gg; rr < SVD_TR; rr += 8) {
+                    float xa[4], xb[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) { xa[i] = tile[rr][ga0 + i]; xb[i] = tile[rr][gb0 + i]; }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], xb[j], acc[i][j]);
                 }
                 __syncthreads();
             }
 #pragma unroll
-            for (int u = 0; u < GE; ++u) {
-                const int b = gb0 + u;
-                G[ga][b] = (ga < nc && b < nc) ? acc[u] : (ga == b ? 1.f : 0.f);
-                W[ga][b] = ga == b ? 1.f : 0.f;
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], o);
+            if (gg == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int a = ga0 + i, b = gb0 + j;
+                        G[a][b] = (a < nc && b < nc) ? acc[i][j] : (a == b ? 1.f : 0.f);
+                    }
             }
+            for (int e = tid; e < SVD_PC * SVD_PC; e += SVD_BT) W[e / SVD_PC][e % SVD_PC] = (e / SVD_PC == e % SVD_PC);
             __syncthreads();
-            // off-diagonal measure before the rotations
+            // off-diagonal measure before the rotations (thread t: row t / 16, columns 2 (t % 16) + u)
             {
+                const int ga = tid / (SVD_PC / 2), gbp = (tid % (SVD_PC / 2)) * 2;
                 float m = 0.f;
 #pragma unroll
-                for (int u = 0; u < GE; ++u) {
-                    const int b = gb0 + u;
+                for (int u = 0; u < 2; ++u) {
+                    const int b = gbp + u;
                     if (ga < b && b < nc) {
                         const float d = sqrtf(G[ga][ga] * G[b][b]);
                         if (d > 0.f) m = fmaxf(m, fabsf(G[ga][b]) / d);
@@ -409,11 +447,13 @@ __global__ void __launch_bounds__(SVD_BT) svd_block_sweep_kernel(const SvdSector
                     const float gab = G[a][b], gaa = G[a][a], gbb = G[b][b];
                     float c = 1.f, sn = 0.f;
                     if (gab != 0.f && gaa > 0.f && gbb > 0.f && fabsf(gab) > 1e-7f * sqrtf(gaa * gbb)) {
-                        const double zeta = ((double)gbb - gaa) / (2.0 * gab);
-                        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        const double cd = 1.0 / sqrt(1.0 + t * t);
-                        c = (float)cd;
-                        sn = (float)(cd * t);
+                        // the rotation in FP32 (this phase only preconditions; FP64 arithmetic
+                        // runs at GB300's much lower FP64 rate): a zeta too large to square
+                        // gives t = 0, the limit of the formula
+                        const float zeta = (gbb - gaa) / (2.f * gab);
+                        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                        c = rsqrtf(fmaf(t, t, 1.f));
+                        sn = c * t;
                     }
                     rc[tid] = c;
                     rs[tid] = sn;
@@ -449,32 +489,46 @@ __global__ void __launch_bounds__(SVD_BT) svd_block_sweep_kernel(const SvdSector
                 }
                 __syncthreads();
             }
-            // 3. P <- P W for the columns of J (r rows) and of V (k rows), 64-row tiles
+            // 3. P <- P W for the columns of J (r rows) and of V (k rows), 128-row tiles,
+            //    register-tiled: warp w takes the output columns 2w, 2w + 1 (their W columns
+            //    held in registers), lane l the tile rows l, l + 32, l + 64, l + 96: 32 shared-
+            //    memory loads per 64 FMAs, coalesced column stores
+            static_assert(SVD_BT / 32 == SVD_PC / 2 && SVD_TR == 128, "update tiling: one warp per column pair");
+            const int ua = 2 * (tid >> 5), ul = tid & 31;
+            float w0[SVD_PC], w1[SVD_PC];
+#pragma unroll
+            for (int bb = 0; bb < SVD_PC; ++bb) { w0[bb] = W[bb][ua]; w1[bb] = W[bb][ua + 1]; }
             for (int pass = 0; pass < 2; ++pass) {
                 float* M = pass == 0 ? J : V;
                 const int rows = pass == 0 ? sc.r : sc.k;
+                load_tile(M, rows, 0);
                 for (int r0 = 0; r0 < rows; r0 += SVD_TR) {
-                    for (int e = tid; e < SVD_TR * SVD_PC; e += SVD_BT) {
-                        const int a = e / SVD_TR, rr = e % SVD_TR;
-                        const int cidx = col[a];
-                        tile[rr][a] = (cidx >= 0 && r0 + rr < rows) ? M[(int64_t)cidx * rows + r0 + rr] : 0.f;
+                    stage_tile();
+                    __syncthreads();
+                    if (r0 + SVD_TR < rows) load_tile(M, rows, r0 + SVD_TR);
+                    float o0[4], o1[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = ul + 32 * i;
+                        float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+                        for (int bb = 0; bb < SVD_PC; ++bb) {
+                            const float t = tile[rr][bb];
+                            v0 = fmaf(t, w0[bb], v0);
+                            v1 = fmaf(t, w1[bb], v1);
+                        }
+                        o0[i] = v0;
+                        o1[i] = v1;
                     }
                     __syncthreads();
-                    float out[SVD_TR * SVD_PC / SVD_BT];
+                    const int c0 = col[ua], c1 = col[ua + 1];
 #pragma unroll
-                    for (int u = 0; u < SVD_TR * SVD_PC / SVD_BT; ++u) {
-                        const int e = tid + SVD_BT * u, a = e / SVD_TR, rr = e % SVD_TR;
-                        float v = 0.f;
-#pragma unroll 8
-                        for (int bb = 0; bb < SVD_PC; ++bb) v = fmaf(tile[rr][bb], W[bb][a], v);
-                        out[u] = v;
-                    }
-                    __syncthreads();
-#pragma unroll
-                    for (int u = 0; u < SVD_TR * SVD_PC / SVD_BT; ++u) {
-                        const int e = tid + SVD_BT * u, a = e / SVD_TR, rr = e % SVD_TR;
-                        const int cidx = col[a];
-                        if (cidx >= 0 && r0 + rr < rows) M[(int64_t)cidx * rows + r0 + rr] = out[u];
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = ul + 32 * i;
+                        if (r0 + rr < rows) {
+                            if (c0 >= 0) M[(int64_t)c0 * rows + r0 + rr] = o0[i];
+                            if (c1 >= 0) M[(int64_t)c1 * rows + r0 + rr] = o1[i];
+                        }
                     }
                 }
             }
@@ -726,7 +780,11 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
     SVD_CK(cudaMemcpyAsync(d_pair_off, S->pair_off.data(), S->pair_off.size() * sizeof(int), cudaMemcpyHostToDevice,
                            st));
     SVD_CK(cudaMemsetAsync(d_bar, 0, 3 * sizeof(unsigned int), st));
-    auto sweeps = [&](auto* base, float tol, int max_sweeps, int& out) -> int {
+    // stop_below: a sweep whose largest off-diagonal measure (taken before its rotations) is
+    // below this ends the loop; for the FP64 phase it is sqrt(tol): Jacobi sweeps converge
+    // quadratically, so that sweep's rotations leave the measure near tol, and a further
+    // sweep would only confirm it
+    auto sweeps = [&](auto* base, float stop_below, int max_sweeps, int& out) -> int {
         using T = typename std::remove_pointer<decltype(base)>::type;
         out = 0;
         if (kk_all < 2) return HEFF_OK;
@@ -754,7 +812,7 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
             SVD_CK(cudaStreamSynchronize(st));
             if (e) return fail(HEFF_ERR_TIMEOUT, "SVD sweep: grid barrier timed out");
             ++out;
-            if (m < tol) break;
+            if (m < stop_below) break;
         }
         return HEFF_OK;
     };
@@ -816,8 +874,9 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
     if ((rc = heff::launch_bgemm(S->jv, ws, ws, ws, nullptr, nullptr, 1.0, stream))) return rc;
     svd_copy_w_kernel<<<dim3(128, nsec), 256, 0, st>>>(S->d_sec, ws);
     heff::count_launches(1);
-    // FP64 sweeps to convergence
-    if ((rc = sweeps(ws, 1e-14f, 40, S->fp64_sweeps))) return rc;
+    // FP64 sweeps to convergence: off-diagonal measure 1e-14, i.e. stop after the sweep that
+    // saw at most 1e-7
+    if ((rc = sweeps(ws, 1e-7f, 40, S->fp64_sweeps))) return rc;
     const int sweep = S->fp64_sweeps;
     svd_norms_kernel<<<dim3((S->max_k + 3) / 4 + 1, nsec), 128, 0, st>>>(S->d_sec, ws, sv);
     heff::count_launches(1);
