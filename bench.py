@@ -84,7 +84,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's default tile widths (for profiling: serialised launches under a "
                          "profiler would time the candidates differently)")
-    ap.add_argument("--part", default="", choices=["", "lanczos", "svd", "env_update", "backward", "energy"],
+    ap.add_argument("--part", default="",
+                    choices=["", "lanczos", "svd", "env_update", "backward", "energy", "batched"],
                     help="time one step of the DMRG bond update alone and print its own JSON line "
                          "(the profiling cases): the FP64 Lanczos eigensolver (30 iterations, BF16x3 "
                          "matvecs), the block SVD truncation, the environment update, the gradients")
@@ -587,6 +588,9 @@ def run_part(args):
         out = backward_timing(dev, stream, precs)
     elif args.part == "energy":
         out = ground_state_compare(args.workload, dev, stream)
+    elif args.part == "batched":
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        out = batched_graph(args.workload, 32, dev, stream, flush)
     else:
         out = svd_timing(args, dev, stream)
     print(json.dumps({"part": args.part, "workload": args.workload, **out}), flush=True)
