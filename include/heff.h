@@ -456,6 +456,15 @@ int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1, const voi
                        const void* x, void* y, void* stream);
 
 /*
+ * heff_apply_noalloc_status -- heff_workspace_status for the built-in workspace of the
+ * current device: reads and clears its sticky error flag (HEFF_ERR_TIMEOUT when a bounded
+ * device-side wait expired in the last heff_apply_noalloc, whose output is then incomplete).
+ * heff_apply_noalloc clears the flag when it starts, so read it after a call whose result
+ * matters.  Allocates nothing; synchronises `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+int heff_apply_noalloc_status(const heff_plan* plan, void* stream);
+
+/*
  * Tensor-core tile variants of a GEMM (the plan builds all three task lists):
  *   HEFF_TILE_256       one CTA per 128 x 256 output tile (the default)
  *   HEFF_TILE_128       one CTA per 128 x 128 output tile

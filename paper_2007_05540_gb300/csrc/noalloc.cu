@@ -68,3 +68,19 @@ extern "C" int heff_apply_noalloc(heff_plan* plan, const void* L, const void* W1
     if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return heff_apply(plan, L, W1, W2, R, x, y, ws, (size_t)HEFF_NOALLOC_WORKSPACE_BYTES, stream);
 }
+
+// Read and clear the error flag of the built-in workspace: an expired bounded wait inside a
+// heff_apply_noalloc call leaves it set (heff_apply_noalloc clears it when it starts, so read
+// it after each call whose result matters).  No allocation either.
+extern "C" int heff_apply_noalloc_status(const heff_plan* plan, void* stream) {
+    heff::clear_error();
+    if (!plan) return fail(HEFF_ERR_INVALID_ARG, "heff_apply_noalloc_status: null plan");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(HEFF_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    void* ws = nullptr;
+    int rc = static_workspace(dev, &ws);
+    if (rc) return rc;
+    return heff_workspace_status(plan, ws, (size_t)HEFF_NOALLOC_WORKSPACE_BYTES, stream);
+}

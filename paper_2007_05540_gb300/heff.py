@@ -74,6 +74,7 @@ _sig = {
     "heff_apply": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "heff_apply_batched": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(_vp), _P(_vp), _i32, _vp, _sz, _vp]),
     "heff_apply_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "heff_apply_noalloc_status": (C.c_int, [_vp, _vp]),
     "heff_svd_create": (C.c_int, [_vp, _P(_vp)]),
     "heff_svd_workspace_size": (C.c_int, [_vp, _P(_sz)]),
     "heff_svd_compute": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _P(_i32)]),
@@ -501,6 +502,11 @@ def heff_apply_noalloc(plan, L, W1, W2, R, x, y, stream=None):
     calls that overlap on the GPU race on that shared workspace."""
     _check(_lib.heff_apply_noalloc(plan, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(x), _ptr(y),
                                    _stream(stream)), "heff_apply_noalloc")
+
+
+def heff_apply_noalloc_status(plan, stream=None):
+    """Read and clear the built-in workspace's error flag; returns the status (0 or -6)."""
+    return int(_lib.heff_apply_noalloc_status(plan, _stream(stream)))
 
 
 TILE_256, TILE_128, TILE_PAIR_256, TILE_VARIANTS = 256, 128, 512, 3

@@ -309,3 +309,48 @@ def test_wait_status_entries_check_arguments_before_touching_the_device():
     with pytest.raises(heff.HeffError) as e:
         heff.heff_wait_selftest(P64.handle, small, 0, st)
     assert e.value.code == -1
+
+
+def test_ground_state_and_block_status_entries_check_arguments():
+    """heff_ground_state, heff_env_status and heff_grad_status reject bad arguments on the host
+    before any CUDA call; FP64 block products have no device-side waits (status HEFF_OK)."""
+    import types
+
+    import torch
+    w = wl.workload_by_name("spin_m24")
+    lays, bufs = library_problem(w)
+    st = types.SimpleNamespace(cuda_stream=0)
+    t = torch.zeros(64, dtype=torch.float64)             # host memory, never dereferenced
+    small = torch.empty(16, dtype=torch.uint8)
+    Pb = _plan(w, lays, bufs, "bf16x3", "f64")
+    P32 = _plan(w, lays, bufs, "bf16x3", "f32")
+    # null tensors / output
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_ground_state(Pb.handle, None, None, t, t, t, t, 10, 2, 1e-8, t, small, None, small, st)
+    assert e.value.code == -1
+    # io dtype: the eigensolvers need FP64 tensors
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_ground_state(P32.handle, None, t, t, t, t, t, 10, 2, 1e-8, t, small, None, small, st)
+    assert e.value.code == -3
+    # step count, cycles, tolerance
+    for n_iter, cycles, tol in ((0, 2, 1e-8), (127, 2, 1e-8), (10, 0, 1e-8), (10, 2, -1.0)):
+        with pytest.raises(heff.HeffError) as e:
+            heff.heff_ground_state(Pb.handle, None, t, t, t, t, t, n_iter, cycles, tol, t, small, None, small, st)
+        assert e.value.code == -1
+    # the FP64 plan must be FP64
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_ground_state(Pb.handle, Pb.handle, t, t, t, t, t, 10, 2, 1e-8, t, small, small, small, st)
+    assert e.value.code == -1
+    # a workspace below heff_ground_state_workspace_size
+    assert heff.heff_ground_state_workspace_size(Pb.handle, 10) > small.numel()
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_ground_state(Pb.handle, None, t, t, t, t, t, 10, 2, 1e-8, t, small, None, small, st)
+    assert e.value.code == -7
+    # status calls
+    hs = [x.handle for x in lays]
+    g = heff.heff_grad_plan_create(*hs, bufs["W1"], bufs["W2"], 0)
+    assert heff.heff_grad_status(g, small, st) == 0                       # FP64 products: no waits
+    heff.heff_grad_plan_set_precision(g, "bf16x3")
+    assert heff.heff_grad_status(g, small, st) == -7                      # too small
+    assert heff.heff_grad_status(None, small, st) == -1
+    heff.heff_grad_plan_destroy(g)

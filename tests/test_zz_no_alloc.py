@@ -55,6 +55,7 @@ def test_noalloc_matches_apply_on_two_calls(name, prec):
         y = torch.full_like(d["x"], float("nan"))
         heff.heff_apply_noalloc(plan.handle, d["L"], d["W1"], d["W2"], d["R"], d["x"], y)
         torch.cuda.synchronize()
+        assert heff.heff_apply_noalloc_status(plan.handle) == 0    # no bounded wait expired
         y = y.double().cpu().numpy()
         assert not np.isnan(y).any()
         err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
