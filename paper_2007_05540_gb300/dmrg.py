@@ -14,8 +14,10 @@ structure (sector charges and dimensions) that the truncation returns.  The swee
 start from a product state with the requested total charge (all sites then both left-
 and right-canonical), so no orthonormalisation of a random state is needed; two-site
 updates grow the bonds up to the schedule's m.  Only the matvecs use the plan's
-precision; vectors, orthogonalisation, the SVD and the environments are FP64.  With a
-split precision the energy of the final bond's vector is recomputed with an FP64 apply.
+precision; vectors, orthogonalisation, the SVD and the environments are FP64 buffers, and
+the environment updates' block products run in FP64 or, with ``env_precision="bf16x3"``, on
+the tensor cores (FP32-accumulated, about 1e-5 relative per update).  With a split
+precision the energy of the final bond's vector is recomputed with an FP64 apply.
 """
 import numpy as np
 
@@ -49,7 +51,7 @@ class GpuDMRG:
     ``done_index(N)`` the boundary channels) in the sector of total charge ``total``."""
 
     def __init__(self, mpo, total, precision="fp64", n_iter=20, cutoff=1e-12, states=None, device="cuda",
-                 solver="lanczos", davidson_vecs=2, seed=0):
+                 solver="lanczos", davidson_vecs=2, seed=0, env_precision="fp64"):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -59,6 +61,7 @@ class GpuDMRG:
         self.nq = self.phys.shape[1]
         self.total = np.asarray(total, dtype=np.int32).reshape(self.nq)
         self.precision = precision
+        self.env_precision = env_precision
         self.n_iter = int(n_iter)
         self.cutoff = float(cutoff)
         if solver not in ("lanczos", "davidson"):
@@ -117,6 +120,7 @@ class GpuDMRG:
         W_l, W_host, W_dev = self.W[n]
         plan = heff.heff_env_plan_create(env[0].handle, site[0].handle, W_l.handle, new_l.handle, W_host, side)
         try:
+            heff.heff_env_plan_set_precision(plan, self.env_precision)
             ws = torch.empty(max(heff.heff_env_workspace_size(plan), 256), dtype=torch.uint8, device=self.dev)
             out = torch.empty(new_l.nelem, dtype=torch.float64, device=self.dev)
             heff.heff_env_update(plan, env[1], site[1], W_dev, out, ws)
@@ -210,13 +214,13 @@ class GpuDMRG:
 
 
 def dmrg(mpo, total, m_schedule, precision="fp64", n_iter=20, cutoff=1e-12, device="cuda", solver="lanczos",
-         davidson_vecs=2, states=None):
+         davidson_vecs=2, states=None, env_precision="fp64"):
     """Run one full sweep per entry of ``m_schedule`` (the bond cap of that sweep); the
     eigensolver is Lanczos (n_iter steps) or Algorithm 1's Davidson (davidson_vecs vectors).
     ``states`` (one local state per site) chooses the product state the sweeps start from.
     Returns dict(sweep_energies, energy, refined_energy, bond_dims, max_discarded)."""
     run = GpuDMRG(mpo, total, precision, n_iter, cutoff, states=states, device=device, solver=solver,
-                  davidson_vecs=davidson_vecs)
+                  davidson_vecs=davidson_vecs, env_precision=env_precision)
     for m in m_schedule:
         run.sweep(int(m))
     out = {"sweep_energies": list(run.energies), "energy": run.energies[-1], "bond_dims": run.bond_dims(),
