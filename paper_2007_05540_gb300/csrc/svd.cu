@@ -157,6 +157,15 @@ __global__ void svd_copy_w_kernel(const SvdSector* __restrict__ secs, double* __
 // barrier is a counter and a generation word in global memory; its wait is bounded (about a
 // second), after which the kernel sets err and returns.  Each block writes the largest
 // off-diagonal measure it saw to block_max[blockIdx.x].
+//
+// Column norms are carried instead of recomputed per pair (as in the standard one-sided
+// Jacobi codes): the sweep starts by computing every column's squared norm into nrm
+// (indexed like the singular values, s_off + column), and a rotation by tan(theta) = t of
+// columns with squared norms a, b and inner product g leaves exactly a - t g and b + t g
+// (the rotation zeroes the inner product).  A pair then needs one dot product instead of
+// three.  The updates change a norm by t g, tiny once the columns are nearly orthogonal, and
+// the norms are recomputed at the start of every sweep, so the rounding drift stays at a
+// few ulps of the column's norm.
 constexpr int SVD_SWEEP_NT = 256;
 #ifndef SVD_UNROLL
 #define SVD_UNROLL 8        // column pieces per lane loaded together in a pair's loops
@@ -201,7 +210,8 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 template <typename T>
 __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector* __restrict__ secs, int nsec,
                                                                  const int* __restrict__ pair_off, int kk_all,
-                                                                 T* __restrict__ base, float* __restrict__ block_max,
+                                                                 T* __restrict__ base, T* __restrict__ nrm,
+                                                                 int ncols_all, float* __restrict__ block_max,
                                                                  unsigned int* __restrict__ bar, int* __restrict__ err) {
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -209,7 +219,32 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
     const int gw = blockIdx.x * warps + w, nw = gridDim.x * warps;
     const int npairs = pair_off[nsec];
     float mymax = 0.f;
-    for (int round = 0; round < kk_all - 1; ++round) {
+    constexpr int UJ = SVD_UNROLL;
+    // squared column norms (one warp per column; the sectors' s_off are prefix sums of k)
+    bool go = true;
+    if (ncols_all > 0) {
+        for (int item = gw; item < ncols_all; item += nw) {
+            int lo = 0, hi = nsec;                       // sector: s_off[lo] <= item < s_off[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (secs[mid].s_off <= item) lo = mid; else hi = mid;
+            }
+            const SvdSector s = secs[lo];
+            const T* c = base + (F32 ? s.j32_off : s.j_off) + (int64_t)(item - s.s_off) * s.r;
+            T a = 0;
+            for (int i0 = lane; i0 < s.r; i0 += 32 * UJ) {
+                T u[UJ];
+#pragma unroll
+                for (int t = 0; t < UJ; ++t) u[t] = i0 + 32 * t < s.r ? c[i0 + 32 * t] : (T)0;
+#pragma unroll
+                for (int t = 0; t < UJ; ++t) a = fma(u[t], u[t], a);
+            }
+            a = warp_sum_t(a);
+            if (lane == 0) nrm[item] = a;
+        }
+        go = grid_barrier(bar, bar + 1, gridDim.x, err);
+    }
+    for (int round = 0; go && round < kk_all - 1; ++round) {
         for (int item = gw; item < npairs; item += nw) {
             int lo = 0, hi = nsec;                       // sector: pair_off[lo] <= item < pair_off[lo + 1]
             while (hi - lo > 1) {
@@ -229,8 +264,10 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
             T* cq = J + (int64_t)q * s.r;
             // (the column pieces of UJ iterations are loaded together: the pair's loops are
             // bound by L2 latency; each lane's sums keep their order)
-            constexpr int UJ = SVD_UNROLL;
-            T a = 0, b = 0, g = 0;
+            T* np = nrm + s.s_off + p;
+            T* nq = nrm + s.s_off + q;
+            const T a = *np, b = *nq;
+            T g = 0;
             for (int i0 = lane; i0 < s.r; i0 += 32 * UJ) {
                 T u[UJ], v[UJ];
 #pragma unroll
@@ -240,14 +277,9 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
                     v[t] = i < s.r ? cq[i] : (T)0;
                 }
 #pragma unroll
-                for (int t = 0; t < UJ; ++t) {
-                    if (i0 + 32 * t >= s.r) break;
-                    a = fma(u[t], u[t], a);
-                    b = fma(v[t], v[t], b);
-                    g = fma(u[t], v[t], g);
-                }
+                for (int t = 0; t < UJ; ++t) g = fma(u[t], v[t], g);
             }
-            a = warp_sum_t(a); b = warp_sum_t(b); g = warp_sum_t(g);
+            g = warp_sum_t(g);
             if (g == (T)0 || a == (T)0 || b == (T)0) continue;
             const double da = a, db = b, dg = g;
             const double meas = fabs(dg) / sqrt(da * db);
@@ -257,6 +289,10 @@ __global__ void __launch_bounds__(SVD_SWEEP_NT) svd_sweep_kernel(const SvdSector
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double cd = 1.0 / sqrt(1.0 + t * t);
             const T c = (T)cd, sn = (T)(cd * t);
+            if (lane == 0) {                             // the rotated columns' squared norms
+                *np = (T)(da - t * dg);
+                *nq = (T)(db + t * dg);
+            }
             // rotate the two columns of J and of V in one loop (both only need c, sn)
             T* V = base + (F32 ? s.v32_off : s.v_off);
             T* vp = V + (int64_t)p * s.k;
@@ -798,9 +834,11 @@ extern "C" int heff_svd_compute(heff_svd* S, const double* x, void* workspace, s
         const SvdSector* secs = S->d_sec;
         int nsec_i = nsec, kk_i = kk_all;
         T* base_t = base;
+        T* nrm_t = reinterpret_cast<T*>(sv);             // the singular-value slots, free until the end
+        int ncols_i = (int)S->s_total;
         while (out < max_sweeps) {
             void* args[] = {(void*)&secs, (void*)&nsec_i, (void*)&d_pair_off, (void*)&kk_i, (void*)&base_t,
-                            (void*)&slots, (void*)&d_bar, (void*)&d_err};
+                            (void*)&nrm_t, (void*)&ncols_i, (void*)&slots, (void*)&d_bar, (void*)&d_err};
             SVD_CK(cudaLaunchCooperativeKernel((const void*)svd_sweep_kernel<T>, dim3(grid), dim3(SVD_SWEEP_NT),
                                                args, 0, st));
             svd_offmax_kernel<<<1, 256, 0, st>>>(slots, grid, offmax);
