@@ -70,8 +70,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--mode", default="shard", choices=["shard", "replicas"],
                     help="N > 1: row shards of one apply + all-reduce of y (default), or independent problems")
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--workload", default="spin_m4096")
@@ -271,6 +271,39 @@ def _events_ms(fn, n, stream, flush=None):
     return float(np.mean(ts))
 
 
+def dense_gemm_rates(dev, stream):
+    """cuBLAS dense-GEMM rates of this GPU (through torch.matmul) in TF32 and FP64, and BF16
+    as a check against the measured peak: the denominators of the other precisions'
+    rooflines (square products, inputs resident, median of timed repetitions)."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, reps in (("bf16", torch.bfloat16, 8192, 10), ("tf32", torch.float32, 8192, 10),
+                                  ("fp64", torch.float64, 4096, 3)):
+            torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+            g = torch.Generator(device=dev).manual_seed(7)
+            a = torch.randn(n, n, device=dev, dtype=torch.float32, generator=g).to(dt)
+            b = torch.randn(n, n, device=dev, dtype=torch.float32, generator=g).to(dt)
+            c = torch.empty(n, n, device=dev, dtype=dt)
+            with torch.cuda.stream(stream):
+                torch.matmul(a, b, out=c)
+                ts = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    torch.matmul(a, b, out=c)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (float(np.median(ts)) * 1e-3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
 def extras(args, w, lays, bufs, dev, stream, flush, value):
     """Same workload in the other precisions, the eigensolver step around the apply, the
     SVD truncation, and the batched electron workload replayed from a captured graph."""
@@ -301,6 +334,22 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
         del P, d, ws, y
     out["applies_per_s"] = rates
     out["speedup_vs_fp64_gpu"] = {p: rates[p] / rates["fp64"] for p in rates if p != "fp64"}
+    # whole-apply rooflines of every precision against this GPU's cuBLAS rate for the dtype
+    canon = heff.Plan(Ll, W1l, W2l, Rl, xl, bufs["W1"], bufs["W2"], "fp64", "f64").flops_canonical
+    dense = dense_gemm_rates(dev, stream)
+    dt_of = {"bf16x3": "bf16", "tf32x3": "tf32", "fp64": "fp64"}
+    out["roofline_by_precision"] = {
+        "peaks_tflops": dense,
+        "peak_source": "cuBLAS GEMM through torch.matmul on this GPU (bf16, tf32: 8192^3; fp64: 4096^3)",
+        "note": "whole apply (prepare + pack + GEMM 1 + GEMM 2): canonical flops x applies/s over the dtype's "
+                "dense-GEMM rate; the split precisions issue three tensor-core products per useful "
+                "multiply-add (tensor_pipe_frac)"}
+    for p, r in rates.items():
+        u = canon * r / 1e12
+        e = {"useful_tflops": u, "frac": u / dense[dt_of[p]]}
+        if p != "fp64":
+            e["tensor_pipe_frac"] = 3.0 * e["frac"]
+        out["roofline_by_precision"][p] = e
 
     # eigensolver step: FP64 Lanczos (30 iterations) with BF16x3 and with FP64 matvecs,
     # the FP64 Rayleigh quotient of the mixed Ritz vector, then the block SVD truncation
