@@ -220,9 +220,12 @@ int heff_apply_batched(heff_plan* plan, const void* L, const void* W1, const voi
  * heff_lanczos -- lowest eigenpair of H_eff by n_iter Lanczos steps (the eigensolver of
  * the two-site DMRG step, Section II-C and III; the fixed-iteration alternative to the
  * Davidson routine of Algorithm 1), all in FP64 on the device except the matvecs, which
- * run in the plan's precision.  Full reorthogonalisation by two classical Gram-Schmidt
- * passes per step; the tridiagonal eigenproblem is solved on the device (bisection on the
- * Sturm count + inverse iteration).  The plan must use HEFF_DTYPE_F64 tensors.
+ * run in the plan's precision.  Each step applies the three-term recurrence, then one
+ * classical Gram-Schmidt pass against the whole basis (full reorthogonalisation), and a
+ * second pass when the first removed more than half of the vector's squared norm (the
+ * Daniel-Gragg-Kaufman-Stewart criterion); the tridiagonal eigenproblem is solved on the
+ * device (bisection on the Sturm count + inverse iteration).  The plan must use
+ * HEFF_DTYPE_F64 tensors.
  *   x0      device, nelem(x) doubles: start vector (need not be normalised, must be nonzero)
  *   x_out   device, nelem(x) doubles: normalised Ritz vector of the lowest Ritz value
  *   result  device, 3 + 2 * (n_iter + 1) doubles: [0] lowest Ritz value theta,

@@ -5,10 +5,18 @@
 // Every vector operation runs in FP64 on the device and the loop never synchronises with
 // the host.  Per iteration k:
 //   w = H v_k                       (heff_apply_prepared; any precision, FP64 vectors)
-//   h = V^T w, w -= V h   (twice)   (classical Gram-Schmidt with re-orthogonalisation,
-//                                    "CGS2": full reorthogonalisation against v_0..v_k;
-//                                    alpha_k = h_k + h2_k)
-//   beta_k = ||w||, v_{k+1} = w / beta_k
+//   a = v_k . (w - beta_{k-1} v_{k-1}),  w -= beta_{k-1} v_{k-1} + a v_k
+//                                   (the three-term recurrence, with ||w||^2 after it)
+//   h = V^T w, w -= V h             (classical Gram-Schmidt against v_0..v_k: the full
+//                                    reorthogonalisation, with ||w||^2 after it)
+//   h2 = V^T w, w -= V h2           (a second pass, only when the first removed more than half
+//                                    of ||w||^2: the criterion of Daniel, Gragg, Kaufman and
+//                                    Stewart (1976); "twice is enough")
+//   alpha_k = a + h_k (+ h2_k), beta_k = ||w||, v_{k+1} = w / beta_k
+// The recurrence goes first so that the Gram-Schmidt pass acts on a vector already
+// orthogonal to V up to the basis' own small loss of orthogonality: a pass applied to
+// H v_k itself would carry that loss, times ||H v_k|| / beta_k, into v_{k+1} (large once
+// the start vector is nearly an eigenvector, as in the later sweeps of DMRG).
 // then the lowest eigenpair of the (n x n) tridiagonal matrix is found on the device
 // (bisection + inverse iteration), and the Ritz vector x = sum_j s_j v_j is formed and
 // normalised.  If beta_k falls below 1e-13 |alpha_k| the Krylov space is invariant: the
@@ -29,13 +37,17 @@ constexpr int RT = 256;          // threads per reduction block
 constexpr int RB = 456;          // reduction blocks (partial sums per vector): 3 per SM on 152 SMs
 constexpr int VT = 8;            // vectors per multi-dot pass
 
+constexpr int GMAX = 4096;       // largest grid of the element-wise kernels (grid_for)
+
 // State in the Lanczos workspace (doubles): [0] n_eff (as double), [1] active flag,
-// [2] theta, [3] residual estimate, [8..8+NMAX) alpha, [8+NMAX..) beta,
-// then h (NMAX), s (NMAX), partials (RB * VT).
+// [2] theta, [3] residual estimate, [4] second Gram-Schmidt pass needed (this step),
+// [8..8+NMAX) alpha, [8+NMAX..) beta, then h (NMAX), s (NMAX), partials (RB * VT), the
+// partial sums of ||w||^2 after the three-term update (RB) and after a Gram-Schmidt pass
+// (GMAX), and a (the three-term projection of the current step).
 struct LzLayout {
     int nmax;
     int64_t n;
-    size_t off_state, off_h, off_s, off_part, off_T, off_V, bytes;
+    size_t off_state, off_h, off_s, off_part, off_wn, off_sq, off_a, off_T, off_V, bytes;
 };
 
 LzLayout lz_layout(int64_t n, int n_iter) {
@@ -48,6 +60,9 @@ LzLayout lz_layout(int64_t n, int n_iter) {
     l.off_h = o;     o = al(o + sizeof(double) * (size_t)l.nmax);
     l.off_s = o;     o = al(o + sizeof(double) * (size_t)l.nmax);
     l.off_part = o;  o = al(o + sizeof(double) * (size_t)RB * VT);
+    l.off_wn = o;    o = al(o + sizeof(double) * (size_t)RB);
+    l.off_sq = o;    o = al(o + sizeof(double) * (size_t)GMAX);
+    l.off_a = o;     o = al(o + sizeof(double));
     l.off_T = o;     o = al(o + sizeof(double) * 2 * (size_t)l.nmax * l.nmax);
     l.off_V = o;     o = al(o + sizeof(double) * (size_t)(l.nmax + 1) * (size_t)n);   // V + w
     l.bytes = o;
@@ -55,10 +70,13 @@ LzLayout lz_layout(int64_t n, int n_iter) {
 }
 
 struct Lz {
-    double* state;   // n_eff, active, theta, resid, alpha[nmax], beta[nmax]
+    double* state;   // n_eff, active, theta, resid, second pass, alpha[nmax], beta[nmax]
     double* h;
     double* s;
     double* part;
+    double* wn;      // partial sums of ||w||^2 after the three-term update (RB)
+    double* sq;      // partial sums of ||w||^2 after a combine (one per block of its grid)
+    double* a;       // the three-term projection a of the current step
     double* T;       // nmax x nmax matrix + nmax x nmax eigenvectors
     double* V;       // (nmax) basis vectors, then w
     int64_t n;
@@ -80,12 +98,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return v;
 }
 
+// Whether a gated kernel runs: gate 0 while the iteration is active, gate 1 only when the
+// active step also needs its second Gram-Schmidt pass (state[4]).
+__device__ __forceinline__ bool gated_off(const double* state, int gate) {
+    return state[1] == 0.0 || (gate == 1 && state[4] == 0.0);
+}
+
 // partial[b * VT + t] = sum over block b's chunk of V[j0 + t] . w, t < nv
 __global__ void __launch_bounds__(RT) multidot_kernel(const double* __restrict__ V, const double* __restrict__ w,
                                                       int64_t n, int j0, int nv, double* __restrict__ part,
-                                                      const double* __restrict__ state) {
+                                                      const double* __restrict__ state, int gate = 0) {
     __shared__ double sh[RT / 32];
-    if (state[1] == 0.0) return;
+    if (gated_off(state, gate)) return;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t beg = (int64_t)blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
     double acc[VT];
@@ -118,11 +142,44 @@ __global__ void __launch_bounds__(RT) multidot_kernel(const double* __restrict__
     }
 }
 
-// out[j0 + t] = (accumulate ? out : 0) + sum_b partial[b * VT + t]
-__global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int j0, int nv, double* out,
-                                   int accumulate, const double* __restrict__ state) {
+// The three-term recurrence of step k, in two launches: mode 0 writes partial sums of
+// v_k . (w - beta_{k-1} v_{k-1}) to part[b * VT] (a = their sum, by finish_dots into
+// *ap); mode 1 updates w -= beta_{k-1} v_{k-1} + a v_k and writes the partial sums of the
+// new ||w||^2 to wn[b].  k = 0 has no v_{k-1} term.
+__global__ void __launch_bounds__(RT) three_term_kernel(const double* __restrict__ V, double* __restrict__ w,
+                                                        int64_t n, int k, int nmax, double* __restrict__ part,
+                                                        double* __restrict__ wn, const double* __restrict__ state,
+                                                        const double* __restrict__ ap, int mode) {
     __shared__ double sh[RT / 32];
     if (state[1] == 0.0) return;
+    const double* vk = V + (int64_t)k * n;
+    const double* vp = k > 0 ? V + (int64_t)(k - 1) * n : vk;
+    const double b = k > 0 ? state[8 + nmax + k - 1] : 0.0;
+    const double a = mode == 1 ? *ap : 0.0;
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * RT;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += stride) {
+        const double x = w[i] - b * vp[i];
+        if (mode == 0) {
+            acc = fma(vk[i], x, acc);
+        } else {
+            const double y = x - a * vk[i];
+            w[i] = y;
+            acc = fma(y, y, acc);
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        if (mode == 0) part[blockIdx.x * VT] = acc;
+        else wn[blockIdx.x] = acc;
+    }
+}
+
+// out[j0 + t] = (accumulate ? out : 0) + sum_b partial[b * VT + t]
+__global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int j0, int nv, double* out,
+                                   int accumulate, const double* __restrict__ state, int gate = 0) {
+    __shared__ double sh[RT / 32];
+    if (gated_off(state, gate)) return;
     for (int t = 0; t < nv; ++t) {
         double v = 0.0;
         for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT + t];
@@ -131,18 +188,22 @@ __global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int 
     }
 }
 
-// y[i] = (beta_y * y[i]) + sign * sum_{j < nv} c[j] V[j][i]   (c from device memory)
+// y[i] = (beta_y * y[i]) + sign * sum_{j < nv} c[j] V[j][i]   (c from device memory); with
+// sq, also sq[b] = block b's sum of the new y[i]^2
 __global__ void __launch_bounds__(RT) combine_kernel(const double* __restrict__ V, int64_t n, int nv,
                                                      const double* __restrict__ c, double sign, double beta_y,
                                                      double* __restrict__ y, const double* __restrict__ state,
-                                                     int ignore_active) {
+                                                     int ignore_active, int gate = 0,
+                                                     double* __restrict__ sq = nullptr) {
     __shared__ double cs[128];
-    if (!ignore_active && state[1] == 0.0) return;
+    __shared__ double sh[RT / 32];
+    if (!ignore_active && gated_off(state, gate)) return;
     for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = c[j];
     __syncthreads();
     // two elements per iteration (their loads in flight together), then the remainder
     const int64_t stride = (int64_t)gridDim.x * RT;
     int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x;
+    double yy = 0.0;
     for (; i + stride < n; i += 2 * stride) {
         double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
@@ -150,14 +211,23 @@ __global__ void __launch_bounds__(RT) combine_kernel(const double* __restrict__ 
             a0 = fma(cs[j], V[(int64_t)j * n + i], a0);
             a1 = fma(cs[j], V[(int64_t)j * n + i + stride], a1);
         }
-        y[i] = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a0;
-        y[i + stride] = (beta_y == 0.0 ? 0.0 : beta_y * y[i + stride]) + sign * a1;
+        const double y0 = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a0;
+        const double y1 = (beta_y == 0.0 ? 0.0 : beta_y * y[i + stride]) + sign * a1;
+        y[i] = y0;
+        y[i + stride] = y1;
+        yy = fma(y1, y1, fma(y0, y0, yy));
     }
     for (; i < n; i += stride) {
         double a = 0.0;
 #pragma unroll 8
         for (int j = 0; j < nv; ++j) a = fma(cs[j], V[(int64_t)j * n + i], a);
-        y[i] = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a;
+        const double y0 = (beta_y == 0.0 ? 0.0 : beta_y * y[i]) + sign * a;
+        y[i] = y0;
+        yy = fma(y0, y0, yy);
+    }
+    if (sq) {                                        // block-uniform
+        yy = block_sum(yy, sh);
+        if (threadIdx.x == 0) sq[blockIdx.x] = yy;
     }
 }
 
@@ -174,12 +244,13 @@ __global__ void __launch_bounds__(RT) sumsq_kernel(const double* __restrict__ x,
 // dst = src / sqrt(sum part); mode 0: initial vector (sets active); mode 1: Lanczos step k
 __global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict__ part, int nb,
                                                        const double* __restrict__ src, double* __restrict__ dst,
-                                                       int64_t n, double* state, int mode, int k, int nmax) {
+                                                       int64_t n, double* state, int mode, int k, int nmax,
+                                                       int pstride = VT) {
     __shared__ double sh[RT / 32];
     __shared__ double nrm;
     if ((mode == 1 || mode == 3) && state[1] == 0.0) return;     // 3: plain, only while active
     double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * pstride];
     v = block_sum(v, sh);
     if (threadIdx.x == 0) nrm = sqrt(v);
     __syncthreads();
@@ -202,10 +273,25 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict_
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) dst[i] = src[i] * inv;
 }
 
-// alpha_k = h1[k] + h2[k], the projections of H v_k on v_k of both Gram-Schmidt passes
-__global__ void set_alpha_kernel(double* state, const double* h1, const double* h2, int k) {
+// After the first Gram-Schmidt pass of step k: whether the second runs (state[4]), i.e.
+// whether the pass left less than half of ||w||^2 (before: wn, nb1 partials; after: sq, nb2
+// partials).
+__global__ void lz_second_pass_kernel(double* state, const double* __restrict__ wn, int nb1,
+                                      const double* __restrict__ sq, int nb2) {
+    __shared__ double sh[RT / 32];
     if (state[1] == 0.0) return;
-    state[8 + k] = h1[k] + h2[k];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb1; i += blockDim.x) a += wn[i];
+    for (int i = threadIdx.x; i < nb2; i += blockDim.x) b += sq[i];
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) state[4] = (b < 0.5 * a) ? 1.0 : 0.0;
+}
+
+// alpha_k = a + h1[k] (+ h2[k] when the second pass ran): every projection of H v_k on v_k
+__global__ void set_alpha_kernel(double* state, const double* a, const double* h1, const double* h2, int k) {
+    if (state[1] == 0.0) return;
+    state[8 + k] = *a + h1[k] + (state[4] != 0.0 ? h2[k] : 0.0);
 }
 
 // Lowest eigenpair of the n_eff x n_eff tridiagonal matrix T (diagonal alpha, off-diagonal
@@ -459,6 +545,8 @@ Lz lz_view(const LzLayout& lay, void* lz_ws, int64_t n) {
     char* base = static_cast<char*>(lz_ws);
     return Lz{reinterpret_cast<double*>(base + lay.off_state), reinterpret_cast<double*>(base + lay.off_h),
               reinterpret_cast<double*>(base + lay.off_s), reinterpret_cast<double*>(base + lay.off_part),
+              reinterpret_cast<double*>(base + lay.off_wn), reinterpret_cast<double*>(base + lay.off_sq),
+              reinterpret_cast<double*>(base + lay.off_a),
               reinterpret_cast<double*>(base + lay.off_T), reinterpret_cast<double*>(base + lay.off_V), n,
               lay.nmax};
 }
@@ -480,23 +568,32 @@ int lanczos_core(heff_plan* plan, const double* x0, int32_t n_iter, double* x_ou
         double* vk = z.V + (int64_t)k * n;
         // w = H v_k (skipped work is harmless after breakdown: the result is not used)
         if ((rc = heff_apply_prepared(plan, vk, z.w(), apply_ws, apply_ws_bytes, stream))) return rc;
-        // two classical Gram-Schmidt passes: h1 -> z.h, h2 -> z.s
+        // three-term recurrence: a -> z.a, w -= beta_{k-1} v_{k-1} + a v_k
+        three_term_kernel<<<RB, RT, 0, st>>>(z.V, z.w(), n, k, z.nmax, z.part, z.wn, z.state, z.a, 0);
+        finish_dots_kernel<<<1, RT, 0, st>>>(z.part, RB, 0, 1, z.a, 0, z.state);
+        three_term_kernel<<<RB, RT, 0, st>>>(z.V, z.w(), n, k, z.nmax, z.part, z.wn, z.state, z.a, 1);
+        count_launches(3);
+        // classical Gram-Schmidt: h1 -> z.h, then (when needed) h2 -> z.s; each combine also
+        // leaves the partial sums of ||w||^2 in z.sq for the test and the normalisation
         for (int pass = 0; pass < 2; ++pass) {
             double* hp = pass == 0 ? z.h : z.s;
             for (int j0 = 0; j0 <= k; j0 += VT) {
                 const int nv = k + 1 - j0 < VT ? k + 1 - j0 : VT;
-                multidot_kernel<<<RB, RT, 0, st>>>(z.V, z.w(), n, j0, nv, z.part, z.state);
-                finish_dots_kernel<<<1, RT, 0, st>>>(z.part, RB, j0, nv, hp, 0, z.state);
+                multidot_kernel<<<RB, RT, 0, st>>>(z.V, z.w(), n, j0, nv, z.part, z.state, pass);
+                finish_dots_kernel<<<1, RT, 0, st>>>(z.part, RB, j0, nv, hp, 0, z.state, pass);
                 count_launches(2);
             }
-            combine_kernel<<<G, RT, 0, st>>>(z.V, n, k + 1, hp, -1.0, 1.0, z.w(), z.state, 0);
+            combine_kernel<<<G, RT, 0, st>>>(z.V, n, k + 1, hp, -1.0, 1.0, z.w(), z.state, 0, pass, z.sq);
             count_launches(1);
+            if (pass == 0) {
+                lz_second_pass_kernel<<<1, RT, 0, st>>>(z.state, z.wn, RB, z.sq, G);
+                count_launches(1);
+            }
         }
-        set_alpha_kernel<<<1, 1, 0, st>>>(z.state, z.h, z.s, k);
-        sumsq_kernel<<<RB, RT, 0, st>>>(z.w(), n, z.part);
-        normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, 1, k,
-                                           z.nmax);
-        count_launches(3);
+        set_alpha_kernel<<<1, 1, 0, st>>>(z.state, z.a, z.h, z.s, k);
+        normalize_kernel<<<GN, RT, 0, st>>>(z.sq, G, z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, 1, k,
+                                           z.nmax, 1);
+        count_launches(2);
     }
     tridiag_eig_kernel<<<1, 32, 0, st>>>(z.state, z.T, z.s, z.nmax);
     // x = V s (rows beyond n_eff have s = 0), then normalise
