@@ -38,10 +38,11 @@ constexpr int RB = 456;          // reduction blocks (partial sums per vector): 
 constexpr int VT = 8;            // vectors per multi-dot pass
 
 constexpr int GMAX = 4096;       // largest grid of the element-wise kernels (grid_for)
+constexpr int NVMAX = 128;       // basis vectors of one Lanczos workspace, at most
 
 // State in the Lanczos workspace (doubles): [0] n_eff (as double), [1] active flag,
 // [2] theta, [3] residual estimate, [4] second Gram-Schmidt pass needed (this step),
-// [8..8+NMAX) alpha, [8+NMAX..) beta, then h (NMAX), s (NMAX), partials (RB * VT), the
+// [8..8+NMAX) alpha, [8+NMAX..) beta, then h (NMAX), s (NMAX), partials (RB * NVMAX), the
 // partial sums of ||w||^2 after the three-term update (RB) and after a Gram-Schmidt pass
 // (GMAX), and a (the three-term projection of the current step).
 struct LzLayout {
@@ -59,7 +60,7 @@ LzLayout lz_layout(int64_t n, int n_iter) {
     l.off_state = o; o = al(o + sizeof(double) * (8 + 2 * (size_t)l.nmax));
     l.off_h = o;     o = al(o + sizeof(double) * (size_t)l.nmax);
     l.off_s = o;     o = al(o + sizeof(double) * (size_t)l.nmax);
-    l.off_part = o;  o = al(o + sizeof(double) * (size_t)RB * VT);
+    l.off_part = o;  o = al(o + sizeof(double) * (size_t)RB * NVMAX);
     l.off_wn = o;    o = al(o + sizeof(double) * (size_t)RB);
     l.off_sq = o;    o = al(o + sizeof(double) * (size_t)GMAX);
     l.off_a = o;     o = al(o + sizeof(double));
@@ -81,8 +82,6 @@ struct Lz {
     double* V;       // (nmax) basis vectors, then w
     int64_t n;
     int nmax;
-    double* alpha() const { return state + 8; }
-    double* beta() const { return state + 8 + nmax; }
     double* w() const { return V + (int64_t)nmax * n; }
 };
 
@@ -271,6 +270,84 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict_
     if (!(r > 0.0)) return;
     const double inv = 1.0 / r;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) dst[i] = src[i] * inv;
+}
+
+// All the projections of one Gram-Schmidt pass in one launch: block (b, g) computes the
+// dots of basis vectors g VT .. g VT + VT - 1 (those below nvec) with w over chunk b, into
+// part[j * gridDim.x + b]; vec_finish_kernel adds each vector's partials in a fixed order.
+__global__ void __launch_bounds__(RT) multidot_all_kernel(const double* __restrict__ V,
+                                                          const double* __restrict__ w, int64_t n, int nvec,
+                                                          double* __restrict__ part,
+                                                          const double* __restrict__ state, int gate) {
+    __shared__ double sh[RT / 32];
+    if (gated_off(state, gate)) return;
+    const int j0 = blockIdx.y * VT;
+    const int nv = nvec - j0 < VT ? nvec - j0 : VT;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t beg = (int64_t)blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+    double acc[VT];
+#pragma unroll
+    for (int t = 0; t < VT; ++t) acc[t] = 0.0;
+    int64_t i = beg + threadIdx.x;
+    for (; i + RT < end; i += 2 * RT) {
+        const double w0 = w[i], w1 = w[i + RT];
+        double v0[VT], v1[VT];
+#pragma unroll
+        for (int t = 0; t < VT; ++t) {
+            v0[t] = t < nv ? V[(int64_t)(j0 + t) * n + i] : 0.0;
+            v1[t] = t < nv ? V[(int64_t)(j0 + t) * n + i + RT] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < VT; ++t) acc[t] = fma(v1[t], w1, fma(v0[t], w0, acc[t]));
+    }
+    for (; i < end; i += RT) {
+        const double wi = w[i];
+#pragma unroll
+        for (int t = 0; t < VT; ++t)
+            if (t < nv) acc[t] = fma(V[(int64_t)(j0 + t) * n + i], wi, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < VT; ++t) {
+        if (t >= nv) break;                          // block-uniform
+        const double sum = block_sum(acc[t], sh);
+        if (threadIdx.x == 0) part[(int64_t)(j0 + t) * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+// out[j] = sum over b < nb of part[j * nb + b], one block per vector j
+__global__ void vec_finish_kernel(const double* __restrict__ part, int nb, double* __restrict__ out,
+                                  const double* __restrict__ state, int gate) {
+    __shared__ double sh[RT / 32];
+    if (gated_off(state, gate)) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(int64_t)blockIdx.x * nb + b];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+// beta_k = ||w|| from the nb partial sums of squares; records beta_k and n_eff = k + 1 and
+// ends the iteration when beta_k <= 1e-13 |alpha_k| (an invariant Krylov space)
+__global__ void lz_beta_kernel(const double* __restrict__ sq, int nb, double* state, int k, int nmax) {
+    __shared__ double sh[RT / 32];
+    if (state[1] == 0.0) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += sq[b];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        const double r = sqrt(v), a = state[8 + k];
+        state[8 + nmax + k] = r;
+        state[0] = (double)(k + 1);
+        if (!(r > 1e-13 * fabs(a)) || !(r > 1e-300)) state[1] = 0.0;
+    }
+}
+
+// v_{k+1} = w / beta_k while the iteration is active
+__global__ void __launch_bounds__(RT) lz_scale_kernel(const double* __restrict__ w, double* __restrict__ v,
+                                                      int64_t n, const double* __restrict__ state, int k,
+                                                      int nmax) {
+    if (state[1] == 0.0) return;
+    const double inv = 1.0 / state[8 + nmax + k];
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) v[i] = w[i] * inv;
 }
 
 // After the first Gram-Schmidt pass of step k: whether the second runs (state[4]), i.e.
@@ -577,23 +654,20 @@ int lanczos_core(heff_plan* plan, const double* x0, int32_t n_iter, double* x_ou
         // leaves the partial sums of ||w||^2 in z.sq for the test and the normalisation
         for (int pass = 0; pass < 2; ++pass) {
             double* hp = pass == 0 ? z.h : z.s;
-            for (int j0 = 0; j0 <= k; j0 += VT) {
-                const int nv = k + 1 - j0 < VT ? k + 1 - j0 : VT;
-                multidot_kernel<<<RB, RT, 0, st>>>(z.V, z.w(), n, j0, nv, z.part, z.state, pass);
-                finish_dots_kernel<<<1, RT, 0, st>>>(z.part, RB, j0, nv, hp, 0, z.state, pass);
-                count_launches(2);
-            }
+            multidot_all_kernel<<<dim3(RB, (k + VT) / VT), RT, 0, st>>>(z.V, z.w(), n, k + 1, z.part, z.state,
+                                                                         pass);
+            vec_finish_kernel<<<k + 1, RT, 0, st>>>(z.part, RB, hp, z.state, pass);
             combine_kernel<<<G, RT, 0, st>>>(z.V, n, k + 1, hp, -1.0, 1.0, z.w(), z.state, 0, pass, z.sq);
-            count_launches(1);
+            count_launches(3);
             if (pass == 0) {
                 lz_second_pass_kernel<<<1, RT, 0, st>>>(z.state, z.wn, RB, z.sq, G);
                 count_launches(1);
             }
         }
         set_alpha_kernel<<<1, 1, 0, st>>>(z.state, z.a, z.h, z.s, k);
-        normalize_kernel<<<GN, RT, 0, st>>>(z.sq, G, z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, 1, k,
-                                           z.nmax, 1);
-        count_launches(2);
+        lz_beta_kernel<<<1, RT, 0, st>>>(z.sq, G, z.state, k, z.nmax);
+        lz_scale_kernel<<<G, RT, 0, st>>>(z.w(), z.V + (int64_t)(k + 1) * n, n, z.state, k, z.nmax);
+        count_launches(3);
     }
     tridiag_eig_kernel<<<1, 32, 0, st>>>(z.state, z.T, z.s, z.nmax);
     // x = V s (rows beyond n_eff have s = 0), then normalise
