@@ -176,7 +176,10 @@ void heff_plan_destroy(heff_plan* plan);
  * buffers in their layouts, element type opts.io_dtype; y: device buffer in x's layout
  * (overwritten, must not alias x).  workspace: device, >= heff_plan_workspace_size
  * bytes, 256-byte aligned, not shared with another call in flight.  stream: cudaStream_t.
- * Runs heff_prepare then heff_apply_prepared.  Errors: INVALID_ARG, WORKSPACE, CUDA.
+ * Runs heff_prepare then heff_apply_prepared.  When x's layout has no allowed block (an
+ * empty two-site space) y has no elements: this and the other apply entries return HEFF_OK
+ * at once (x, y may then be NULL); the eigensolvers reject such a plan (INVALID_ARG).
+ * Errors: INVALID_ARG, WORKSPACE, CUDA.
  */
 int heff_apply(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream);

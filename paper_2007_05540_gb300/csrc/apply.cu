@@ -528,6 +528,7 @@ extern "C" int heff_prepare(heff_plan* plan, const void* L, const void* W1, cons
 extern "C" int heff_apply_prepared(heff_plan* plan, const void* x, void* y, void* workspace,
                                    size_t workspace_bytes, void* stream) {
     heff::clear_error();
+    if (plan && plan->nelem_x == 0) return HEFF_OK;            // an empty two-site space: y has no elements
     if (!plan || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_apply_prepared: null argument");
     if (x == y) return fail(HEFF_ERR_INVALID_ARG, "y must not alias x");
     int rc = check_ws(plan, workspace, workspace_bytes);
@@ -542,6 +543,7 @@ extern "C" int heff_apply_prepared(heff_plan* plan, const void* x, void* y, void
 extern "C" int heff_apply(heff_plan* plan, const void* L, const void* W1, const void* W2, const void* R,
                           const void* x, void* y, void* workspace, size_t workspace_bytes, void* stream) {
     heff::clear_error();
+    if (plan && plan->nelem_x == 0) return HEFF_OK;            // an empty two-site space: y has no elements
     if (!plan || !L || !W1 || !W2 || !R || !x || !y) return fail(HEFF_ERR_INVALID_ARG, "heff_apply: null argument");
     if (x == y) return fail(HEFF_ERR_INVALID_ARG, "y must not alias x");
     int rc = check_ws(plan, workspace, workspace_bytes);
@@ -583,6 +585,7 @@ extern "C" int heff_apply_host(heff_plan* plan, const void* L, const void* W1, c
                                const void* x, void* y, void* staging, size_t staging_bytes, void* workspace,
                                size_t workspace_bytes, void* stream) {
     heff::clear_error();
+    if (plan && plan->nelem_x == 0) return HEFF_OK;            // an empty two-site space: y has no elements
     if (!plan || !L || !W1 || !W2 || !R || !x || !y || !staging)
         return fail(HEFF_ERR_INVALID_ARG, "heff_apply_host: null argument");
     const Staging sl = staging_layout(plan);
@@ -609,6 +612,7 @@ extern "C" int heff_apply_batched(heff_plan* plan, const void* L, const void* W1
         return fail(HEFF_ERR_INVALID_ARG, "heff_apply_batched: null argument");
     if (nbatch < 1 || nbatch > plan->opts.max_batch)
         return fail(HEFF_ERR_INVALID_ARG, "nbatch %d outside 1..max_batch (%d)", nbatch, plan->opts.max_batch);
+    if (plan->nelem_x == 0) return HEFF_OK;                   // an empty two-site space: no y has elements
     for (int b = 0; b < nbatch; ++b) {
         if (!x[b] || !y[b]) return fail(HEFF_ERR_INVALID_ARG, "null x or y at batch entry %d", b);
         if (x[b] == y[b]) return fail(HEFF_ERR_INVALID_ARG, "y must not alias x (batch entry %d)", b);

@@ -188,15 +188,18 @@ __global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int 
 }
 
 // y[i] = (beta_y * y[i]) + sign * sum_{j < nv} c[j] V[j][i]   (c from device memory); with
-// sq, also sq[b] = block b's sum of the new y[i]^2
+// sq, also sq[b] = block b's sum of the new y[i]^2.  With clamp, only the first state[0]
+// rows (the Krylov dimension reached) enter: rows never written after a breakdown are not
+// read.
 __global__ void __launch_bounds__(RT) combine_kernel(const double* __restrict__ V, int64_t n, int nv,
                                                      const double* __restrict__ c, double sign, double beta_y,
                                                      double* __restrict__ y, const double* __restrict__ state,
                                                      int ignore_active, int gate = 0,
-                                                     double* __restrict__ sq = nullptr) {
+                                                     double* __restrict__ sq = nullptr, int clamp = 0) {
     __shared__ double cs[128];
     __shared__ double sh[RT / 32];
     if (!ignore_active && gated_off(state, gate)) return;
+    if (clamp) nv = min(nv, (int)state[0]);
     for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = c[j];
     __syncthreads();
     // two elements per iteration (their loads in flight together), then the remainder
@@ -386,7 +389,10 @@ __global__ void tridiag_eig_kernel(double* state, double* T, double* s, int nmax
     const int n = (int)state[0];
     for (int i = lane; i < nmax; i += 32) s[i] = 0.0;
     __syncwarp();                        // lane 0 writes s below: the zeros land first
-    if (n <= 0) return;
+    if (n <= 0) {                        // a zero start vector: no Krylov space
+        if (lane == 0) { state[2] = 0.0; state[3] = 0.0; }
+        return;
+    }
     const double* al = state + 8;
     const double* be = state + 8 + nmax;
     double lo = al[0], hi = al[0];
@@ -671,7 +677,7 @@ int lanczos_core(heff_plan* plan, const double* x0, int32_t n_iter, double* x_ou
     }
     tridiag_eig_kernel<<<1, 32, 0, st>>>(z.state, z.T, z.s, z.nmax);
     // x = V s (rows beyond n_eff have s = 0), then normalise
-    combine_kernel<<<G, RT, 0, st>>>(z.V, n, z.nmax, z.s, 1.0, 0.0, x_out, z.state, 1);
+    combine_kernel<<<G, RT, 0, st>>>(z.V, n, z.nmax, z.s, 1.0, 0.0, x_out, z.state, 1, 0, nullptr, 1);
     sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, z.part);
     normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x_out, x_out, n, z.state, 2, 0, z.nmax);
     count_launches(4);
@@ -697,6 +703,7 @@ extern "C" int heff_lanczos(heff_plan* plan, const void* L, const void* W1, cons
     if (plan->opts.io_dtype != HEFF_DTYPE_F64)
         return fail(HEFF_ERR_UNSUPPORTED, "heff_lanczos needs a plan with HEFF_DTYPE_F64 tensors");
     if (n_iter < 1 || n_iter > 126) return fail(HEFF_ERR_INVALID_ARG, "n_iter must be 1..126");
+    if (plan->nelem_x == 0) return fail(HEFF_ERR_INVALID_ARG, "heff_lanczos: the two-site space is empty");
     const LzLayout lay = lz_layout(plan->nelem_x, n_iter);
     if (lz_ws_bytes < lay.bytes || reinterpret_cast<uintptr_t>(lz_ws) % 256)
         return fail(HEFF_ERR_WORKSPACE, "Lanczos workspace of %zu bytes, needs %zu (256-byte aligned)",
@@ -768,6 +775,7 @@ extern "C" int heff_ground_state(heff_plan* plan, heff_plan* plan64, const void*
         return fail(HEFF_ERR_UNSUPPORTED, "heff_ground_state needs a plan with HEFF_DTYPE_F64 tensors");
     if (n_iter < 1 || n_iter > 126 || max_cycles < 1 || !(tol >= 0.0))
         return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state: n_iter 1..126, max_cycles >= 1, tol >= 0");
+    if (plan->nelem_x == 0) return fail(HEFF_ERR_INVALID_ARG, "heff_ground_state: the two-site space is empty");
     // the FP64 Rayleigh quotient: plan64, or the plan itself when it is the FP64 path
     heff_plan* p64 = plan64 ? plan64 : (plan->opts.precision == HEFF_PREC_FP64 ? plan : nullptr);
     void* ws64 = plan64 ? apply_ws64 : apply_ws;
@@ -882,6 +890,7 @@ extern "C" int heff_davidson(heff_plan* plan, const void* L, const void* W1, con
     if (plan->opts.io_dtype != HEFF_DTYPE_F64)
         return fail(HEFF_ERR_UNSUPPORTED, "heff_davidson needs a plan with HEFF_DTYPE_F64 tensors");
     if (max_vecs < 1 || max_vecs > 64) return fail(HEFF_ERR_INVALID_ARG, "max_vecs must be 1..64");
+    if (plan->nelem_x == 0) return fail(HEFF_ERR_INVALID_ARG, "heff_davidson: the two-site space is empty");
     if (!(tol >= 0.0)) return fail(HEFF_ERR_INVALID_ARG, "tol must be >= 0");
     const DavLayout lay = dav_layout(plan->nelem_x, max_vecs);
     if (dav_ws_bytes < lay.bytes || reinterpret_cast<uintptr_t>(dav_ws) % 256)

@@ -852,6 +852,7 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
 int launch_tc_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const GemmList& gl = which == 1 ? p->g1 : p->g2;
+    if (gl.tasks.empty()) return HEFF_OK;         // nothing to contract (no tensor maps needed)
     const bool wide = gl.tn == 256, pair = gl.cl == 2;
     if (p->opts.precision == HEFF_PREC_BF16X3)
         return pair ? launch_tc_t<HEFF_PREC_BF16X3, 256, 2>(p, which, ws, y, nbatch, st)

@@ -137,6 +137,16 @@ def test_restart_from_converged_vector_breaks_down_cleanly():
     assert ov > 1 - 1e-10, ov
 
 
+def test_zero_start_vector_gives_empty_krylov_space():
+    """A zero start vector spans nothing: Krylov dimension 0, theta and the residual
+    estimate 0, a zero output vector, all finite (nothing reads past the empty basis)."""
+    p = LzProblem("spin_m24")
+    p.x0 = torch.zeros_like(p.x0)
+    res, x = p.lanczos("fp64", 10)
+    assert res[2] == 0 and res[0] == 0.0 and res[1] == 0.0
+    assert torch.count_nonzero(x) == 0
+
+
 # ---------------------------------------------------------------- Davidson (Algorithm 1)
 def _davidson(p, prec, max_vecs, tol, x0=None, seed=7):
     P = p.plan(prec)

@@ -186,3 +186,34 @@ def test_full_size_sampled_sectors(name, sectors, prec):
             mask[off:off + size] = True
     assert not np.isnan(y).any()
     _check(y, y_ref, TOL[prec], mask)
+
+
+def test_empty_two_site_space():
+    """A target charge no x block satisfies: the plan has no work, every apply entry is a
+    no-op that returns success (also with NULL x and y), and the eigensolvers refuse it."""
+    w = wl.workload_by_name("spin_m24")
+    lays = heff.heff_layouts((w.alpha_q, w.alpha_d), (w.beta_q, w.beta_d), w.phys, w.ql, w.qm, w.qr,
+                             target=np.array([1001], dtype=np.int32))
+    assert lays[4].nelem == 0 and lays[0].nelem > 0
+    W1 = lays[1].assemble(lambda k: w.W1[k])
+    W2 = lays[2].assemble(lambda k: w.W2[k])
+    L = torch.from_numpy(lays[0].assemble(lambda k: w.L_block((k[0], k[1], k[2])))).cuda()
+    R = torch.from_numpy(lays[3].assemble(lambda k: w.R_block((k[0], k[1], k[2])))).cuda()
+    d1, d2 = torch.from_numpy(W1).cuda(), torch.from_numpy(W2).cuda()
+    x = torch.empty(0, dtype=torch.float64, device="cuda")
+    y = torch.empty(0, dtype=torch.float64, device="cuda")
+    for prec in ("fp64", "bf16x3"):
+        io = torch.float64 if prec == "fp64" else torch.float32
+        P = heff.Plan(*lays, W1, W2, prec, "f64" if prec == "fp64" else "f32")
+        assert P.flops_canonical == 0.0
+        ws = P.workspace()
+        args = [t.to(io) for t in (L, d1, d2, R)]
+        heff.heff_apply(P.handle, *args, x.to(io), y.to(io), ws)
+        heff.heff_apply_batched(P.handle, *args, [x.to(io)], [y.to(io)], ws)
+        torch.cuda.synchronize()
+    P = heff.Plan(*lays, W1, W2, "fp64", "f64")
+    lz = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_lanczos(P.handle, L, d1, d2, R, x, 1, y, res, P.workspace(), lz)
+    assert e.value.code == -1

@@ -354,3 +354,18 @@ def test_ground_state_and_block_status_entries_check_arguments():
     assert heff.heff_grad_status(g, small, st) == -7                      # too small
     assert heff.heff_grad_status(None, small, st) == -1
     heff.heff_grad_plan_destroy(g)
+
+
+def test_empty_two_site_space_plan():
+    """A target charge that no x block satisfies: an empty layout, and a plan with no work."""
+    w = wl.workload_by_name("spin_m24")
+    lays = heff.heff_layouts((w.alpha_q, w.alpha_d), (w.beta_q, w.beta_d), w.phys, w.ql, w.qm, w.qr,
+                             target=np.array([1001], dtype=np.int32))
+    assert lays[4].nblocks == 0 and lays[4].nelem == 0
+    W1 = lays[1].assemble(lambda k: w.W1[k])
+    W2 = lays[2].assemble(lambda k: w.W2[k])
+    for prec, io in (("fp64", "f64"), ("bf16x3", "f32"), ("tf32x3", "f32")):
+        P = heff.Plan(*lays, W1, W2, prec, io)
+        assert P.flops_canonical == 0.0
+        st = P.stats
+        assert st[3] == 0 and st[4] == 0 and st[5] == 0      # no GEMM tasks, no pack tiles
