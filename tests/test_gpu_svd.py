@@ -91,3 +91,49 @@ def test_svd_split_matches_oracle(name, m_max, cutoff, absorb_right):
             assert np.abs(G - np.eye(d[c])).max() < 1e-10
     finally:
         heff.heff_svd_destroy(s)
+
+
+def _gpu_svd(x_l, xflat, m_max, cutoff, nq):
+    s = heff.heff_svd_create(x_l.handle)
+    try:
+        ws = torch.empty(heff.heff_svd_workspace_size(s), dtype=torch.uint8, device="cuda")
+        heff.heff_svd_compute(s, torch.from_numpy(xflat).to("cuda", torch.float64), ws)
+        q, d, disc, nrm = heff.heff_svd_truncate(s, m_max, cutoff, nq, 4096)
+        sv = heff.heff_svd_singular_values(s, max(1, int(d.sum())))[:int(d.sum())]
+        return q, d, disc, nrm, sv
+    finally:
+        heff.heff_svd_destroy(s)
+
+
+def test_svd_of_rank_one_tensor():
+    """Degenerate input: the oracle's rank-1 truncation of a two-site tensor (one singular
+    triplet in one charge sector, every other sector exactly zero).  The GPU keeps exactly
+    that triplet at the cutoff 1e-12: the same bond, singular value and norm."""
+    w = wl.workload_by_name("spin_m200")
+    lays, bufs = library_problem(w)
+    x_l = lays[4]
+    L, W1, W2, R, xo = oh.problem_from_workload(w)
+    A1, B1, s1, _ = osvd.svd_split(xo, 1, 0.0, "right")
+    x1 = omps.two_site(A1, B1)
+    xflat = x_l.assemble(lambda k: x1.blocks[k])
+    A_o, B_o, s_o, disc_o = osvd.svd_split(x1, 64, 1e-12, "right")
+    q, d, disc, nrm, sv = _gpu_svd(x_l, xflat, 64, 1e-12, w.nq)
+    assert int(d.sum()) == 1 and len(s_o) == 1
+    assert np.array_equal(q, A_o.indices[2].charges) and np.array_equal(d, A_o.indices[2].dims)
+    assert abs(nrm - x1.norm()) < 1e-12 * x1.norm()
+    assert abs(sv[0] / nrm - s_o[0] / x1.norm()) < 1e-12
+    assert disc < 1e-24
+
+
+def test_svd_of_zero_tensor():
+    """All-zero input: no singular value reaches any positive cutoff (an empty bond, nothing
+    discarded, norm 0, nothing NaN); with cutoff 0 every zero singular value up to m_max is
+    kept."""
+    w = wl.workload_by_name("spin_m64")
+    lays, _ = library_problem(w)
+    x_l = lays[4]
+    xflat = np.zeros(x_l.nelem)
+    q, d, disc, nrm, sv = _gpu_svd(x_l, xflat, 16, 1e-12, w.nq)
+    assert len(d) == 0 and nrm == 0.0 and disc == 0.0
+    q, d, disc, nrm, sv = _gpu_svd(x_l, xflat, 16, 0.0, w.nq)
+    assert int(d.sum()) == 16 and np.all(sv == 0.0) and disc == 0.0
