@@ -357,7 +357,8 @@ void heff_two_site_destroy(heff_two_site* plan);
  * Gradients of the Rayleigh quotient rho = <x|K|x> / <x|x> of the effective Hamiltonian
  * K (Section II-C): rho is linear in L, R, W1 and W2, so each gradient is the closed-form
  * contraction of the bra x, the ket x and the other three operators; d rho/dx =
- * 2 (K x - rho x) / <x|x>.  heff_grad_plan_create builds the block-product schedule for
+ * 2 (K x - rho x) / <x|x>; rho is undefined at x = 0, where every result is NaN (the
+ * call does not synchronise to test for it).  heff_grad_plan_create builds the block-product schedule for
  * the five layouts (host MPO copies drop exactly-zero entries from the W1.W2 pattern; the
  * W gradients are computed for every allowed entry).  heff_backward computes y = K x with
  * `plan` (any precision; HEFF_DTYPE_F64 tensors) and the rest in FP64:
