@@ -106,9 +106,9 @@ __device__ __forceinline__ bool gated_off(const double* state, int gate) {
 // partial[b * VT + t] = sum over block b's chunk of V[j0 + t] . w, t < nv
 __global__ void __launch_bounds__(RT) multidot_kernel(const double* __restrict__ V, const double* __restrict__ w,
                                                       int64_t n, int j0, int nv, double* __restrict__ part,
-                                                      const double* __restrict__ state, int gate = 0) {
+                                                      const double* __restrict__ state) {
     __shared__ double sh[RT / 32];
-    if (gated_off(state, gate)) return;
+    if (state[1] == 0.0) return;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t beg = (int64_t)blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
     double acc[VT];
@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(RT) three_term_kernel(const double* __restrict
 
 // out[j0 + t] = (accumulate ? out : 0) + sum_b partial[b * VT + t]
 __global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int j0, int nv, double* out,
-                                   int accumulate, const double* __restrict__ state, int gate = 0) {
+                                   int accumulate, const double* __restrict__ state) {
     __shared__ double sh[RT / 32];
-    if (gated_off(state, gate)) return;
+    if (state[1] == 0.0) return;
     for (int t = 0; t < nv; ++t) {
         double v = 0.0;
         for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT + t];
@@ -243,30 +243,21 @@ __global__ void __launch_bounds__(RT) sumsq_kernel(const double* __restrict__ x,
     if (threadIdx.x == 0) part[blockIdx.x * VT] = a;
 }
 
-// dst = src / sqrt(sum part); mode 0: initial vector (sets active); mode 1: Lanczos step k
+// dst = src / sqrt(sum part); mode 0: initial vector (sets active and n_eff = 0); mode 2:
+// plain; mode 3: plain, only while active
 __global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict__ part, int nb,
                                                        const double* __restrict__ src, double* __restrict__ dst,
-                                                       int64_t n, double* state, int mode, int k, int nmax,
-                                                       int pstride = VT) {
+                                                       int64_t n, double* state, int mode) {
     __shared__ double sh[RT / 32];
     __shared__ double nrm;
-    if ((mode == 1 || mode == 3) && state[1] == 0.0) return;     // 3: plain, only while active
+    if (mode == 3 && state[1] == 0.0) return;
     double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * pstride];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b * VT];
     v = block_sum(v, sh);
     if (threadIdx.x == 0) nrm = sqrt(v);
     __syncthreads();
     const double r = nrm;
-    if (mode == 1) {
-        // alpha_k was accumulated in h[k]; beta_k = ||w||
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            const double a = state[8 + k];
-            state[8 + nmax + k] = r;
-            state[0] = (double)(k + 1);
-            if (!(r > 1e-13 * fabs(a)) || !(r > 1e-300)) state[1] = 0.0;    // invariant subspace
-        }
-        if (!(r > 1e-13 * fabs(state[8 + k])) || !(r > 1e-300)) return;
-    } else if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
         state[0] = 0.0;
         state[1] = r > 0.0 ? 1.0 : 0.0;
     }
@@ -645,7 +636,7 @@ int lanczos_core(heff_plan* plan, const double* x0, int32_t n_iter, double* x_ou
     int rc;
     // v_0 = x0 / ||x0||
     sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, z.part);
-    normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x0, z.V, n, z.state, 0, 0, z.nmax);
+    normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x0, z.V, n, z.state, 0);
     count_launches(2);
     for (int k = 0; k < n_iter; ++k) {
         double* vk = z.V + (int64_t)k * n;
@@ -679,7 +670,7 @@ int lanczos_core(heff_plan* plan, const double* x0, int32_t n_iter, double* x_ou
     // x = V s (rows beyond n_eff have s = 0), then normalise
     combine_kernel<<<G, RT, 0, st>>>(z.V, n, z.nmax, z.s, 1.0, 0.0, x_out, z.state, 1, 0, nullptr, 1);
     sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, z.part);
-    normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x_out, x_out, n, z.state, 2, 0, z.nmax);
+    normalize_kernel<<<GN, RT, 0, st>>>(z.part, RB, x_out, x_out, n, z.state, 2);
     count_launches(4);
     // result: [theta, residual estimate, n_eff, alpha..., beta...]
     cudaMemcpyAsync(result, z.state + 2, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st);
@@ -915,7 +906,7 @@ extern "C" int heff_davidson(heff_plan* plan, const void* L, const void* W1, con
     dav_init_state_kernel<<<1, 32, 0, st>>>(state, tol);
     // v_0 = x0 / ||x0|| (sets active when x0 != 0), v^A_0 = A v_0
     sumsq_kernel<<<RB, RT, 0, st>>>(x0, n, part);
-    normalize_kernel<<<GN, RT, 0, st>>>(part, RB, x0, V, n, state, 0, 0, max_vecs);
+    normalize_kernel<<<GN, RT, 0, st>>>(part, RB, x0, V, n, state, 0);
     count_launches(3);
     if ((rc = heff_apply_prepared(plan, V, VA, apply_ws, apply_ws_bytes, stream))) return rc;
     auto gram_schmidt = [&](int nv) {          // q -= V (V^T q) over v_0 .. v_{nv-1}
@@ -958,13 +949,13 @@ extern "C" int heff_davidson(heff_plan* plan, const void* L, const void* W1, con
         gram_schmidt(i + 1);
         double* vn = V + (int64_t)(i + 1) * n;
         sumsq_kernel<<<RB, RT, 0, st>>>(q, n, part);
-        normalize_kernel<<<GN, RT, 0, st>>>(part, RB, q, vn, n, state, 3, 0, max_vecs);
+        normalize_kernel<<<GN, RT, 0, st>>>(part, RB, q, vn, n, state, 3);
         count_launches(2);
         if ((rc = heff_apply_prepared(plan, vn, VA + (int64_t)(i + 1) * n, apply_ws, apply_ws_bytes, stream)))
             return rc;
     }
     sumsq_kernel<<<RB, RT, 0, st>>>(x_out, n, part);
-    normalize_kernel<<<GN, RT, 0, st>>>(part, RB, x_out, x_out, n, state, 2, 0, max_vecs);
+    normalize_kernel<<<GN, RT, 0, st>>>(part, RB, x_out, x_out, n, state, 2);
     count_launches(2);
     // result: [lambda, ||q||, vectors used]
     cudaMemcpyAsync(result, state + 2, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st);
