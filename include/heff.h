@@ -116,7 +116,8 @@ void heff_layout_destroy(heff_layout* lay);
  * task lists, workspace layout and flop counts) and upload the schedule tables to the
  * current CUDA device.  W1_host / W2_host: host copies of the MPO tensors in their
  * layouts (double); an entry equal to 0.0 is dropped from the schedule, so later calls
- * must pass device MPO tensors that are zero there too.  Synchronises once (table
+ * must pass device MPO tensors that are zero there too (heff_plan_check_mpo counts the
+ * entries that are not).  Synchronises once (table
  * upload).  Errors: INVALID_ARG, CHARGE_MISMATCH, UNSUPPORTED, OOM, CUDA.
  *
  * Row shards (one apply spread over S GPUs): every y block belongs to the left sector
@@ -132,6 +133,18 @@ void heff_layout_destroy(heff_layout* lay);
 int heff_plan_create(const heff_layout* L, const heff_layout* W1, const heff_layout* W2,
                      const heff_layout* R, const heff_layout* x, const double* W1_host,
                      const double* W2_host, const heff_plan_opts* opts, heff_plan** out);
+
+/*
+ * heff_plan_check_mpo -- the plan keeps only the MPO entries that were nonzero in the host
+ * copies given to heff_plan_create; an apply ignores the others.  This counts the entries
+ * of the device tensors W1, W2 (layouts of the plan, element type opts.io_dtype) that are
+ * nonzero at those dropped positions into *violations (host): 0 means the tensors fit the
+ * plan.  Not called by the apply entries (it would cost a device pass and a host
+ * synchronisation per call).  Synchronises `stream`; not for concurrent use on one plan
+ * (one device counter).  Errors: INVALID_ARG, UNSUPPORTED (plan without a device), CUDA.
+ */
+int heff_plan_check_mpo(const heff_plan* plan, const void* W1, const void* W2, void* stream,
+                        int64_t* violations);
 
 /* Left sectors a' (indices into x's first index) whose y blocks this plan computes, in
  * increasing order; sectors may be NULL to query the count. */

@@ -340,6 +340,9 @@ int plan_upload(heff_plan* p) {
         if ((rc = upload(g->tasks, &g->d_tasks)) != HEFF_OK) return rc;
         if ((rc = upload(g->segs, &g->d_segs)) != HEFF_OK) return rc;
     }
+    if ((rc = upload(p->w1_zero, &p->d_w1_zero)) != HEFF_OK) return rc;
+    if ((rc = upload(p->w2_zero, &p->d_w2_zero)) != HEFF_OK) return rc;
+    CK(cudaMalloc((void**)&p->d_wcount, sizeof(unsigned long long)));
     p->uploaded = true;
     return HEFF_OK;
 }
@@ -352,6 +355,9 @@ void plan_free_device(heff_plan* p) {
     for (int k = 0; k < 5; ++k)
         if (p->ev[k]) { cudaEventDestroy(static_cast<cudaEvent_t>(p->ev[k])); p->ev[k] = nullptr; }
     cudaFree(p->d_pack); cudaFree(p->d_mix); cudaFree(p->d_terms);
+    cudaFree(p->d_w1_zero); cudaFree(p->d_w2_zero); cudaFree(p->d_wcount);
+    p->d_w1_zero = p->d_w2_zero = nullptr;
+    p->d_wcount = nullptr;
     cudaFree(p->g1.d_tasks); cudaFree(p->g1.d_segs); cudaFree(p->g2.d_tasks); cudaFree(p->g2.d_segs);
     for (GemmList* g : {&p->g1_alt, &p->g2_alt, &p->g1_pair, &p->g2_pair}) {
         cudaFree(g->d_tasks); cudaFree(g->d_segs);
@@ -472,6 +478,18 @@ int launch_gemm(heff_plan* p, int which, void* ws, void* const* y, int nbatch, v
 }
 
 }  // namespace heff
+
+// ------------------------------------------------------------------ MPO check
+// *count += the entries W[idx[i]], i < n, that are not zero
+template <typename T>
+__global__ void __launch_bounds__(256) mpo_nonzero_at_kernel(const T* __restrict__ W, const int32_t* __restrict__ idx,
+                                                             int n, unsigned long long* count) {
+    unsigned long long c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        c += W[idx[i]] != (T)0 ? 1ull : 0ull;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
 
 // ------------------------------------------------------------------ C ABI
 static int check_ws(const heff_plan* p, void* ws, size_t bytes) {
@@ -742,5 +760,33 @@ extern "C" int heff_plan_timings(heff_plan* plan, float* ms) {
     CK(cudaEventElapsedTime(&ms[1], e[1], e[2]));
     CK(cudaEventElapsedTime(&ms[2], e[2], e[3]));
     CK(cudaEventElapsedTime(&ms[3], e[3], e[4]));
+    return HEFF_OK;
+}
+
+extern "C" int heff_plan_check_mpo(const heff_plan* plan, const void* W1, const void* W2, void* stream,
+                                   int64_t* violations) {
+    heff::clear_error();
+    if (!plan || !W1 || !W2 || !violations) return fail(HEFF_ERR_INVALID_ARG, "heff_plan_check_mpo: null argument");
+    if (!plan->uploaded) return fail(HEFF_ERR_UNSUPPORTED, "plan was created without a CUDA device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(plan->d_wcount, 0, sizeof(unsigned long long), st));
+    const bool f64 = plan->opts.io_dtype == HEFF_DTYPE_F64;
+    const struct { const void* W; const int32_t* idx; size_t n; } parts[2] = {
+        {W1, plan->d_w1_zero, plan->w1_zero.size()}, {W2, plan->d_w2_zero, plan->w2_zero.size()}};
+    for (const auto& pt : parts) {
+        if (pt.n == 0) continue;
+        const int grid = (int)std::min<size_t>((pt.n + 255) / 256, 1024);
+        if (f64)
+            mpo_nonzero_at_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(pt.W), pt.idx,
+                                                                 (int)pt.n, plan->d_wcount);
+        else
+            mpo_nonzero_at_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(pt.W), pt.idx,
+                                                                (int)pt.n, plan->d_wcount);
+        heff::count_launches(1);
+    }
+    unsigned long long c = 0;
+    CK(cudaMemcpyAsync(&c, plan->d_wcount, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *violations = (int64_t)c;
     return HEFF_OK;
 }

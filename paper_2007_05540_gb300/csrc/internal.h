@@ -195,6 +195,11 @@ struct heff_plan {
     heff::PackTile* d_pack = nullptr;
     heff::MixTile* d_mix = nullptr;
     heff::MixTerm* d_terms = nullptr;
+    // MPO entries the schedule dropped (exactly zero in the host copies), for heff_plan_check_mpo
+    std::vector<int32_t> w1_zero, w2_zero;
+    int32_t* d_w1_zero = nullptr;
+    int32_t* d_w2_zero = nullptr;
+    unsigned long long* d_wcount = nullptr;
     heff::GemmList g1, g2;            // active task lists
     heff::GemmList g1_alt, g2_alt;    // the other tile width (tensor-core paths), see heff_plan_autotune
     heff::GemmList g1_pair, g2_pair;  // N = 256 tiles in CTA pairs sharing B (tensor-core paths)

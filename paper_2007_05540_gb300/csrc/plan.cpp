@@ -142,6 +142,8 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
     }
     P->nelem_x = x->nelem; P->nelem_L = L->nelem; P->nelem_R = R->nelem;
     P->nelem_W1 = W1->nelem; P->nelem_W2 = W2->nelem;
+    for (int64_t e = 0; e < W1->nelem; ++e) if (W1_host[e] == 0.0) P->w1_zero.push_back((int32_t)e);
+    for (int64_t e = 0; e < W2->nelem; ++e) if (W2_host[e] == 0.0) P->w2_zero.push_back((int32_t)e);
 
     try {
         const int na = alpha.nsec, nb = beta.nsec, d1 = ph1.nsec, d2 = ph2.nsec;

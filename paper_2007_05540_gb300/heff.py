@@ -104,6 +104,7 @@ _sig = {
     "heff_lanczos": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
     "heff_plan_autotune": (C.c_int, [_vp] * 8 + [_sz, _vp, _P(_i32), _P(C.c_float)]),
     "heff_plan_set_timing": (C.c_int, [_vp, _i32]),
+    "heff_plan_check_mpo": (C.c_int, [_vp, _vp, _vp, _vp, _P(_i64)]),
     "heff_plan_timings": (C.c_int, [_vp, _P(C.c_float)]),
     "heff_workspace_status": (C.c_int, [_vp, _vp, _sz, _vp]),
     "heff_wait_selftest": (C.c_int, [_vp, _vp, _sz, _i32, _vp, _P(C.c_float)]),
@@ -527,6 +528,14 @@ def heff_plan_autotune(plan, L, W1, W2, R, x, y, ws, stream=None, times=None):
 
 def heff_plan_set_timing(plan, enable=True):
     _check(_lib.heff_plan_set_timing(plan, 1 if enable else 0), "heff_plan_set_timing")
+
+
+def heff_plan_check_mpo(plan, W1, W2, stream=None):
+    """Entries of the device MPO tensors that are nonzero where the plan's host copies were
+    zero (0: the tensors fit the plan)."""
+    v = _i64()
+    _check(_lib.heff_plan_check_mpo(plan, _ptr(W1), _ptr(W2), _stream(stream), C.byref(v)), "heff_plan_check_mpo")
+    return int(v.value)
 
 
 def heff_plan_timings(plan):

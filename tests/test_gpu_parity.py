@@ -217,3 +217,22 @@ def test_empty_two_site_space():
     with pytest.raises(heff.HeffError) as e:
         heff.heff_lanczos(P.handle, L, d1, d2, R, x, 1, y, res, P.workspace(), lz)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_check_mpo_counts_entries_the_plan_dropped(prec):
+    """The device MPO tensors the plan was made from fit it (0); a value placed where the host
+    copy was zero (an entry the schedule dropped, which the apply would ignore) is counted,
+    in W1 and in W2."""
+    w = wl.workload_by_name("spin_m64")
+    lib = Lib(w, prec)
+    assert heff.heff_plan_check_mpo(lib.plan.handle, lib.W1, lib.W2) == 0
+    z1 = np.flatnonzero(np.asarray(lib.bufs["W1"]) == 0.0)
+    z2 = np.flatnonzero(np.asarray(lib.bufs["W2"]) == 0.0)
+    assert len(z1) > 0 and len(z2) > 0
+    W1, W2 = lib.W1.clone(), lib.W2.clone()
+    W1[int(z1[0])] = 0.5
+    assert heff.heff_plan_check_mpo(lib.plan.handle, W1, W2) == 1
+    W2[int(z2[-1])] = -2.0
+    W2[int(z2[0])] = 1e-30
+    assert heff.heff_plan_check_mpo(lib.plan.handle, W1, W2) == 3

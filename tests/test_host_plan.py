@@ -369,3 +369,23 @@ def test_empty_two_site_space_plan():
         assert P.flops_canonical == 0.0
         st = P.stats
         assert st[3] == 0 and st[4] == 0 and st[5] == 0      # no GEMM tasks, no pack tiles
+
+
+def test_check_mpo_arguments():
+    """heff_plan_check_mpo rejects null tensors on the host and needs a plan with a device."""
+    import types
+
+    import torch
+    w = wl.workload_by_name("spin_m24")
+    lays, bufs = library_problem(w)
+    P = _plan(w, lays, bufs, "fp64", "f64")
+    assert len(np.flatnonzero(bufs["W1"] == 0.0)) > 0          # the schedule drops entries
+    t = torch.zeros(8, dtype=torch.float64)                     # host memory, never dereferenced
+    st = types.SimpleNamespace(cuda_stream=0)
+    with pytest.raises(heff.HeffError) as e:
+        heff.heff_plan_check_mpo(P.handle, None, t, st)
+    assert e.value.code == -1
+    if not torch.cuda.is_available():                           # a host-only plan
+        with pytest.raises(heff.HeffError) as e:
+            heff.heff_plan_check_mpo(P.handle, t, t, st)
+        assert e.value.code == -3
