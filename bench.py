@@ -85,7 +85,7 @@ def parse():
                     help="keep the planner's default tile widths (for profiling: serialised launches under a "
                          "profiler would time the candidates differently)")
     ap.add_argument("--part", default="",
-                    choices=["", "lanczos", "svd", "env_update", "backward", "energy", "batched"],
+                    choices=["", "lanczos", "svd", "env_update", "backward", "energy", "batched", "dmrg"],
                     help="time one step of the DMRG bond update alone and print its own JSON line "
                          "(the profiling cases): the FP64 Lanczos eigensolver (30 iterations, BF16x3 "
                          "matvecs), the block SVD truncation, the environment update, the gradients")
@@ -440,6 +440,8 @@ def extras(args, w, lays, bufs, dev, stream, flush, value):
     for name in ("electron_m2048", "electron_hubbard_4x8_m2048", "electron_tri_xc6_m2048", "electron_tri_xc6c_m2048",
                  "electron_tri_xc6ci_m2048"):
         out[name + "_batch32_graph"] = batched_graph(name, 32, dev, stream, flush)
+    # the GPU two-site DMRG driver: full sweeps of the 6x6 J1-J2 cylinder, bond caps 16 .. 1024
+    out["dmrg_6x6_sweeps"] = dmrg_sweep_timing()
     return out
 
 
@@ -640,9 +642,40 @@ def run_part(args):
     elif args.part == "batched":
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         out = batched_graph(args.workload, 32, dev, stream, flush)
+    elif args.part == "dmrg":
+        out = dmrg_sweep_timing()
     else:
         out = svd_timing(args, dev, stream)
     print(json.dumps({"part": args.part, "workload": args.workload, **out}), flush=True)
+
+
+def dmrg_sweep_timing(m_schedule=(16, 32, 64, 128, 256, 512, 1024), precision="bf16x3"):
+    """Two-site DMRG on the GPU (dmrg.py: per bond the Lanczos eigensolver, the block SVD
+    split and the environment update) for the snake-ordered 6x6 J1-J2 (J2 = 0.5) cylinder
+    from the Neel product state, one sweep per bond cap: the host wall time and the energy of
+    each sweep (no oracle at these sizes: the test suite checks the driver against the
+    oracle's DMRG to m = 64)."""
+    import torch
+    import workloads as wl
+    from paper_2007_05540_gb300 import dmrg
+    mpo = wl.heisenberg_mpo(36, wl.cylinder_pairs(6, 6, 1.0, 0.5))
+    states = [0] * 36                             # Neel: the state (x + y) mod 2 on site (x, y)
+    for x in range(6):
+        for y in range(6):
+            states[wl.snake_index(x, y, 6)] = (x + y) % 2
+    run = dmrg.GpuDMRG(mpo, (0,), precision, 20, 1e-12, states=states)
+    sweeps = []
+    for m in m_schedule:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e = run.sweep(int(m))
+        torch.cuda.synchronize()
+        sweeps.append({"m_max": int(m), "s": time.perf_counter() - t0, "energy": e,
+                       "max_bond": int(max(run.bond_dims()))})
+    return {"lattice": "6x6 J1-J2 cylinder (J2 = 0.5), 36 sites, MPO k = 26", "matvec": precision,
+            "lanczos_steps_per_bond": 20, "sweeps": sweeps, "refined_energy": run.refined_energy(),
+            "note": "one sweep = 70 two-site bond updates (left to right and back), each building its plans, "
+                    "Lanczos, block SVD split and environment update on the GPU; host wall time per sweep"}
 
 
 def svd_timing(args, dev, stream):
