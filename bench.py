@@ -924,7 +924,8 @@ def run_ours(args):
 
     out = {
         "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms,
+        "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True,
         "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": {"bf16x3": "bf16x3->f32", "tf32x3": "tf32x3->f32", "fp64": "f64"}[prec],
         "data": "synthetic (seeded; no dataset)",
