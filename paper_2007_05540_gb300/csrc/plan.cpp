@@ -18,6 +18,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <queue>
 #include <set>
 #include <stdexcept>
 #include <tuple>
@@ -196,6 +197,23 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         auto W1i = [&](int a, int t, int s, int m) { return w1i[((a * d1 + t) * d1 + s) * km + m]; };
         auto W2i = [&](int m, int t, int s, int r) { return w2i[((m * d2 + t) * d2 + s) * kr + r]; };
 
+        // ---- charge arithmetic and block lookups as tables (sector charges are distinct, so
+        // q(a) + q(wl) == q(a') is a_plus_l[a][wl] == a'), for the row-group loops below
+        std::vector<int> a_plus_l((size_t)na * kl), b_plus_r((size_t)nb * kr);
+        for (int a = 0; a < na; ++a)
+            for (int w = 0; w < kl; ++w) a_plus_l[(size_t)a * kl + w] = alpha.find(add(alpha.q(a), chl.q(w)));
+        for (int b = 0; b < nb; ++b)
+            for (int w = 0; w < kr; ++w) b_plus_r[(size_t)b * kr + w] = beta.find(add(beta.q(b), chr.q(w)));
+        std::vector<int64_t> loff((size_t)na * kl * na, -1), roff((size_t)nb * kr * nb, -1);   // -1: no block
+        for (size_t blk = 0; blk < L->offsets.size(); ++blk) {
+            const int32_t* k = &L->keys[blk * 3];
+            loff[((size_t)k[0] * kl + k[1]) * na + k[2]] = L->offsets[blk];
+        }
+        for (size_t blk = 0; blk < R->offsets.size(); ++blk) {
+            const int32_t* k = &R->keys[blk * 3];
+            roff[((size_t)k[0] * kr + k[1]) * nb + k[2]] = R->offsets[blk];
+        }
+
         // ---- canonical flop count (the oracle's two-contraction list algorithm), also per
         // output left sector a' (for the row shards)
         std::vector<double> canon1_ip, canon2_ip;
@@ -217,6 +235,11 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             double g1 = 0, g2 = 0;
             canon1_ip.assign(na, 0.0);
             canon2_ip.assign(na, 0.0);
+            // the distinct Z blocks (a', t1, t2, wr, b): a dense flag array walked in index
+            // (= lexicographic) order, or an ordered set when that domain is very large
+            const size_t zdom = (size_t)na * d1 * d2 * kr * nb;
+            const bool zdense = zdom <= ((size_t)1 << 26);
+            std::vector<char> zseen(zdense ? zdom : 0, 0);
             std::set<std::tuple<int, int, int, int, int>> zkeys;
             for (size_t b = 0; b < x->offsets.size(); ++b) {
                 int i = x->keys[b * 4], s1 = x->keys[b * 4 + 1], s2 = x->keys[b * 4 + 2], j = x->keys[b * 4 + 3];
@@ -227,18 +250,32 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                     if (f == feeds.end() || f->second.empty()) continue;
                     g1 += 2.0 * alpha.dims[pw.first] * alpha.dims[i] * beta.dims[j];
                     canon1_ip[pw.first] += 2.0 * alpha.dims[pw.first] * alpha.dims[i] * beta.dims[j];
-                    for (auto& t : f->second)
-                        zkeys.insert({pw.first, std::get<0>(t), std::get<1>(t), std::get<2>(t), j});
+                    for (auto& t : f->second) {
+                        if (zdense)
+                            zseen[((((size_t)pw.first * d1 + std::get<0>(t)) * d2 + std::get<1>(t)) * kr +
+                                   std::get<2>(t)) * nb + j] = 1;
+                        else
+                            zkeys.insert({pw.first, std::get<0>(t), std::get<1>(t), std::get<2>(t), j});
+                    }
                 }
             }
-            for (auto& z : zkeys) {
-                auto rk = R_by_ket.find({std::get<3>(z), std::get<4>(z)});
-                if (rk == R_by_ket.end()) continue;
+            auto zflops = [&](int ip, int wr, int j) {
+                auto rk = R_by_ket.find({wr, j});
+                if (rk == R_by_ket.end()) return;
                 for (int jp : rk->second) {
-                    const double f = 2.0 * alpha.dims[std::get<0>(z)] * beta.dims[std::get<4>(z)] * beta.dims[jp];
+                    const double f = 2.0 * alpha.dims[ip] * beta.dims[j] * beta.dims[jp];
                     g2 += f;
-                    canon2_ip[std::get<0>(z)] += f;
+                    canon2_ip[ip] += f;
                 }
+            };
+            if (zdense) {
+                for (size_t z = 0; z < zdom; ++z) {
+                    if (!zseen[z]) continue;
+                    const int j = (int)(z % nb), wr = (int)(z / nb % kr);
+                    zflops((int)(z / ((size_t)nb * kr * d2 * d1)), wr, j);
+                }
+            } else {
+                for (auto& z : zkeys) zflops(std::get<0>(z), std::get<3>(z), std::get<4>(z));
             }
             P->flops_canonical = g1 + g2;
             P->stats[16] = (int64_t)g1;
@@ -259,10 +296,10 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                         const CGroup& g = Q[q].cg[c];
                         RowGroup::Seg seg{c, {}};
                         for (int wl = 0; wl < kl; ++wl) {
-                            if (add(alpha.q(g.sec), chl.q(wl)) != alpha.q(ip)) continue;
+                            if (a_plus_l[(size_t)g.sec * kl + wl] != ip) continue;
                             int32_t wi = W1i(wl, t1, g.s, wm);
                             if (wi < 0) continue;
-                            int64_t off = L->offset_of({ip, wl, g.sec});
+                            int64_t off = loff[((size_t)ip * kl + wl) * na + g.sec];
                             if (off < 0) continue;
                             seg.terms.push_back({off, wi, 0});
                         }
@@ -275,6 +312,12 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                     rgs.push_back(std::move(rg));
                 }
         // ---- RW row groups (GEMM 2 columns) and the segments they need
+        std::vector<int> q_minus_m((size_t)Q.size() * km, -1);         // sector of Q - q(wm)
+        for (int q = 0; q < (int)Q.size(); ++q)
+            for (int wm = 0; wm < km; ++wm) {
+                auto qi = qid.find(add(Q[q].q, chm.q(wm), -1));
+                if (qi != qid.end()) q_minus_m[(size_t)q * km + wm] = qi->second;
+            }
         std::vector<RWGroup> rws;
         std::vector<std::set<std::pair<int, int>>> used(Q.size());     // per Q': (wm, src flat eg id)
         for (int q = 0; q < (int)Q.size(); ++q)
@@ -282,17 +325,17 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                 const CGroup& ge = Q[q].eg[e];                           // (t2, j')
                 RWGroup rw{q, e, {}};
                 for (int wm = 0; wm < km; ++wm) {
-                    auto qi = qid.find(add(Q[q].q, chm.q(wm), -1));
-                    if (qi == qid.end()) continue;
-                    const QSec& qs = Q[qi->second];
+                    const int qsrc = q_minus_m[(size_t)q * km + wm];
+                    if (qsrc < 0) continue;
+                    const QSec& qs = Q[qsrc];
                     for (int f = 0; f < (int)qs.eg.size(); ++f) {
                         const CGroup& gs = qs.eg[f];                     // (s2, j)
-                        RWGroup::Seg seg{wm, qi->second, f, {}};
+                        RWGroup::Seg seg{wm, qsrc, f, {}};
                         for (int wr = 0; wr < kr; ++wr) {
-                            if (add(beta.q(gs.sec), chr.q(wr)) != beta.q(ge.sec)) continue;
+                            if (b_plus_r[(size_t)gs.sec * kr + wr] != ge.sec) continue;
                             int32_t wi = W2i(wm, ge.s, gs.s, wr);
                             if (wi < 0) continue;
-                            int64_t off = R->offset_of({ge.sec, wr, gs.sec});
+                            int64_t off = roff[((size_t)ge.sec * kr + wr) * nb + gs.sec];
                             if (off < 0) continue;
                             seg.terms.push_back({off, wi, 0});
                         }
@@ -325,6 +368,31 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             rows_t += qs.mrows;
             qs.rw_row0 = rows_rw;
             rows_rw += qs.nrows;
+        }
+        // dense forms of the lookups the task-list loops repeat: row groups present,
+        // T column offsets (-1: none), Q + q(wm), and x's block offsets
+        std::vector<char> present_tab((size_t)Q.size() * d1 * km, 0);
+        for (auto& kv : rg_of)
+            present_tab[((size_t)std::get<0>(kv.first) * d1 + std::get<1>(kv.first)) * km + std::get<2>(kv.first)] = 1;
+        std::vector<size_t> toff_base((size_t)Q.size() * km + 1, 0);
+        for (int q = 0; q < (int)Q.size(); ++q)
+            for (int wm = 0; wm < km; ++wm) {
+                const int qs_ = q_minus_m[(size_t)q * km + wm];
+                toff_base[(size_t)q * km + wm + 1] = toff_base[(size_t)q * km + wm] + (qs_ >= 0 ? Q[qs_].eg.size() : 0);
+            }
+        std::vector<int32_t> toff_flat(toff_base.back(), -1);
+        for (int q = 0; q < (int)Q.size(); ++q)
+            for (auto& kv : Q[q].toff) toff_flat[toff_base[(size_t)q * km + kv.first.first] + kv.first.second] = kv.second;
+        std::vector<int> q_plus_m((size_t)Q.size() * km, -1);
+        for (int q = 0; q < (int)Q.size(); ++q)
+            for (int wm = 0; wm < km; ++wm) {
+                auto qi = qid.find(add(Q[q].q, chm.q(wm)));
+                if (qi != qid.end()) q_plus_m[(size_t)q * km + wm] = qi->second;
+            }
+        std::vector<int64_t> xoff((size_t)na * d1 * d2 * nb, -1);
+        for (size_t blk = 0; blk < x->offsets.size(); ++blk) {
+            const int32_t* k = &x->keys[blk * 4];
+            xoff[(((size_t)k[0] * d1 + k[1]) * d2 + k[2]) * nb + k[3]] = x->offsets[blk];
         }
         P->rows_x = rows_x; P->ld_x = ld_x; P->rows_lw = std::max<int64_t>(rows_lw, 1);
         P->rows_t = std::max<int64_t>(rows_t, 1); P->ld_t = ld_t; P->rows_rw = std::max<int64_t>(rows_rw, 1);
@@ -385,9 +453,9 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         // GEMM 1: rows of a row group x columns of one e-group, written into T
         for (auto& rg : rgs) {
             const QSec& qs = Q[rg.q];
-            auto qpi = qid.find(add(qs.q, chm.q(rg.wm)));
-            if (qpi == qid.end()) continue;
-            const QSec& qp = Q[qpi->second];
+            const int qpi = q_plus_m[(size_t)rg.q * km + rg.wm];
+            if (qpi < 0) continue;
+            const QSec& qp = Q[qpi];
             const CGroup* crow = nullptr;
             for (auto& g : qp.cg) if (g.s == rg.t1 && g.sec == rg.ip) crow = &g;
             if (!crow) continue;
@@ -402,8 +470,8 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
             int32_t sc = (int32_t)rg.segs.size();
             const int mi = alpha.dims[rg.ip];
             for (int f = 0; f < (int)qs.eg.size(); ++f) {
-                auto it = qp.toff.find({rg.wm, f});
-                if (it == qp.toff.end()) continue;
+                const int32_t tcol = toff_flat[toff_base[(size_t)qpi * km + rg.wm] + f];
+                if (tcol < 0) continue;
                 const CGroup& ge = qs.eg[f];
                 for (int m0 = 0; m0 < mi; m0 += TM)
                     for (int n0 = 0; n0 < ge.dim; n0 += TN) {
@@ -412,7 +480,7 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                         t.b_row = qs.xt_row0 + ge.row + n0;
                         t.m = std::min(TM, mi - m0);
                         t.n = std::min(TN, ge.dim - n0);
-                        t.c_off = (qp.t_row0 + crow->row + m0) * ld_t + it->second + n0;
+                        t.c_off = (qp.t_row0 + crow->row + m0) * ld_t + tcol + n0;
                         t.ldc = (int32_t)ld_t;
                         t.n_zero = (n0 + TN >= ge.dim) ? (int32_t)(pad_up(ge.dim, KPAD) - ge.dim) : 0;
                         t.seg_begin = sb;
@@ -433,16 +501,16 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                 int32_t sb = (int32_t)G2.segs.size();
                 int64_t klen = 0, kuse = 0;
                 for (auto& sg : rw.segs) {
-                    if (!present(sg.q_src, gc.s, sg.wm)) continue;
-                    auto it = qs.toff.find({sg.wm, sg.eg_src});
-                    if (it == qs.toff.end()) continue;
+                    if (!present_tab[((size_t)sg.q_src * d1 + gc.s) * km + sg.wm]) continue;
+                    const int32_t tcol = toff_flat[toff_base[(size_t)rw.q * km + sg.wm] + sg.eg_src];
+                    if (tcol < 0) continue;
                     int32_t len = (int32_t)pad_up(Q[sg.q_src].eg[sg.eg_src].dim, KPAD);
-                    G2.segs.push_back({it->second, len});
+                    G2.segs.push_back({tcol, len});
                     klen += len;
                     kuse += Q[sg.q_src].eg[sg.eg_src].dim;
                 }
                 int32_t sc = (int32_t)G2.segs.size() - sb;
-                int64_t yoff = x->offset_of({gc.sec, gc.s, ge.s, ge.sec});
+                int64_t yoff = xoff[(((size_t)gc.sec * d1 + gc.s) * d2 + ge.s) * nb + ge.sec];
                 if (yoff < 0) return false;
                 for (int m0 = 0; m0 < gc.dim; m0 += TM)
                     for (int n0 = 0; n0 < ge.dim; n0 += TN) {
@@ -624,13 +692,17 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                 std::vector<size_t> ord(nt);
                 for (size_t t = 0; t < nt; ++t) ord[t] = t;
                 std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
-                std::vector<double> load(grid, 0.0);
+                // least loaded CTA first, the lowest index among equal loads (a min-heap on
+                // (load, CTA): O(tasks log grid))
+                std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
+                                    std::greater<std::pair<double, int>>> heap;
+                for (int c = 0; c < grid; ++c) heap.push({0.0, c});
                 std::vector<std::vector<size_t>> per(grid);
                 for (size_t t : ord) {
-                    int best = 0;
-                    for (int c = 1; c < grid; ++c) if (load[c] < load[best]) best = c;
-                    load[best] += work[t];
-                    per[best].push_back(t);
+                    const std::pair<double, int> top = heap.top();
+                    heap.pop();
+                    per[top.second].push_back(t);
+                    heap.push({top.first + work[t], top.second});
                 }
                 size_t depth = 0;
                 for (auto& v : per) depth = std::max(depth, v.size());
