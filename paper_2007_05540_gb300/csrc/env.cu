@@ -79,9 +79,15 @@ extern "C" int heff_env_plan_create(const heff_layout* env_old, const heff_layou
     P->side = side;
     try {
         const int d = sp.nsec, kw = W->idx[0].nsec, kv = W->idx[3].nsec;
+        // W entries kept (nonzero in the host copy) as a dense (w, t, s, v) table, -1: dropped
+        std::vector<int32_t> wtab((size_t)kw * d * d * kv, -1);
+        for (size_t bk = 0; bk < W->offsets.size(); ++bk) {
+            const int32_t* k = &W->keys[bk * 4];
+            const int64_t o = W->offsets[bk];
+            if (W_host[o] != 0.0) wtab[(((size_t)k[0] * d + k[1]) * d + k[2]) * kv + k[3]] = (int32_t)o;
+        }
         auto widx = [&](int w, int t, int s, int v) -> int32_t {
-            int64_t o = W->offset_of({w, t, s, v});
-            return (o >= 0 && W_host[o] != 0.0) ? (int32_t)o : -1;
+            return wtab[(((size_t)w * d + t) * d + s) * kv + v];
         };
         // site blocks by key
         auto site_off = [&](int a, int s, int b) { return site->offset_of({a, s, b}); };
