@@ -40,6 +40,25 @@ using Charge = std::vector<int32_t>;
 
 namespace {
 
+// Cost of one K block of a tensor-core tile, for the LPT ordering and schedule:
+// 0: its MMA width (n rounded up to 16); 1: the operand rows it streams (the A box, 64 or
+// 128 rows, plus the B box of n rows); 2: the larger of the two, each scaled to a 128 x 256
+// tile; 3: their mean.  Chosen per GEMM (GEMM 1 lists, GEMM 2 lists).
+#ifndef HEFF_TILE_COST_G1
+#define HEFF_TILE_COST_G1 0
+#endif
+#ifndef HEFF_TILE_COST_G2
+#define HEFF_TILE_COST_G2 2
+#endif
+inline int64_t tile_width_cost(int m, int n, int model) {
+    const int64_t mma = (n + 15) / 16 * 16;
+    const int64_t rows = (m <= 64 ? 64 : 128) + (n <= 64 ? 64 : (n <= 128 ? 128 : 256));
+    if (model == 0) return mma;
+    if (model == 1) return rows;
+    if (model == 2) return std::max(mma * 384 / 256, rows);
+    return (mma * 384 / 256 + rows) / 2;
+}
+
 Charge add(const Charge& a, const Charge& b, int sb = 1) {
     Charge r(a);
     for (size_t c = 0; c < r.size(); ++c) r[c] += sb * b[c];
@@ -535,12 +554,13 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         // longest tasks first (LPT order for the persistent kernels); a tile's tensor time
         // scales with its padded K and its MMA width (n rounded up to 16)
         for (heff::GemmList* g : {&G1, &G2}) {
+            const int model = g == &G1 ? HEFF_TILE_COST_G1 : HEFF_TILE_COST_G2;
             std::vector<int64_t> work(g->tasks.size());
             std::vector<size_t> ord(g->tasks.size());
             for (size_t t = 0; t < g->tasks.size(); ++t) {
                 int64_t k = 0;
                 for (int s = 0; s < g->tasks[t].seg_count; ++s) k += g->segs[g->tasks[t].seg_begin + s].klen;
-                work[t] = k * ((g->tasks[t].n + 15) / 16 * 16);
+                work[t] = k * tile_width_cost(g->tasks[t].m, g->tasks[t].n, model);
                 ord[t] = t;
             }
             std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
@@ -679,6 +699,8 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
         // CTA pairs are scheduled the same way, an entry (two tasks) per cluster.
         if (tc && HEFF_LPT_SCHEDULE) {
             for (heff::GemmList* G : {&P->g1, &P->g2, &P->g1_alt, &P->g2_alt, &P->g1_pair, &P->g2_pair}) {
+                const int model = (G == &P->g1 || G == &P->g1_alt || G == &P->g1_pair) ? HEFF_TILE_COST_G1
+                                                                                        : HEFF_TILE_COST_G2;
                 const size_t CLn = (size_t)G->cl;
                 const size_t nt = G->tasks.size() / CLn;          // entries
                 if (nt == 0) continue;
@@ -687,7 +709,7 @@ extern "C" int heff_plan_create(const heff_layout* L, const heff_layout* W1, con
                 for (size_t t = 0; t < nt; ++t)
                     for (size_t r = 0; r < CLn; ++r) {
                         const heff::GemmTask& k = G->tasks[t * CLn + r];
-                        work[t] = std::max(work[t], (double)(k.ktotal / KPAD + 4) * ((k.n + 15) / 16 * 16));
+                        work[t] = std::max(work[t], (double)(k.ktotal / KPAD + 4) * tile_width_cost(k.m, k.n, model));
                     }
                 std::vector<size_t> ord(nt);
                 for (size_t t = 0; t < nt; ++t) ord[t] = t;
