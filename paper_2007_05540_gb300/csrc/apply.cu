@@ -22,10 +22,12 @@ using heff::fail;
 namespace heff {
 
 // ------------------------------------------------------------------ element planes
-// A workspace operand is stored as `planes` arrays of one element type:
-//   FP64   : one double plane
+// A workspace operand holds `planes` values per element, of one element type:
+//   FP64   : one double
 //   BF16X3 : hi = bf16(v), lo = bf16(v - hi)
 //   TF32X3 : hi = v with the 13 low mantissa bits cleared (exact in TF32), lo = v - hi
+// The two halves of the split precisions are interleaved by 64-byte K blocks within each
+// row (split_col): a row of ld columns takes 2 ld elements.
 template <int PREC> struct Plane;
 template <> struct Plane<HEFF_PREC_FP64> {
     using T = double;
@@ -81,14 +83,17 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // (columns b contiguous, one element per lane, all loads in flight), transposes through
 // its own shared-memory tile, and writes XT rows b, columns a contiguous (a in [m_a, a_pad)
 // are the zero padding), two columns per lane and two rows per pass: every store
-// instruction writes two full 32-column row pieces of a plane.
+// instruction writes two full 32-column row pieces of a half (hi or lo).
 constexpr int PACK_WARPS = 4;
 
 template <typename In, int PREC>
 __global__ void __launch_bounds__(32 * PACK_WARPS) pack_kernel(const PackTile* __restrict__ tiles, int ntiles,
                                                                PtrBatch xs, char* __restrict__ xt, int64_t ld,
-                                                               int64_t plane_elems, int64_t batch_elems) {
+                                                               int64_t batch_elems) {
     using E = typename Plane<PREC>::T;
+    constexpr bool SPLIT = PREC != HEFF_PREC_FP64;
+    constexpr int KB = 64 / (int)sizeof(E);          // elements per K block of one half
+    const int64_t pitch = SPLIT ? 2 * ld : ld;
     using Acc = typename std::conditional<PREC == HEFF_PREC_FP64, double, float>::type;
     __shared__ Acc s[PACK_WARPS][32][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -109,20 +114,20 @@ __global__ void __launch_bounds__(32 * PACK_WARPS) pack_kernel(const PackTile* _
             sw[r][lane] = (bv && r < na) ? to_acc<Acc>(x[(int64_t)(t.a0 + r) * t.m_b + b]) : (Acc)0;
     }
     __syncwarp();
-    E* hi = reinterpret_cast<E*>(xt) + (int64_t)bz * batch_elems;
-    E* lo = hi + plane_elems;
+    E* base = reinterpret_cast<E*>(xt) + (int64_t)bz * batch_elems;
     const int c = 2 * (lane & 15), h = lane >> 4;
     const int nb = t.m_b - t.b0;                    // XT rows of this tile
-    const int64_t o0 = (t.xt_row0 + t.b0) * ld + t.xt_col0 + t.a0 + c;
+    const int64_t col = t.xt_col0 + t.a0 + c;       // even: both columns in one K block
+    const int64_t o0 = (t.xt_row0 + t.b0) * pitch + (SPLIT ? split_col<KB>(col) : col);
 #pragma unroll 4
     for (int r = h; r < 32; r += 2) {
         if (r >= nb) break;
         E h0, l0, h1, l1;
         Plane<PREC>::split(sw[c][r], h0, l0);
         Plane<PREC>::split(sw[c + 1][r], h1, l1);
-        const int64_t o = o0 + (int64_t)r * ld;
-        Plane<PREC>::store2(hi + o, h0, h1);
-        if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lo + o, l0, l1);
+        const int64_t o = o0 + (int64_t)r * pitch;
+        Plane<PREC>::store2(base + o, h0, h1);
+        if (SPLIT) Plane<PREC>::store2(base + o + KB, l0, l1);
     }
 }
 
@@ -138,8 +143,8 @@ struct MixArgs {
     const MixTile* tiles;
     const MixTerm* terms;
     const void *L, *W1, *W2, *R;
-    char* lw; int64_t ld_lw, lw_plane;
-    char* rw; int64_t ld_rw, rw_plane;
+    char* lw; int64_t ld_lw;
+    char* rw; int64_t ld_rw;
 };
 
 template <typename In, int PREC>
@@ -151,7 +156,7 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
     const In* __restrict__ R = static_cast<const In*>(a.R);
     char* __restrict__ lw = a.lw;
     char* __restrict__ rw = a.rw;
-    const int64_t ld_lw = a.ld_lw, lw_plane = a.lw_plane, ld_rw = a.ld_rw, rw_plane = a.rw_plane;
+    const int64_t ld_lw = a.ld_lw, ld_rw = a.ld_rw;
     // FP64 path accumulates in double; the split paths in float (1-4 terms, each product
     // exact to 24 bits, well inside the 16-bit (bf16 hi+lo) / 22-bit (tf32 hi+lo) split).
     using E = typename Plane<PREC>::T;
@@ -167,9 +172,10 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
         srco[k] = m.src_off;
     }
     __syncthreads();
-    E* hi = reinterpret_cast<E*>(t.which ? rw : lw);
-    const int64_t ld = t.which ? ld_rw : ld_lw;
-    E* lo = hi + (t.which ? rw_plane : lw_plane);
+    constexpr bool SPLIT = PREC != HEFF_PREC_FP64;
+    constexpr int KB = 64 / (int)sizeof(E);          // elements per K block of one half
+    E* base = reinterpret_cast<E*>(t.which ? rw : lw);
+    const int64_t pitch = SPLIT ? 2 * (t.which ? ld_rw : ld_lw) : (t.which ? ld_rw : ld_lw);
     // warps over rows, lanes over column pairs: each thread writes two adjacent columns
     // (dst_col0 and cols_pad are multiples of 32, so the pair stores are aligned) of RW rows,
     // U pairs 64 columns apart per pass, with all loads of a term issued before its FMAs
@@ -223,7 +229,7 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
 #pragma unroll
             for (int i = 0; i < RW; ++i) {
                 if (!rv[i]) break;
-                const int64_t o = (t.dst_row0 + t.r0 + rr + i) * ld + t.dst_col0;
+                const int64_t o = (t.dst_row0 + t.r0 + rr + i) * pitch;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int c = cb + 64 * u;
@@ -231,8 +237,10 @@ __device__ __forceinline__ void mix_tile(const MixTile& t, const MixArgs& a) {
                     E h0, l0, h1, l1;
                     Plane<PREC>::split(a0[i][u], h0, l0);
                     Plane<PREC>::split(a1[i][u], h1, l1);
-                    Plane<PREC>::store2(hi + o + c, h0, h1);
-                    if (PREC != HEFF_PREC_FP64) Plane<PREC>::store2(lo + o + c, l0, l1);
+                    const int64_t col = t.dst_col0 + c;     // even: both columns in one K block
+                    const int64_t p = o + (SPLIT ? split_col<KB>(col) : col);
+                    Plane<PREC>::store2(base + p, h0, h1);
+                    if (SPLIT) Plane<PREC>::store2(base + p + KB, l0, l1);
                 }
             }
         }
@@ -260,7 +268,6 @@ struct GemmArgs {
     char* C; int64_t c_batch_elems;         // GEMM 1 output (T) and per-batch offset
     PtrBatch y;                             // GEMM 2 outputs (one per batch entry)
     int mode;                               // 0: write T (plane type), 1: write y (io type)
-    int64_t c_plane_elems;                  // plane stride of T
 };
 
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
@@ -367,7 +374,6 @@ void plan_free_device(heff_plan* p) {
     p->g1.d_tasks = p->g2.d_tasks = nullptr; p->g1.d_segs = p->g2.d_segs = nullptr;
 }
 
-static int64_t plane_elems_xt(const heff_plan* p) { return (int64_t)p->opts.max_batch * p->rows_x * p->ld_x; }
 
 template <typename In, int PREC>
 static void launch_pack_t(heff_plan* p, const PtrBatch& xs, int nb, char* ws, cudaStream_t st) {
@@ -382,7 +388,7 @@ static void launch_pack_t(heff_plan* p, const PtrBatch& xs, int nb, char* ws, cu
     cfg.attrs = at;
     cfg.numAttrs = HEFF_PDL ? 1 : 0;
     cudaLaunchKernelEx(&cfg, pack_kernel<In, PREC>, static_cast<const PackTile*>(p->d_pack), nt, xs,
-                       ws + p->off_xt, p->ld_x, plane_elems_xt(p), p->rows_x * p->ld_x);
+                       ws + p->off_xt, p->ld_x, (int64_t)p->planes * p->rows_x * p->ld_x);
 }
 
 int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, void* stream) {
@@ -392,7 +398,7 @@ int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, 
         int nb = nbatch - b0 < MAXB ? nbatch - b0 : MAXB;
         PtrBatch xs{};
         for (int b = 0; b < nb; ++b) xs.p[b] = x[b0 + b];
-        char* w = static_cast<char*>(ws) + (size_t)b0 * p->rows_x * p->ld_x * p->esize;
+        char* w = static_cast<char*>(ws) + (size_t)b0 * p->rows_x * p->ld_x * p->esize * p->planes;
         const bool f32 = p->opts.io_dtype == HEFF_DTYPE_F32;
         switch (p->opts.precision) {
             case HEFF_PREC_FP64: launch_pack_t<double, HEFF_PREC_FP64>(p, xs, nb, w, st); break;
@@ -411,8 +417,7 @@ int launch_pack_batch(heff_plan* p, const void* const* x, int nbatch, void* ws, 
 }
 
 static MixArgs mix_args(heff_plan* p, const void* L, const void* W1, const void* W2, const void* R, char* ws) {
-    return MixArgs{p->d_mix, p->d_terms, L, W1, W2, R, ws + p->off_lw, p->ld_x, p->rows_lw * p->ld_x,
-                   ws + p->off_rw, p->ld_t, p->rows_rw * p->ld_t};
+    return MixArgs{p->d_mix, p->d_terms, L, W1, W2, R, ws + p->off_lw, p->ld_x, ws + p->off_rw, p->ld_t};
 }
 
 template <typename In, int PREC>

@@ -10,6 +10,16 @@
 
 namespace heff {
 
+// Rows of the split-precision operand arrays (hi and lo halves of every element): the row
+// is cut into K blocks of KB elements (64 bytes of one half), and each K block of hi values
+// is followed by the same K block of lo values, so a row of ld columns takes 2 ld elements
+// and one 128-byte row of a TMA box carries both halves of a K block.  Column c of a row
+// sits at element c + KB floor(c / KB); its lo half is KB elements further on.
+template <int KB>
+__host__ __device__ __forceinline__ int64_t split_col(int64_t c) {
+    return c + (c & ~(int64_t)(KB - 1));
+}
+
 // binary64 -> binary32, round to nearest even.  Results below the normal binary32 range
 // (|x| < 2^-126) become a zero of the same sign (no subnormal results); values above it
 // round to infinity; infinities stay infinite and NaNs stay NaN.

@@ -2,9 +2,10 @@
 // split-precision paths of the two-site H_eff matvec (Section II-C / Fig. 1d).
 //
 // Each task is one output tile C[m x n] (m <= 128, n <= TN) = sum over its contraction
-// segments of A[a_row + r, k] * B[b_row + c, k].  A and B live in the workspace as two
-// planes (hi, lo) of one element type:
-//   BF16X3: bf16 planes, kind::f16 MMAs;  TF32X3: fp32 planes read as TF32, kind::tf32.
+// segments of A[a_row + r, k] * B[b_row + c, k].  A and B live in the workspace as hi and
+// lo halves of one element type, interleaved by 64-byte K blocks within each row, so one
+// TMA box with 128-byte rows brings both halves of a K block:
+//   BF16X3: bf16 halves, kind::f16 MMAs;  TF32X3: fp32 halves read as TF32, kind::tf32.
 // Every K block does three MMAs, A_hi.B_hi + A_hi.B_lo + A_lo.B_hi, accumulated in FP32
 // in tensor memory (the "3-product" split: error ~ 2^-16 (bf16) / 2^-22 (tf32) relative).
 //
@@ -21,7 +22,8 @@
 // which biases a long sum toward zero (relative bias growing with the number of steps);
 // chunking bounds the steps per accumulator.
 // T (GEMM 1) leaves through TMA: each warp splits 32 rows x 32 columns into hi/lo in
-// registers, writes them to a swizzled shared-memory box and issues bulk tensor stores;
+// registers, writes them to a swizzled shared-memory box (hi and lo K blocks side by side,
+// the workspace's interleaved rows) and issues bulk tensor stores;
 // quarters with fewer than 32 valid rows go through an XOR-swizzled transpose and leave
 // in 16-byte row pieces (several rows per store instruction); y (GEMM 2, per-block pitch)
 // leaves through the same transpose in 128-byte row stores.
@@ -63,15 +65,15 @@ template <int PREC> __host__ __device__ constexpr int tc_epi_warps() {
 template <int PREC> __host__ __device__ constexpr int tc_threads() { return 64 + 32 * tc_epi_warps<PREC>(); }
 constexpr int TM = 128;
 
-// Shared-memory ring: STAGES x {A_hi, A_lo (128 rows), B_hi, B_lo (TN rows)}, each row SWZ
-// bytes of one K block (SWZ = 64: 32 bf16 / 16 fp32; SWZ = 128: 64 bf16 / 32 fp32), then
-// 32 KB shared by the epilogue warps (per warp: one hi + lo pair of TMA store boxes, or the
-// 32 x 32 float transpose), then barriers.
+// Shared-memory ring: STAGES x {A (128 rows), B (TN rows)}, each row one K block of the hi
+// half (SWZ = 64 bytes: 32 bf16 / 16 fp32) followed by the same K block of the lo half, in
+// the 128-byte swizzle; then 32 KB shared by the epilogue warps (per warp: the TMA store
+// boxes of a 32-column chunk of T, or the 32 x 32 float transpose), then barriers.
 template <int TN, int STAGES, int SWZ>
 struct Smem {
-    static constexpr int A_BYTES = TM * SWZ;
-    static constexpr int B_BYTES = TN * SWZ;
-    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int A_BYTES = TM * 2 * SWZ;
+    static constexpr int B_BYTES = TN * 2 * SWZ;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int EPI_OFF = STAGES * STAGE_BYTES;  // 1024-byte aligned
     static constexpr int EPI_BYTES = 32768;
     static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
@@ -213,11 +215,10 @@ struct TcArgs {
     const GemmTask* tasks;
     const KSeg* segs;
     int ntasks, nbatch;
-    int64_t a_plane_rows, b_plane_rows;   // row offset of the lo plane in the A / B maps
     int64_t a_batch_rows, b_batch_rows;   // row offset per batch entry
-    char* C;                              // mode 0: T (hi plane base)
-    int64_t c_batch_elems, c_plane_elems;
-    int c_batch_rows, c_plane_rows;       // the same in rows of the T store map
+    char* C;                              // mode 0: T
+    int64_t c_batch_elems;                // element offset of T per batch entry
+    int c_batch_rows;                     // the same in rows of the T store map
     PtrBatch y;                           // mode 1: outputs per batch entry
     int mode;                             // 0: write T planes, 1: write y
     int kchunk;                           // K blocks per accumulation chunk (0: whole tile)
@@ -237,6 +238,7 @@ struct TcArgs {
 template <int PREC, int TN, int STAGES, int SWZ, int CL>
 __global__ void __launch_bounds__(tc_threads<PREC>(), 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
+    static_assert(SWZ == 64, "a K block of one half is 64 bytes; hi + lo fill a 128-byte row");
     using S = Smem<TN / CL, STAGES, SWZ>;      // B rows per CTA: TN, or TN / 2 in a pair
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -308,8 +310,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             const GemmTask t = tn;
             if (gi + ncl < total) tn = g.tasks[CL * ent(gi + ncl) + rank];
             const int b = g.b0 + bat(gi);
-            const int ah = (int)(t.a_row + b * g.a_batch_rows), al = (int)(ah + g.a_plane_rows);
-            const int bh = (int)(t.b_row + b * g.b_batch_rows), bl = (int)(bh + g.b_plane_rows);
+            const int ar = (int)(t.a_row + b * g.a_batch_rows), br = (int)(t.b_row + b * g.b_batch_rows);
             const int ia = t.m <= 64 ? 0 : 1, ib = t.n <= 64 ? 0 : (t.n <= 128 ? 1 : 2);
             const CUtensorMap* ma = &maps.a[CL == 1 ? ia : 1];   // a pair always loads 128 A rows
             const CUtensorMap* mb = &maps.b[ib];
@@ -319,6 +320,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
             const CUtensorMap* mh = hb == 0 ? &maps.bq : &maps.b[hb - 1];
             const uint32_t bytes = CL == 1 ? 2u * (uint32_t)((64 << ia) + (64 << ib)) * SWZ
                                            : (uint32_t)CL * 2u * (uint32_t)(128 + (32 << hb)) * SWZ;
+            // a K block at column k of the rows starts at element 2 k of the interleaved rows
             KSeg sn = t.seg_count > 0 ? g.segs[t.seg_begin] : KSeg{};
             for (int s = 0; s < t.seg_count && ok; ++s) {
                 const KSeg sg = sn;
@@ -328,18 +330,14 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     uint8_t* base = smem + st * S::STAGE_BYTES;
                     if constexpr (CL == 1) {
                         mbar_expect_tx(&full[st], bytes);
-                        tma_load(base, ma, &full[st], k, ah);
-                        tma_load(base + S::A_BYTES, ma, &full[st], k, al);
-                        tma_load(base + 2 * S::A_BYTES, mb, &full[st], k, bh);
-                        tma_load(base + 2 * S::A_BYTES + S::B_BYTES, mb, &full[st], k, bl);
+                        tma_load(base, ma, &full[st], 2 * k, ar);
+                        tma_load(base + S::A_BYTES, mb, &full[st], 2 * k, br);
                     } else {
                         // both CTAs' loads complete on the even CTA's barrier, which expects them all
                         const uint32_t fb = full_pair + (uint32_t)(st * sizeof(uint64_t));
                         if (rank == 0) mbar_expect_tx(&full[st], bytes);
-                        tma_load_pair(base, ma, fb, k, ah);
-                        tma_load_pair(base + S::A_BYTES, ma, fb, k, al);
-                        tma_load_pair(base + 2 * S::A_BYTES, mh, fb, k, bh + (int)rank * half);
-                        tma_load_pair(base + 2 * S::A_BYTES + S::B_BYTES, mh, fb, k, bl + (int)rank * half);
+                        tma_load_pair(base, ma, fb, 2 * k, ar);
+                        tma_load_pair(base + S::A_BYTES, mh, fb, 2 * k, br + (int)rank * half);
                     }
                     ++issued;
                     if (++st == STAGES) { st = 0; ph ^= 1; }
@@ -372,9 +370,9 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         const int CH = g.kchunk > 0 ? g.kchunk : 0x7fffffff;
         uint32_t ccount = 0;                   // accumulator chunk counter
         uint32_t st = 0, ph = 0;               // ring stage and its phase parity
-        const uint64_t dsc0 = sdesc<SWZ>(su32(smem));
-        constexpr uint64_t O_ALO = S::A_BYTES >> 4, O_BHI = (2 * S::A_BYTES) >> 4;
-        constexpr uint64_t O_BLO = (2 * S::A_BYTES + S::B_BYTES) >> 4, O_STAGE = S::STAGE_BYTES >> 4;
+        const uint64_t dsc0 = sdesc<2 * SWZ>(su32(smem));
+        // the lo half of a K block is SWZ bytes into each 128-byte row
+        constexpr uint64_t O_LO = (uint64_t)SWZ >> 4, O_B = S::A_BYTES >> 4, O_STAGE = S::STAGE_BYTES >> 4;
         bool ok = true;
         GemmTask tn = cid < total ? g.tasks[CL * ent(cid) + rank] : GemmTask{};
         for (long gi = cid; gi < total && ok; gi += ncl) {
@@ -406,8 +404,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                 }
                 if (!(ok = mbar_wait(&full[st], ph, abort_flag, g.err))) break;
                 tc_fence_after();
-                const uint64_t ahi = dsc0 + st * O_STAGE, alo = ahi + O_ALO;
-                const uint64_t bhi = ahi + O_BHI, blo = ahi + O_BLO;
+                const uint64_t ahi = dsc0 + st * O_STAGE, alo = ahi + O_LO;
+                const uint64_t bhi = ahi + O_B, blo = bhi + O_LO;
 #pragma unroll
                 for (int kk = 0; kk < KSUB; ++kk) {
                     const uint64_t o = (uint64_t)(kk * 32) >> 4;     // 32-byte step inside the row
@@ -451,8 +449,11 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         constexpr int NEPI = tc_epi_warps<PREC>();
         constexpr int NH = NEPI / 4;                                // warps per lane quarter
         constexpr int SLOT = S::EPI_BYTES / NEPI;
-        constexpr int BOX = 32 * 32 * (int)sizeof(E);              // one plane of a 32 x 32 box
-        static_assert(2 * BOX <= SLOT, "a hi + lo pair of store boxes fits an epilogue slot");
+        // a 32-column chunk of T rows: 32 rows of hi + lo K blocks, 128 bytes per K block
+        // (one box for bf16, two for fp32), BOX bytes per box
+        constexpr int BOX = 32 * 128;
+        constexpr int NBOX = 32 * (int)sizeof(E) / 64;
+        static_assert(NBOX * BOX <= SLOT, "the store boxes of a chunk fit an epilogue slot");
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int h = (warp - 2) >> 2;          // its chunk phase within the quarter
         uint8_t* slot = smem + S::EPI_OFF + (warp - 2) * SLOT;
@@ -490,10 +491,11 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     // the slot's previous bulk stores must have finished reading it
                     if (lane == 0) bulk_wait_read<0>();
                     __syncwarp();
-                    const uint32_t hb = slot_s, lb = hb + BOX;
+                    const uint32_t hb = slot_s;
                     const int nv = t.n - c0;                   // valid columns in this chunk
                     if constexpr (PREC == HEFF_PREC_BF16X3) {
-                        // row = lane: 64 bytes per plane, 16-byte chunk j at j ^ ((row >> 1) & 3)
+                        // row = lane: the 32 hi values (16-byte chunks 0-3), then the 32 lo
+                        // values (chunks 4-7), chunk j stored at j ^ (row & 7)
                         uint32_t h2[16], l2[16];
 #pragma unroll
                         for (int p = 0; p < 16; ++p) {
@@ -504,15 +506,17 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                             h2[p] = *reinterpret_cast<const uint32_t*>(&h);
                             l2[p] = *reinterpret_cast<const uint32_t*>(&l);
                         }
-                        const uint32_t ro = (uint32_t)lane * 64;
+                        const uint32_t ro = (uint32_t)lane * 128;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const uint32_t o = ro + ((uint32_t)(j ^ ((lane >> 1) & 3)) << 4);
-                            st_shared_v4(hb + o, h2[4 * j], h2[4 * j + 1], h2[4 * j + 2], h2[4 * j + 3]);
-                            st_shared_v4(lb + o, l2[4 * j], l2[4 * j + 1], l2[4 * j + 2], l2[4 * j + 3]);
+                            const uint32_t oh = ro + ((uint32_t)(j ^ (lane & 7)) << 4);
+                            const uint32_t ol = ro + ((uint32_t)((4 + j) ^ (lane & 7)) << 4);
+                            st_shared_v4(hb + oh, h2[4 * j], h2[4 * j + 1], h2[4 * j + 2], h2[4 * j + 3]);
+                            st_shared_v4(hb + ol, l2[4 * j], l2[4 * j + 1], l2[4 * j + 2], l2[4 * j + 3]);
                         }
                     } else {
-                        // row = lane: 128 bytes per plane, 16-byte chunk j at j ^ (row & 7)
+                        // row = lane: box i holds columns 16 i .. 16 i + 15, the 16 hi values
+                        // (chunks 0-3) then the 16 lo values (chunks 4-7), chunk j at j ^ (row & 7)
                         uint32_t hv[32], lv[32];
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
@@ -524,17 +528,24 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                         }
                         const uint32_t ro = (uint32_t)lane * 128;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const uint32_t o = ro + ((uint32_t)(j ^ (lane & 7)) << 4);
-                            st_shared_v4(hb + o, hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
-                            st_shared_v4(lb + o, lv[4 * j], lv[4 * j + 1], lv[4 * j + 2], lv[4 * j + 3]);
-                        }
+                        for (int i = 0; i < 2; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const uint32_t bb = hb + (uint32_t)(i * BOX);
+                                const uint32_t oh = ro + ((uint32_t)(j ^ (lane & 7)) << 4);
+                                const uint32_t ol = ro + ((uint32_t)((4 + j) ^ (lane & 7)) << 4);
+                                const int e = 16 * i + 4 * j;
+                                st_shared_v4(bb + oh, hv[e], hv[e + 1], hv[e + 2], hv[e + 3]);
+                                st_shared_v4(bb + ol, lv[e], lv[e + 1], lv[e + 2], lv[e + 3]);
+                            }
                     }
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        tma_store(&maps.c, hb, x0 + c0, yh);
-                        tma_store(&maps.c, lb, x0 + c0, yh + g.c_plane_rows);
+                        // logical column x0 + c0 (a multiple of 32) starts at element 2 (x0 + c0)
+#pragma unroll
+                        for (int i = 0; i < NBOX; ++i)
+                            tma_store(&maps.c, hb + (uint32_t)(i * BOX), 2 * (x0 + c0) + i * (128 / (int)sizeof(E)), yh);
                         bulk_commit();
                     }
                     continue;
@@ -551,11 +562,14 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                     // columns of one row, RPI rows per store instruction.  T offsets, pitches
                     // and chunk starts are multiples of 32 elements and a tile's columns
                     // (with its zero padding) end on a multiple of 32, so every group is
-                    // aligned and a chunk that starts inside the tile lies inside it.
+                    // aligned, lies in one K block, and a chunk that starts inside the tile
+                    // lies inside it.
                     constexpr int VEC = 16 / (int)sizeof(E), LPR = 32 / VEC, RPI = 32 / LPR;
                     const int cc = (lane % LPR) * VEC, rsub = lane / LPR;
-                    E* hi = reinterpret_cast<E*>(g.C) + t.c_off + (int64_t)b * g.c_batch_elems + c0 + cc;
-                    E* lo = hi + g.c_plane_elems;
+                    const int64_t trow = t.c_off / t.ldc, tcol = t.c_off % t.ldc;
+                    E* hi = reinterpret_cast<E*>(g.C) + (int64_t)b * g.c_batch_elems + trow * 2 * t.ldc +
+                            split_col<KB>(tcol + c0 + cc);
+                    E* lo = hi + KB;
                     if (c0 < ncols) {
                         for (int r0 = 0; r0 < rows; r0 += RPI) {
                             const int rr = r0 + rsub;
@@ -583,7 +597,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
                                     lv[p] = (__float_as_uint(f - __uint_as_float(h)) + 0x1000u) & 0xffffe000u;
                                 }
                             }
-                            const int64_t o = (int64_t)(q * 32 + rr) * t.ldc;
+                            const int64_t o = (int64_t)(q * 32 + rr) * 2 * t.ldc;
                             *reinterpret_cast<uint4*>(hi + o) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                             *reinterpret_cast<uint4*>(lo + o) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                         }
@@ -661,13 +675,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, uint32_t box_rows, int swz) {
+// A 2-D map over rows of `pitch` elements whose boxes are box_rows x swz bytes (the
+// operand arrays: 128-byte boxes, a K block of the hi half and the same of the lo half).
+int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t pitch, uint32_t box_rows, int swz) {
     auto fn = encode_fn();
     if (!fn) return fail(HEFF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     const bool bf = prec == HEFF_PREC_BF16X3;
     const uint32_t es = bf ? 2 : 4;
-    cuuint64_t dims[2] = {ld, rows};
-    cuuint64_t strides[1] = {ld * es};
+    cuuint64_t dims[2] = {pitch, rows};
+    cuuint64_t strides[1] = {pitch * es};
     cuuint32_t box[2] = {(cuuint32_t)swz / es, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
@@ -679,12 +695,13 @@ int make_map(CUtensorMap* m, void* base, int prec, uint64_t rows, uint64_t ld, u
     return HEFF_OK;
 }
 
-// Kernel configurations: 64-byte K blocks; N tile 256 with a 4-stage ring (4 x 48 KB,
+// Kernel configurations: K blocks of 64 bytes per half (128-byte rows of hi + lo); N tile
+// 256 with a 4-stage ring (4 x 48 KB,
 // 512 TMEM columns) or N tile 128 with a 6-stage ring (6 x 32 KB, 256 TMEM columns).
 #ifndef HEFF_SWZ_TC
 #define HEFF_SWZ_TC 64
 #endif
-constexpr int SWZ_TC = HEFF_SWZ_TC;      // bytes of one K block row (32, 64 or 128)
+constexpr int SWZ_TC = HEFF_SWZ_TC;      // bytes of one K block of one half (hi + lo: a 128-byte row)
 static_assert(SWZ_TC / (int)sizeof(__nv_bfloat16) <= KPAD, "a K block must not span two contraction segments");
 // 64-byte K spans per accumulation chunk in GEMM 2 (32 bf16 / 16 tf32 elements each): long
 // enough that a chunk's MMAs (about 0.5 us per block at N = 256) hide the epilogue's
@@ -756,27 +773,30 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
         // a workspace new to the plan: clear its sticky error flag (caller memory, contents unknown)
         cudaError_t ez = cudaMemsetAsync(w + p->off_flags, 0, sizeof(int), st);
         if (ez != cudaSuccess) return fail(HEFF_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(ez));
+        // Operand rows interleave the hi and lo halves by K block: 2 ld elements per row, boxes
+        // of 128-byte rows (a K block of both halves).
         // [0,1] LW (64, 128 rows)  [2,3,4] XT (64, 128, 256)  [5,6] T (64, 128)  [7,8,9] RW (64, 128, 256)
-        // [10] T store boxes: 32 rows x 32 elements (64-byte swizzle for bf16, 128-byte for fp32)
+        // [10] T store boxes: 32 rows x 128 bytes
         struct { char* base; int64_t rows, ld; int slot, nbox; } ops[4] = {
-            {w + p->off_lw, 2 * p->rows_lw, p->ld_x, 0, 2},
-            {w + p->off_xt, 2 * B * p->rows_x, p->ld_x, 2, 3},
-            {w + p->off_t, 2 * B * p->rows_t, p->ld_t, 5, 2},
-            {w + p->off_rw, 2 * p->rows_rw, p->ld_t, 7, 3}};
+            {w + p->off_lw, p->rows_lw, p->ld_x, 0, 2},
+            {w + p->off_xt, B * p->rows_x, p->ld_x, 2, 3},
+            {w + p->off_t, B * p->rows_t, p->ld_t, 5, 2},
+            {w + p->off_rw, p->rows_rw, p->ld_t, 7, 3}};
         for (auto& o : ops)
             for (int k = 0; k < o.nbox; ++k) {
-                int rc = make_map(&m[o.slot + k], o.base, PREC, (uint64_t)o.rows, (uint64_t)o.ld, 64u << k, SWZ_TC);
+                int rc = make_map(&m[o.slot + k], o.base, PREC, (uint64_t)o.rows, (uint64_t)(2 * o.ld), 64u << k,
+                                  2 * SWZ_TC);
                 if (rc) return rc;
             }
-        int rc = make_map(&m[10], w + p->off_t, PREC, (uint64_t)(2 * B * p->rows_t), (uint64_t)p->ld_t, 32u,
-                          PREC == HEFF_PREC_BF16X3 ? 64 : 128);
+        int rc = make_map(&m[10], w + p->off_t, PREC, (uint64_t)(B * p->rows_t), (uint64_t)(2 * p->ld_t), 32u,
+                          2 * SWZ_TC);
         if (rc) return rc;
         // [11] XT, [12] RW with 32-row boxes (halves of a 64-row B box for CTA pairs)
-        if ((rc = make_map(&m[11], w + p->off_xt, PREC, (uint64_t)(2 * B * p->rows_x), (uint64_t)p->ld_x, 32u,
-                           SWZ_TC)))
+        if ((rc = make_map(&m[11], w + p->off_xt, PREC, (uint64_t)(B * p->rows_x), (uint64_t)(2 * p->ld_x), 32u,
+                           2 * SWZ_TC)))
             return rc;
-        if ((rc = make_map(&m[12], w + p->off_rw, PREC, (uint64_t)(2 * p->rows_rw), (uint64_t)p->ld_t, 32u,
-                           SWZ_TC)))
+        if ((rc = make_map(&m[12], w + p->off_rw, PREC, (uint64_t)p->rows_rw, (uint64_t)(2 * p->ld_t), 32u,
+                           2 * SWZ_TC)))
             return rc;
         p->tmap_ws[slot] = ws;
     }
@@ -798,16 +818,12 @@ int launch_tc_t(heff_plan* p, int which, void* ws, void* const* y, int nbatch, c
         g.b0 = b0;
         g.err = reinterpret_cast<int*>(w + p->off_flags);
         if (which == 1) {
-            g.a_plane_rows = p->rows_lw; g.b_plane_rows = B * p->rows_x;
             g.a_batch_rows = 0; g.b_batch_rows = p->rows_x;
             g.C = w + p->off_t;
-            g.c_batch_elems = p->rows_t * p->ld_t;
-            g.c_plane_elems = B * p->rows_t * p->ld_t;
+            g.c_batch_elems = p->rows_t * 2 * p->ld_t;
             g.c_batch_rows = (int)p->rows_t;
-            g.c_plane_rows = (int)(B * p->rows_t);
             g.mode = 0;
         } else {
-            g.a_plane_rows = B * p->rows_t; g.b_plane_rows = p->rows_rw;
             g.a_batch_rows = p->rows_t; g.b_batch_rows = 0;
             for (int b = 0; b < nb; ++b) g.y.p[b] = y[b0 + b];
             g.mode = 1;
