@@ -5,7 +5,9 @@
   pairing);
 * heff_apply_batched captured once in a CUDA graph and replayed gives bitwise the
   results of the uncaptured call, and each batch entry matches the oracle;
-* the same at the electron workload's full size with 32 vectors (sampled sectors).
+* the same at the electron workload's full size with 32 vectors (sampled sectors);
+* a batch of 70 vectors (two launches per kernel, 64 entries and 6) equals the single
+  applies bitwise.
 """
 import numpy as np
 import pytest
@@ -153,3 +155,25 @@ def test_apply_host_equals_device_apply(pinned):
     ref = y_dev.cpu()
     for t in ys:
         assert torch.equal(t, ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_batch_of_more_than_one_launch(prec):
+    """70 vectors run as two launches per kernel (64 entries, then 6): the later launch's
+    pack, GEMM 1 and GEMM 2 address their entries by the absolute batch index in the
+    interleaved hi/lo operand rows.  Every entry equals its own apply bitwise, and entries
+    0, 64 and 69 match the oracle."""
+    nb = 70
+    w, lays, plan, d, xs = _setup("spin_m64", nb, prec)
+    ws = plan.workspace()
+    ys = _batched(plan, d, xs, ws)
+    for b in (0, 1, 63, 64, 65, 69):
+        y1 = torch.full_like(xs[b], float("nan"))
+        heff.heff_apply(plan.handle, d["L"], d["W1"], d["W2"], d["R"], xs[b], y1, ws)
+        torch.cuda.synchronize()
+        assert torch.equal(ys[b], y1), b
+    for b in (0, 64, 69):
+        L, W1, W2, R, x = oh.problem_from_workload(w, b)
+        y_ref = oracle_flat(lays[4], oh.heff_apply(L, W1, W2, R, x))
+        y = ys[b].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref) < (1e-3 if prec == "bf16x3" else 1e-5)
