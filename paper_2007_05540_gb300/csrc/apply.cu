@@ -267,7 +267,7 @@ struct GemmArgs {
     int64_t ld;                             // shared row pitch of A and B
     char* C; int64_t c_batch_elems;         // GEMM 1 output (T) and per-batch offset
     PtrBatch y;                             // GEMM 2 outputs (one per batch entry)
-    int mode;                               // 0: write T (plane type), 1: write y (io type)
+    int mode;                               // 0: write T (operand type), 1: write y (io type)
 };
 
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {

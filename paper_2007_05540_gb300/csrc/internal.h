@@ -179,10 +179,11 @@ struct heff_layout {
 
 struct heff_plan {
     heff_plan_opts opts{};
-    int planes = 1;           // operand planes (hi/lo) in the workspace
-    int esize = 8;            // bytes per plane element
+    int planes = 1;           // values per operand element in the workspace (hi and lo: 2)
+    int esize = 8;            // bytes per value
     int64_t nelem_x = 0, nelem_L = 0, nelem_R = 0, nelem_W1 = 0, nelem_W2 = 0;
-    // operand arrays (rows x pitch, per plane)
+    // operand arrays (rows x pitch columns; a row holds planes x pitch values, the split
+    // precisions' hi and lo interleaved by K block)
     int64_t rows_x = 0, ld_x = 0, rows_lw = 0, rows_t = 0, ld_t = 0, rows_rw = 0;
     // workspace byte offsets
     size_t off_xt = 0, off_lw = 0, off_t = 0, off_rw = 0, off_flags = 0, ws_bytes = 0;

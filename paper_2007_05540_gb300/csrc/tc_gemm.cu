@@ -220,7 +220,7 @@ struct TcArgs {
     int64_t c_batch_elems;                // element offset of T per batch entry
     int c_batch_rows;                     // the same in rows of the T store map
     PtrBatch y;                           // mode 1: outputs per batch entry
-    int mode;                             // 0: write T planes, 1: write y
+    int mode;                             // 0: write T (interleaved hi/lo rows), 1: write y
     int kchunk;                           // K blocks per accumulation chunk (0: whole tile)
     int y_f64;                            // y element type (mode 1)
     int b0;                               // first batch entry of this launch
@@ -441,8 +441,9 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
         // ------------------------------------------------ epilogue
         // Each warp drains its 32 TMEM lanes (tile rows) 32 columns at a time (tcgen05.ld:
         // thread = row); the warps of a lane quarter take alternate 32-column chunks.  T, full
-        // quarters: hi/lo split in registers, swizzled box in shared memory, two bulk tensor
-        // stores (hi plane, lo plane).  Otherwise: transpose through a 32 x 32 buffer (XOR
+        // quarters: hi/lo split in registers, swizzled box of 128-byte rows (a K block of hi
+        // values, then of lo values) in shared memory, bulk tensor stores (one box for bf16,
+        // two for fp32).  Otherwise: transpose through a 32 x 32 buffer (XOR
         // swizzled: conflict-free both ways) and store row by row with consecutive lanes on
         // consecutive columns.
         using E = typename std::conditional<PREC == HEFF_PREC_BF16X3, __nv_bfloat16, float>::type;
